@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark: H^2 matrix-vector product on GB300, memory-bound single-vector workload.
+
+Workload (default): N = 2^20 points on a 1024 x 1024 grid in [0,1]^2, Gaussian kernel
+exp(-r^2/0.01), leaf size 64, 8 x 8 Chebyshev grid (rank 64), eta = 0.7, nv = 1,
+x ~ N(0,1). A step is one full product Y = A_H2 X (upsweep, all-level coupling
+product, dense near field, downsweep, epilogue) in FP32. The headline metric is the
+algorithmic HBM throughput of the product: the operator entries it must stream (coupling
+blocks, dense blocks, leaf bases twice, transfers twice) plus X read and Y written,
+divided by the device time of one product. Gflop/s counts 2 flops per entry per vector.
+
+Timing: W warm-up products, then K timed products with the L2 flushed (a 512 MB write)
+before each one, outside the events; CUDA events on the launching stream; barrier and
+synchronize on both sides; max over ranks. Several GPUs run independent replicas
+(no collective on the data path): the value is the sum over ranks.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload
+family instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic_inputs as si  # noqa: E402
+
+METRIC = "H2 matvec GB/s (nv=1, 2D Gaussian grid N=2^20, rank 64)"
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def entry_counts(info, nv=1):
+    """Matrix entries a product streams, and the vector elements it reads / writes."""
+    mat = info.coupling_entries + info.dense_entries + 2 * info.basis_entries + 2 * info.transfer_entries
+    vec = 2 * info.n * nv
+    return mat, vec
+
+
+def oracle_entry_counts(h):
+    lvl, t, s, dt, ds = h.blocks()
+    lo, hi = h.ranges()
+    k = h.rank
+    dense = int(np.sum((hi[dt] - lo[dt]) * (hi[ds] - lo[ds])))
+    return len(t) * k * k + dense + 2 * h.n * k + 2 * (h.nnodes - 1) * k * k
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(steps: int = 0):
+    """The oracle (plain FP64 C, 1 thread) on a bounded sample: the same workload family
+    at N = 2^16 (256 x 256 grid, same kernel, rank, leaf size and eta), blocks stored."""
+    import oracle
+    w = si.grid_gauss(256)
+    pts = w.make_points()
+    h = oracle.OracleH2(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta, assemble=True)
+    x = w.make_x(len(pts))
+    h.matvec(x)  # warm-up
+    nrep = steps if steps > 0 else 5
+    times = []
+    for _ in range(nrep):
+        t0 = time.perf_counter()
+        h.matvec(x)
+        times.append(time.perf_counter() - t0)
+    ent = oracle_entry_counts(h)
+    nbytes = 8 * (ent + 2 * len(pts))
+    t = statistics.mean(times)
+    return {"value": nbytes / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"256x256 grid (N=65536) of the same kernel/rank/leaf/eta, FP64 blocks stored, "
+                      f"{nrep} products, mean {t * 1e3:.0f} ms", "ms_per_product": t * 1e3,
+            "gflops": 2 * ent / t / 1e9}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    res = None
+    for _ in range(max(0, args.warmup)):
+        pass
+    res = cpu_baseline(steps=max(1, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms_per_product"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "grid256_gauss (bounded sample of grid1024_gauss)", "n": 65536, "nv": 1,
+                       "rank": 64, "leaf": 64, "eta": 0.7},
+            "cpu_baseline": {k: res[k] for k in ("kind", "cores", "sample", "value", "unit")},
+            "e2e": {"value": res["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import paper_2109_05451_gb300 as h2
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = si.GRID1024_GAUSS
+    pts = w.make_points()
+    t0 = time.perf_counter()
+    op = h2.H2Operator(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    build_s = time.perf_counter() - t0
+    info = op.info
+    n = op.n
+    x_host = w.make_x(n)[:, 0]
+    mat_entries, vec_elems = entry_counts(info)
+    flops = 2 * mat_entries
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peak_hbm, peak_kind = measured_peaks()
+
+    def time_products(prec, steps, warmup):
+        t_up = time.perf_counter()
+        op.upload(prec)
+        upload_s = time.perf_counter() - t_up
+        es = 8 if prec == "fp64" else 4
+        X = torch.from_numpy(x_host).to(device="cuda", dtype=op.dtype)
+        Y = torch.empty_like(X)
+        for _ in range(warmup):
+            op.matvec(X, Y)
+        h2.h2_get_timing(op.handle)  # reset counters
+        h2.h2_set_timing(op.handle, True)
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            op.matvec(X, Y)
+            b.record(stream)
+        barrier()
+        h2.h2_set_timing(op.handle, False)
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        phase_ms, phase_launches, prods = h2.h2_get_timing(op.handle)
+        return {"prec": prec, "esize": es, "step_ms": step_ms, "phase_ms": phase_ms / max(prods, 1),
+                "phase_launches": phase_launches, "products": prods, "upload_s": upload_s, "X": X, "Y": Y}
+
+    res_fp64 = None
+    if not args.no_fp64:
+        res_fp64 = time_products("fp64", max(3, args.steps // 2), max(3, args.warmup))
+        del res_fp64["X"], res_fp64["Y"]
+
+    with ClockSampler(local) as clk:
+        res = time_products("fp32", args.steps, max(3, args.warmup))
+    clocks = clk.summary()
+    ms_local = float(np.sum(res["step_ms"]))
+    ms_t = torch.tensor([ms_local], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_total = float(ms_t.item())
+    ms_step = ms_total / args.steps
+    bytes_step = 4 * (mat_entries + vec_elems)
+    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the all-level coupling product (phase 1)
+    cpl_bytes = 4 * (info.coupling_entries + (info.n_nodes + 1) * info.rank * 2)
+    cpl_ms = float(res["phase_ms"][1])
+    cpl_gbs = cpl_bytes / (cpl_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "coupling_traffic.json")
+    if os.path.exists(prof):
+        traffic = json.load(open(prof)).get("fp32_bytes_per_launch")
+
+    # end to end through the public API: pinned host X -> device, product, Y -> host
+    X = res["X"]
+    Y = res["Y"]
+    xh = torch.from_numpy(x_host.astype(np.float32)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(3):
+        X.copy_(xh, non_blocking=True)
+        op.matvec(X, Y)
+        yh.copy_(Y, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        X.copy_(xh, non_blocking=True)
+        op.matvec(X, Y)
+        yh.copy_(Y, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * bytes_step / (float(e2e_t.item()) * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline()
+            cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as exc:  # the baseline is context; its failure must not hide the GPU line
+            cpu = {"value": None, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    launches_per_product = int(np.sum(res["phase_launches"])) // max(res["products"], 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "nv": 1, "rank": info.rank, "leaf": info.leaf_size, "eta": w.eta,
+                   "kernel": "exp(-r^2/0.01)", "depth": info.depth, "coupling_blocks": info.n_coupling,
+                   "dense_blocks": info.n_dense, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (512 MB write) before every timed product"},
+        "gflops": world * flops / (ms_step * 1e-3) / 1e9,
+        "bytes_per_step": bytes_step,
+        "frac_of_hbm": (bytes_step / (ms_step * 1e-3) / 1e9) / peak_hbm,
+        "phases_ms": dict(zip(h2.PHASES, [float(v) for v in res["phase_ms"]])),
+        "roofline": {"kernel": "coupling_rows (all-level coupling product, Alg 4)", "bound": "hbm",
+                     "achieved": cpl_gbs, "peak": peak_hbm, "unit": "GB/s", "frac": cpl_gbs / peak_hbm,
+                     "peak_kind": peak_kind, "traffic": traffic, "algorithmic_bytes": cpl_bytes},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": launches_per_product * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "build_s": build_s, "upload_s": res["upload_s"],
+    }
+    if res_fp64 is not None:
+        ms64 = float(np.mean(res_fp64["step_ms"]))
+        b64 = 8 * (mat_entries + vec_elems)
+        line["fp64"] = {"ms_per_step": ms64, "GB/s": b64 / (ms64 * 1e-3) / 1e9,
+                        "gflops": flops / (ms64 * 1e-3) / 1e9,
+                        "phases_ms": dict(zip(h2.PHASES, [float(v) for v in res_fp64["phase_ms"]]))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * h2.h -- C ABI of libh2, an H^2-matrix library for one GB300 GPU (sm_103a).
+ *
+ * The operator is the H^2 representation of Zampini et al., "H2Opus: a distributed-
+ * memory multi-GPU software package for non-local operators" (arXiv 2109.05451):
+ *
+ *     A_H2 = A_de + <U, S, V^T>                                      (Sec. 2.1)
+ *
+ * with dense m x m blocks A_de at the finest level, k x k coupling blocks S^l_ts on
+ * every level, leaf bases U = V (m x k) and k x k interlevel transfers E = F. The
+ * product y = A_H2 x runs the three phases of Sec. 3: upsweep xhat = V^T x (Sec. 3.1,
+ * Alg 1), tree multiply yhat^l = S^l xhat^l on every level (Sec. 3.2, Alg 4), downsweep
+ * y = U yhat (Sec. 3.3, Alg 6), plus the dense block-sparse product A_de x (Sec. 3).
+ *
+ * Construction (Sec. 2.2, Sec. 6.1, Sec. 6.3-6.4): a k-d tree with leaf size m, the
+ * geometric admissibility condition eta |C_t - C_s| >= (D_t + D_s)/2 on cluster
+ * bounding boxes, tensor Chebyshev interpolation (p points per dimension, rank
+ * k = p^dim) for bases, transfers and couplings, and direct kernel evaluation for the
+ * dense blocks. The tie and rounding rules that the paper leaves open are fixed as:
+ *   - depth q = smallest q >= 0 with n <= m 2^q; all leaves are on level q;
+ *   - split dimension = largest bounding-box extent (lowest dimension on ties); points
+ *     ordered by (coordinate, original index); left child = first floor(size/2);
+ *   - admissibility evaluated in FP64 as eta*sqrt(sum_d (c_t,d-c_s,d)^2) >= 0.5*(D_t+D_s)
+ *     with c = (lo+hi)/2, D = |hi-lo|; equality is admissible; same-level pairs only;
+ *   - first-kind Chebyshev points, box extents clamped below at 1e-12 x root diagonal;
+ *     multi-index nu = j_0 + p j_1 + p^2 j_2.
+ *
+ * Conventions for every call:
+ *   - Every function returns an h2_status (0 = H2_OK); no exception crosses the ABI.
+ *   - Device calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream). Launch errors are returned at once; a
+ *     fault during execution surfaces at a later call or synchronisation as H2_ECUDA.
+ *   - Multivectors are n x nv, column-major, leading dimension n, in the caller's point
+ *     order. Element type: double for H2_FP64, float for H2_FP32 and H2_BF16X2.
+ *   - Inputs are copied at h2_build; device X, Y, b, x stay owned by the caller; the
+ *     handle owns its host operator and its device copy until h2_destroy.
+ *   - One handle may be used by one stream at a time through h2_matvec (its internal
+ *     workspace is shared); use h2_matvec_ws with separate workspaces for concurrent
+ *     products on one handle.
+ */
+#ifndef H2_H
+#define H2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct h2_op *h2_handle; /* opaque, owned by libh2 */
+
+typedef enum {
+    H2_OK = 0,
+    H2_EINVAL = -1,   /* bad argument (null pointer, size out of range, wrong state) */
+    H2_ENOMEM = -2,   /* host or device allocation failed */
+    H2_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    H2_ETIMEOUT = -4, /* a bounded device-side wait ran out */
+    H2_ESTATE = -5,   /* call not valid in the handle's state (e.g. no device copy) */
+    H2_ENOTCONV = 1   /* iterative solve stopped at maxit without reaching tol */
+} h2_status;
+
+typedef enum {
+    H2_K_EXP = 0,   /* exp(-r / a) */
+    H2_K_GAUSS = 1, /* exp(-r^2 / a) */
+    H2_K_IMQ = 2,   /* (r^2 + a)^(-b) */
+    H2_K_POLY = 3   /* prod_d (1 + x_d y_d)^deg (reproduced exactly when deg < p) */
+} h2_kernel_kind;
+
+typedef struct {
+    h2_kernel_kind kind;
+    double a, b;
+    int deg;
+} h2_kernel;
+
+typedef enum {
+    H2_FP64 = 0,  /* entries and arithmetic in double */
+    H2_FP32 = 1,  /* entries and arithmetic in float */
+    H2_BF16X2 = 2 /* entries as bf16 hi + bf16 lo pairs, FP32 accumulation */
+} h2_prec;
+
+#define H2_MAX_LEVELS 32
+
+typedef struct {
+    int64_t n;                  /* number of points */
+    int dim;                    /* 1..3 */
+    int depth;                  /* leaf level q (root = level 0) */
+    int rank;                   /* k = cheb_order^dim */
+    int leaf_size;              /* m */
+    int cheb_order;             /* p */
+    double eta;
+    int64_t n_nodes;            /* 2^(q+1) - 1 clusters, heap numbered 1..n_nodes */
+    int64_t n_leaves;           /* 2^q */
+    int64_t n_coupling;         /* coupling blocks over all levels */
+    int64_t n_dense;            /* dense blocks (leaf level) */
+    int64_t coupling_per_level[H2_MAX_LEVELS];
+    int32_t max_coupling_per_row; /* sparsity constant C_sp over all levels */
+    int32_t max_dense_per_row;
+    int64_t coupling_entries;   /* n_coupling * k * k */
+    int64_t dense_entries;      /* sum over dense blocks of |t| * |s| */
+    int64_t basis_entries;      /* n * k (leaf bases) */
+    int64_t transfer_entries;   /* (n_nodes - 1) * k * k */
+    int uploaded_prec;          /* h2_prec of the device copy, or -1 */
+    size_t device_bytes;        /* bytes held on the device by the handle */
+} h2_info;
+
+/* Build the H^2 operator on the host in FP64 (Sec. 2.2, 6.1, 6.3): k-d tree, admissible
+ * partition, Chebyshev leaf bases and transfers. Coupling and dense entries are defined
+ * by (kernel, cluster Chebyshev points, points) and are materialised on the device by
+ * h2_upload, as each GPU populates its own blocks in Sec. 2.2.
+ *   points: host, n x dim row-major, copied. n >= 1, 1 <= dim <= 3, leaf_size >= 2,
+ *   1 <= cheb_order with cheb_order^dim <= 64, eta >= 0, n < 2^31.
+ *   out: receives the handle. Errors: H2_EINVAL, H2_ENOMEM. Host only: no CUDA call. */
+int h2_build(const double *points, int64_t n, int dim, h2_kernel kernel, int leaf_size,
+             int cheb_order, double eta, h2_handle *out);
+
+/* Copy the operator to the current CUDA device in precision prec, generating every
+ * coupling block S_ts[nu][mu] = kappa(xi^t_nu, xi^s_mu) and dense block kappa(x_i, x_j)
+ * in FP64 on the device and rounding once to prec. Replaces an earlier device copy.
+ * Synchronises the stream before returning. Errors: H2_EINVAL, H2_ENOMEM, H2_ECUDA. */
+int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream);
+
+/* Bytes of device workspace one product with nv vectors needs (tree vectors xhat, yhat,
+ * the permuted input and the dense partial result). 0 if h is NULL or not uploaded. */
+size_t h2_workspace_bytes(h2_handle h, int nv);
+
+/* Y = alpha * A_H2 * X + beta * Y (Sec. 3: upsweep, tree multiply, downsweep, dense).
+ *   X, Y: device, n x nv column-major, ld = n, caller's point order; element type double
+ *   for H2_FP64, float otherwise. X and Y must not overlap. When beta == 0, Y is not
+ *   read (NaN in Y is ignored). nv >= 1. Uses a workspace owned by the handle, allocated
+ *   (synchronously) on first use or when nv grows. Errors: H2_EINVAL, H2_ESTATE (no
+ *   device copy), H2_ENOMEM, H2_ECUDA. */
+int h2_matvec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta,
+              void *cuda_stream);
+
+/* As h2_matvec, with a caller-owned device workspace of ws_bytes >= h2_workspace_bytes
+ * (h, nv), 256-byte aligned. Products on one handle with distinct workspaces may run
+ * concurrently on different streams. Allocates nothing. */
+int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta,
+                 void *workspace, size_t ws_bytes, void *cuda_stream);
+
+/* Unpreconditioned conjugate gradients for (A_H2 + sigma2 I) x = b (the Krylov solve of
+ * Sec. 6.4, without its multigrid preconditioner). The products run in the uploaded
+ * precision; Krylov vectors, dot products and updates are FP64 on the device.
+ *   b: device, n doubles; x: device, n doubles, holds x0 on entry and the solution on
+ *   return. Stops when the recursive residual |r|/|b| < tol or after maxit iterations.
+ *   iters (host, may be NULL): iterations done. true_relres (host, may be NULL):
+ *   |b - (A + sigma2 I) x| / |b| recomputed with one more product. Synchronises the
+ *   stream. Returns H2_OK, H2_ENOTCONV (maxit reached) or an error. */
+int h2_cg_solve(h2_handle h, double sigma2, const double *b, double *x, double tol, int maxit,
+                int *iters, double *true_relres, void *cuda_stream);
+
+/* Sizes and counts of the operator. Host only. */
+int h2_get_info(h2_handle h, h2_info *info);
+
+/* Tree-order position -> caller index permutation (host array of n int64). */
+int h2_get_perm(h2_handle h, int64_t *perm);
+
+/* Coupling partition as block-row CSR over heap-numbered clusters (rows 1..n_nodes,
+ * level-ordered): rowptr (host, n_nodes + 2 int64, row t spans [rowptr[t], rowptr[t+1]))
+ * and col (host, n_coupling int32 heap indices, ascending within a row). */
+int h2_get_coupling_csr(h2_handle h, int64_t *rowptr, int32_t *col);
+
+/* Dense partition as CSR over leaves (0-based leaf index = heap index - 2^q): rowptr
+ * (n_leaves + 1 int64) and col (n_dense int32 leaf indices, ascending within a row). */
+int h2_get_dense_csr(h2_handle h, int64_t *rowptr, int32_t *col);
+
+/* FP64 host copies of the leaf bases (n x k row-major, rows in tree order) and the
+ * transfers ((n_nodes + 1) x k x k; E_c[mu][nu] at c*k*k + mu*k + nu, rows 0 and 1
+ * unused). Either pointer may be NULL. */
+int h2_get_bases(h2_handle h, double *U, double *E);
+
+/* Instrumentation (no counterpart in the paper). With timing on, every product records
+ * a CUDA event pair around each of its phases on the stream that runs the phase.
+ * h2_get_timing waits for those events and returns, per phase, the summed milliseconds
+ * and the number of kernel launches since the previous read, then resets the sums.
+ * Phases: 0 upsweep (leaf projection + transfers, Alg 1), 1 tree multiply (coupling
+ * blocks of all levels, Alg 4), 2 dense near field, 3 downsweep + leaf expansion +
+ * epilogue (Alg 6). phase_ms and phase_launches: host arrays of H2_NPHASES entries (either
+ * may be NULL); products (may be NULL): products timed. Counting launches is always on;
+ * timing adds event records to the stream and is off by default. */
+#define H2_NPHASES 4
+int h2_set_timing(h2_handle h, int enable);
+int h2_get_timing(h2_handle h, double *phase_ms, int64_t *phase_launches, int64_t *products);
+
+/* Free the host operator, its device copy and its workspace. NULL is accepted. */
+int h2_destroy(h2_handle h);
+
+/* Static description of a status code. */
+const char *h2_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2_H */

@@ -1,0 +1,280 @@
+"""paper_2109_05451_gb300 -- H^2 matrix-vector product on one GB300 GPU.
+
+A thin ctypes binding over ``libh2.so`` (``include/h2.h``): functions with the same
+names as the C ABI, plus a small ``H2Operator`` convenience class. Arguments are
+marshalled only; every step of the product runs in the library's CUDA kernels. Device
+buffers are torch tensors (their ``data_ptr()``), streams are torch streams.
+
+There is no CPU fallback: importing works without a GPU (the host build and the
+structure queries are host code), but every device call raises if the library or the
+GPU is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ETIMEOUT, H2_ESTATE, H2_ENOTCONV = 0, -1, -2, -3, -4, -5, 1
+H2_FP64, H2_FP32, H2_BF16X2 = 0, 1, 2
+H2_K_EXP, H2_K_GAUSS, H2_K_IMQ, H2_K_POLY = 0, 1, 2, 3
+H2_MAX_LEVELS = 32
+KERNELS = {"exp": H2_K_EXP, "gauss": H2_K_GAUSS, "imq": H2_K_IMQ, "poly": H2_K_POLY}
+PRECISIONS = {"fp64": H2_FP64, "fp32": H2_FP32, "bf16x2": H2_BF16X2}
+
+
+class H2Error(RuntimeError):
+    def __init__(self, status: int, call: str):
+        super().__init__(f"{call}: {h2_status_str(status)} ({status})")
+        self.status = status
+
+
+class h2_kernel(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.c_double), ("b", C.c_double), ("deg", C.c_int)]
+
+
+class h2_info(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("dim", C.c_int), ("depth", C.c_int), ("rank", C.c_int), ("leaf_size", C.c_int),
+        ("cheb_order", C.c_int), ("eta", C.c_double), ("n_nodes", C.c_int64), ("n_leaves", C.c_int64),
+        ("n_coupling", C.c_int64), ("n_dense", C.c_int64), ("coupling_per_level", C.c_int64 * H2_MAX_LEVELS),
+        ("max_coupling_per_row", C.c_int32), ("max_dense_per_row", C.c_int32), ("coupling_entries", C.c_int64),
+        ("dense_entries", C.c_int64), ("basis_entries", C.c_int64), ("transfer_entries", C.c_int64),
+        ("uploaded_prec", C.c_int), ("device_bytes", C.c_size_t),
+    ]
+
+
+# name -> (restype, argtypes); every symbol declared in include/h2.h
+_P, _I64, _I, _D, _SZ = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_size_t
+SIGNATURES = {
+    "h2_build": (_I, [_P, _I64, _I, h2_kernel, _I, _I, _D, C.POINTER(_P)]),
+    "h2_upload": (_I, [_P, _I, _P]),
+    "h2_workspace_bytes": (_SZ, [_P, _I]),
+    "h2_matvec": (_I, [_P, _P, _P, _I, _D, _D, _P]),
+    "h2_matvec_ws": (_I, [_P, _P, _P, _I, _D, _D, _P, _SZ, _P]),
+    "h2_cg_solve": (_I, [_P, _D, _P, _P, _D, _I, C.POINTER(_I), C.POINTER(_D), _P]),
+    "h2_get_info": (_I, [_P, C.POINTER(h2_info)]),
+    "h2_get_perm": (_I, [_P, _P]),
+    "h2_get_coupling_csr": (_I, [_P, _P, _P]),
+    "h2_get_dense_csr": (_I, [_P, _P, _P]),
+    "h2_get_bases": (_I, [_P, _P, _P]),
+    "h2_set_timing": (_I, [_P, _I]),
+    "h2_get_timing": (_I, [_P, _P, _P, _P]),
+    "h2_destroy": (_I, [_P]),
+    "h2_status_str": (C.c_char_p, [_I]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libh2.so (building it if missing or stale); raises if that is impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libh2.so not built ({path}); run paper_2109_05451_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, call: str, allow=(H2_OK,)):
+    if rc not in allow:
+        raise H2Error(rc, call)
+    return rc
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- C ABI, same names
+
+def h2_status_str(status: int) -> str:
+    return load().h2_status_str(int(status)).decode()
+
+
+def h2_build(points, kernel, leaf_size: int, cheb_order: int, eta: float) -> int:
+    """Build on the host; returns the opaque handle (an integer address)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    n, dim = pts.shape
+    name, a, b, deg = kernel
+    ker = h2_kernel(KERNELS[name], float(a), float(b), int(deg))
+    h = C.c_void_p()
+    _check(load().h2_build(_np_ptr(pts), n, dim, ker, int(leaf_size), int(cheb_order), float(eta), C.byref(h)),
+           "h2_build")
+    return h.value
+
+
+def h2_upload(h: int, prec, stream=None) -> None:
+    prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    _check(load().h2_upload(h, prec, _stream_ptr(stream)), "h2_upload")
+
+
+def h2_workspace_bytes(h: int, nv: int) -> int:
+    return int(load().h2_workspace_bytes(h, int(nv)))
+
+
+def h2_matvec(h: int, X, Y, nv: int, alpha: float = 1.0, beta: float = 0.0, stream=None) -> None:
+    """X, Y: device tensors (n x nv column-major, i.e. shape (nv, n) contiguous or a
+    Fortran-ordered (n, nv) view); pointers are passed through unchanged."""
+    _check(load().h2_matvec(h, X.data_ptr(), Y.data_ptr(), int(nv), float(alpha), float(beta),
+                            _stream_ptr(stream)), "h2_matvec")
+
+
+def h2_matvec_ws(h: int, X, Y, nv: int, alpha: float, beta: float, workspace, ws_bytes: int, stream=None) -> None:
+    _check(load().h2_matvec_ws(h, X.data_ptr(), Y.data_ptr(), int(nv), float(alpha), float(beta),
+                               workspace.data_ptr(), int(ws_bytes), _stream_ptr(stream)), "h2_matvec_ws")
+
+
+def h2_cg_solve(h: int, sigma2: float, b, x, tol: float, maxit: int, stream=None):
+    """Returns (status, iterations, true relative residual); status is H2_OK or H2_ENOTCONV."""
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    rc = load().h2_cg_solve(h, float(sigma2), b.data_ptr(), x.data_ptr(), float(tol), int(maxit), C.byref(it),
+                            C.byref(rr), _stream_ptr(stream))
+    _check(rc, "h2_cg_solve", allow=(H2_OK, H2_ENOTCONV))
+    return rc, it.value, rr.value
+
+
+def h2_get_info(h: int) -> h2_info:
+    info = h2_info()
+    _check(load().h2_get_info(h, C.byref(info)), "h2_get_info")
+    return info
+
+
+def h2_get_perm(h: int) -> np.ndarray:
+    info = h2_get_info(h)
+    out = np.empty(info.n, dtype=np.int64)
+    _check(load().h2_get_perm(h, _np_ptr(out)), "h2_get_perm")
+    return out
+
+
+def h2_get_coupling_csr(h: int):
+    info = h2_get_info(h)
+    rowptr = np.empty(info.n_nodes + 2, dtype=np.int64)
+    col = np.empty(max(1, info.n_coupling), dtype=np.int32)
+    _check(load().h2_get_coupling_csr(h, _np_ptr(rowptr), _np_ptr(col)), "h2_get_coupling_csr")
+    return rowptr, col[:info.n_coupling]
+
+
+def h2_get_dense_csr(h: int):
+    info = h2_get_info(h)
+    rowptr = np.empty(info.n_leaves + 1, dtype=np.int64)
+    col = np.empty(max(1, info.n_dense), dtype=np.int32)
+    _check(load().h2_get_dense_csr(h, _np_ptr(rowptr), _np_ptr(col)), "h2_get_dense_csr")
+    return rowptr, col[:info.n_dense]
+
+
+def h2_get_bases(h: int):
+    info = h2_get_info(h)
+    U = np.empty((info.n, info.rank))
+    E = np.empty((info.n_nodes + 1, info.rank, info.rank))
+    _check(load().h2_get_bases(h, _np_ptr(U), _np_ptr(E)), "h2_get_bases")
+    return U, E
+
+
+H2_NPHASES = 4
+PHASES = ("upsweep", "coupling", "dense", "downsweep")
+
+
+def h2_set_timing(h: int, enable: bool) -> None:
+    _check(load().h2_set_timing(h, int(bool(enable))), "h2_set_timing")
+
+
+def h2_get_timing(h: int):
+    """Waits for the recorded phase events; returns (ms per phase, launches per phase, products)."""
+    ms = np.zeros(H2_NPHASES)
+    launches = np.zeros(H2_NPHASES, dtype=np.int64)
+    prods = np.zeros(1, dtype=np.int64)
+    _check(load().h2_get_timing(h, _np_ptr(ms), _np_ptr(launches), _np_ptr(prods)), "h2_get_timing")
+    return ms, launches, int(prods[0])
+
+
+def h2_destroy(h: int) -> None:
+    if h:
+        _check(load().h2_destroy(h), "h2_destroy")
+
+
+# ---------------------------------------------------------------- convenience class
+
+class H2Operator:
+    """Owns one handle. ``matvec`` takes torch tensors of shape (n, nv) in column-major
+    (Fortran) layout or (n,) vectors; the dtype must match the uploaded precision."""
+
+    def __init__(self, points, kernel, leaf_size: int, cheb_order: int, eta: float):
+        self.handle = h2_build(points, kernel, leaf_size, cheb_order, eta)
+        self.info = h2_get_info(self.handle)
+        self.n = int(self.info.n)
+        self.prec = None
+
+    def upload(self, prec="fp32", stream=None):
+        h2_upload(self.handle, prec, stream)
+        self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.info = h2_get_info(self.handle)
+        return self
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.prec == H2_FP64 else torch.float32
+
+    def new_vectors(self, nv: int, fill=None):
+        """A device (n, nv) column-major tensor of the operator's dtype."""
+        import torch
+        t = torch.empty((nv, self.n), dtype=self.dtype, device="cuda")
+        if fill is not None:
+            t.fill_(fill)
+        return t.t()
+
+    def matvec(self, X, Y=None, alpha: float = 1.0, beta: float = 0.0, stream=None):
+        nv = 1 if X.dim() == 1 else X.shape[1]
+        _check_colmajor(X, self.n, nv, self.dtype)
+        if Y is None:
+            Y = self.new_vectors(nv).squeeze(1) if X.dim() == 1 else self.new_vectors(nv)
+            beta = 0.0
+        _check_colmajor(Y, self.n, nv, self.dtype)
+        h2_matvec(self.handle, X, Y, nv, alpha, beta, stream)
+        return Y
+
+    def close(self):
+        if getattr(self, "handle", None):
+            h2_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_colmajor(t, n: int, nv: int, dtype):
+    if not t.is_cuda or t.dtype != dtype:
+        raise ValueError(f"expected a CUDA tensor of dtype {dtype}")
+    if t.dim() == 1:
+        ok = t.shape[0] == n and nv == 1 and t.stride(0) == 1
+    else:
+        ok = tuple(t.shape) == (n, nv) and t.stride(0) == 1 and (nv == 1 or t.stride(1) == n)
+    if not ok:
+        raise ValueError("expected an (n, nv) column-major tensor with leading dimension n")

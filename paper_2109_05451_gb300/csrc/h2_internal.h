@@ -1,0 +1,47 @@
+// h2_internal.h -- host-side operator state shared by the host build (h2_host.cpp) and
+// the device upload / matvec (h2_device.cu). Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/h2.h"
+
+struct h2_device;  // device copy, defined in h2_device.cu
+
+struct h2_op {
+    // parameters
+    int64_t n = 0;
+    int dim = 0, m = 0, p = 0, k = 0, q = 0;
+    double eta = 0;
+    h2_kernel ker{};
+
+    // geometry (FP64, host)
+    std::vector<double> pts;         // n * dim, caller order
+    std::vector<int64_t> perm;       // tree position -> caller index
+    int64_t nnodes = 0;              // heap nodes 1 .. nnodes
+    std::vector<int64_t> lo, hi;     // [nnodes + 1] tree-order ranges
+    std::vector<double> bmin, bmax;  // [(nnodes + 1) * dim] tight boxes
+    std::vector<double> cheb;        // [(nnodes + 1) * dim * p] 1-D Chebyshev points
+
+    // bases (FP64, host)
+    std::vector<double> U;           // n * k, rows in tree order
+    std::vector<double> E;           // (nnodes + 1) * k * k, E_c[mu][nu]
+
+    // partition
+    std::vector<int64_t> cpl_rowptr; // nnodes + 2, rows = heap indices (level-ordered)
+    std::vector<int32_t> cpl_col;    // heap index of the column cluster
+    std::vector<int64_t> dns_rowptr; // nleaves + 1
+    std::vector<int32_t> dns_col;    // leaf index of the column cluster
+
+    int64_t nleaves() const { return int64_t(1) << q; }
+    int64_t first_leaf() const { return int64_t(1) << q; }
+
+    h2_device *dev = nullptr;
+};
+
+// h2_host.cpp
+int h2_host_build(h2_op *op, const double *points, int64_t n, int dim, h2_kernel kernel,
+                  int leaf_size, int cheb_order, double eta);
+// h2_device.cu
+void h2_device_free(h2_op *op);

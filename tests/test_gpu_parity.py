@@ -1,0 +1,146 @@
+"""GPU parity: libh2's CUDA product against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (relative l2 over the compared entries): 1e-12 for FP64, 1e-5 for FP32.
+Small cases compare every output entry; the full-size 2^20 grid compares the output
+rows of sampled leaves that the oracle computes exactly (its upsweep is complete and
+its tree multiply / downsweep follow each sampled leaf's ancestors).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2109_05451_gb300 as h2  # noqa: E402
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def to_dev(X, prec):
+    X = np.asfortranarray(X)
+    return torch.from_numpy(np.ascontiguousarray(X.T)).to(device="cuda", dtype=DT[prec]).t()
+
+
+def to_host(Y):
+    return Y.t().contiguous().cpu().double().numpy().T
+
+
+def gpu_matvec(op, X, prec, alpha=1.0, beta=0.0, Y0=None):
+    Xd = to_dev(X, prec)
+    Yd = to_dev(Y0, prec) if Y0 is not None else op.new_vectors(X.shape[1], fill=float("nan"))
+    op.matvec(Xd, Yd, alpha=alpha, beta=beta)
+    torch.cuda.synchronize()
+    return to_host(Yd)
+
+
+CASES = {
+    "grid64_exp": lambda: (si.grid_2d(64), ("exp", 0.1, 0, 0), 64, 4, 0.9),
+    "grid37_gauss_k25": lambda: (si.grid_2d(37), ("gauss", 0.01, 0, 0), 32, 5, 0.7),
+    "cloud3d_k64": lambda: (si.uniform_cloud(6000, 3, 0), ("exp", 0.2, 0, 0), 64, 4, 0.7),
+    "cloud3d_k27_ragged": lambda: (si.uniform_cloud(3001, 3, 5), ("exp", 0.2, 0, 0), 40, 3, 0.7),
+    "cloud1d_imq": lambda: (si.uniform_cloud(999, 1, 4), ("imq", 1e-4, 1.5, 0), 16, 6, 1.0),
+    "poly_exact": lambda: (si.uniform_cloud(2000, 2, 6), ("poly", 0, 0, 3), 32, 4, 0.7),
+    "tiny_single_leaf": lambda: (si.uniform_cloud(7, 2, 1), ("exp", 0.1, 0, 0), 64, 4, 0.9),
+    "all_dense": lambda: (si.grid_2d(20), ("exp", 0.1, 0, 0), 16, 4, 1e-9),
+}
+
+
+@pytest.fixture(scope="module")
+def built():
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            pts, ker, m, p, eta = CASES[name]()
+            cache[name] = (pts, ker, oracle.OracleH2(pts, ker, m, p, eta), h2.H2Operator(pts, ker, m, p, eta))
+        return cache[name]
+    return get
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_matvec_matches_oracle(built, name, prec):
+    pts, ker, orc, op = built(name)
+    op.upload(prec)
+    X = si.gaussian_vectors(len(pts), 1, 1)
+    ref = orc.matvec(X)
+    got = gpu_matvec(op, X, prec)
+    assert np.all(np.isfinite(got))
+    assert relerr(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_alpha_beta_and_nan_output(built, prec):
+    pts, ker, orc, op = built("cloud3d_k64")
+    op.upload(prec)
+    X = si.gaussian_vectors(len(pts), 2, 1)
+    Y0 = si.gaussian_vectors(len(pts), 2, 2)
+    assert relerr(gpu_matvec(op, X, prec, 0.75, -1.25, Y0), orc.matvec(X, 0.75, -1.25, Y0)) <= TOL[prec]
+    # beta = 0: Y (NaN here) is not read
+    got = gpu_matvec(op, X, prec, 2.0, 0.0)
+    assert np.all(np.isfinite(got)) and relerr(got, orc.matvec(X, 2.0)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_multi_rhs_columns_and_repeatability(built, prec):
+    pts, ker, orc, op = built("grid37_gauss_k25")
+    op.upload(prec)
+    X = si.gaussian_vectors(len(pts), 5, 3)
+    Y = gpu_matvec(op, X, prec)
+    assert relerr(Y, orc.matvec(X)) <= TOL[prec]
+    for v in (0, 3):
+        Yv = gpu_matvec(op, X[:, v:v + 1], prec)
+        assert relerr(Yv[:, 0], Y[:, v]) <= 10 * np.finfo(np.float32 if prec == "fp32" else np.float64).eps
+    assert np.array_equal(gpu_matvec(op, X, prec), Y)  # bitwise repeatable (no atomics)
+
+
+def test_workspace_entry_point(built):
+    pts, ker, orc, op = built("grid64_exp")
+    op.upload("fp64")
+    nv = 2
+    X = si.gaussian_vectors(len(pts), nv, 7)
+    Xd = to_dev(X, "fp64")
+    Yd = op.new_vectors(nv, fill=0.0)
+    nbytes = h2.h2_workspace_bytes(op.handle, nv)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    with pytest.raises(h2.H2Error):
+        h2.h2_matvec_ws(op.handle, Xd, Yd, nv, 1.0, 0.0, ws, nbytes - 1)
+    h2.h2_matvec_ws(op.handle, Xd, Yd, nv, 1.0, 0.0, ws, nbytes)
+    torch.cuda.synchronize()
+    assert relerr(to_host(Yd), orc.matvec(X)) <= TOL["fp64"]
+
+
+@pytest.fixture(scope="module")
+def grid1024():
+    w = si.GRID1024_GAUSS
+    pts = w.make_points()
+    orc = oracle.OracleH2(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    op = h2.H2Operator(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    X = w.make_x(len(pts))
+    rng = np.random.default_rng(123)
+    first = 2 ** orc.depth
+    leaves = np.unique(np.concatenate([[first, first + 1, orc.nnodes],
+                                       rng.integers(first, orc.nnodes + 1, 29)]))
+    rows, ref = orc.matvec_leaves(X, leaves)
+    return w, op, X, rows, ref, orc
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_full_size_grid1024_sampled_leaves(grid1024, prec):
+    """N = 2^20 Gaussian grid, rank 64, eta 0.7, nv = 1 -- the benchmarked workload."""
+    w, op, X, rows, ref, orc = grid1024
+    info = h2.h2_get_info(op.handle)
+    assert info.depth == orc.depth == 14 and info.rank == 64
+    op.upload(prec)
+    got = gpu_matvec(op, X, prec)
+    assert np.all(np.isfinite(got))
+    assert relerr(got[rows], ref) <= TOL[prec]
+    op.upload("fp32")  # leave the cheaper copy resident for later tests
