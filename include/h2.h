@@ -174,9 +174,10 @@ int h2_get_bases(h2_handle h, double *U, double *E);
  * a CUDA event pair around each of its phases on the stream that runs the phase.
  * h2_get_timing waits for those events and returns, per phase, the summed milliseconds
  * and the number of kernel launches since the previous read, then resets the sums.
- * Phases: 0 upsweep (leaf projection + transfers, Alg 1), 1 tree multiply (coupling
- * blocks of all levels, Alg 4), 2 dense near field, 3 downsweep + leaf expansion +
- * epilogue (Alg 6). phase_ms and phase_launches: host arrays of H2_NPHASES entries (either
+ * Phases: 0 gather + upsweep of the lowest levels (Alg 1), 1 streaming product of the
+ * coupling rows of those levels (Alg 4) and of the dense rows (the dominant kernel),
+ * 2 the top levels on the side stream (upsweep, coupling rows, downsweep), 3 downsweep of
+ * the lowest levels + leaf expansion + epilogue (Alg 6). phase_ms and phase_launches: host arrays of H2_NPHASES entries (either
  * may be NULL); products (may be NULL): products timed. Counting launches is always on;
  * timing adds event records to the stream and is off by default. */
 #define H2_NPHASES 4

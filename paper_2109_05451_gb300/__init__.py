@@ -195,7 +195,7 @@ def h2_get_bases(h: int):
 
 
 H2_NPHASES = 4
-PHASES = ("upsweep", "coupling", "dense", "downsweep")
+PHASES = ("upsweep", "stream", "top", "downsweep")
 
 
 def h2_set_timing(h: int, enable: bool) -> None:

@@ -1,11 +1,18 @@
 // h2_device.cu -- device copy of the H^2 operator, the product and the C ABI entry points.
 //
-// h2_upload materialises the operator in HBM: leaf bases and transfers are copied from
-// the host build; coupling blocks S_ts = kappa(xi_t, xi_s) and dense blocks are generated
-// on the device in FP64 and rounded once to the requested precision (each GPU populates
-// its own blocks, Sec. 2.2). h2_matvec runs Sec. 3 as: leaf projection -> upsweep levels
-// (Alg 1) -> all-level coupling product (Alg 4) -> downsweep levels (Alg 6) -> leaf
-// expansion fused with the dense near field result and the alpha/beta epilogue.
+// h2_upload materialises the operator in HBM: leaf bases and transfers come from the host
+// build (plus transposed copies for the downsweep), coupling blocks S_ts = kappa(xi_t, xi_s)
+// and dense blocks are generated on the device in FP64 and rounded once to the requested
+// precision (each GPU populates its own blocks, Sec. 2.2). It also builds the flat list of
+// tile descriptors that the streaming kernel walks, split over persistent CTAs by bytes.
+//
+// h2_matvec runs the three phases of Sec. 3 plus the dense product on two streams:
+//   stream A: gather -> bottom upsweep (leaves + lowest L levels, Alg 1) -> streaming
+//             product of every coupling row of the lower levels and every dense row
+//             (Alg 4 + A_de x) -> [join] -> bottom downsweep + leaf expansion + epilogue (Alg 6)
+//   stream B: [after the bottom upsweep] top upsweep levels -> coupling rows of the top
+//             levels -> top downsweep levels -> [join]
+// Stream B's latency-bound small levels run underneath stream A's bandwidth-bound stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,35 +23,45 @@
 
 #include "h2_internal.h"
 #include "h2_kernels.cuh"
+#include "h2_stream.cuh"
 
 namespace {
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+inline int round4(int x) { return (x + 3) / 4 * 4; }
+
+// Column chunk of one product pass (the streaming kernels keep nv <= 4 accumulators).
+constexpr int kChunk = 4;
+constexpr int kMaxLeaf = 128;
 
 }  // namespace
 
 struct h2_device {
     int device = -1;
+    int num_sms = 0;
     h2_prec prec = H2_FP64;
     size_t esize = 8;
     void *arena = nullptr;  // one allocation for the whole operator
     size_t arena_bytes = 0;
-    // views into the arena
-    int32_t *perm = nullptr;       // n
-    int32_t *leaf_lo = nullptr;    // nleaves + 1
-    void *U = nullptr;             // n * k
-    void *E = nullptr;             // (nnodes + 1) * k * k
-    int64_t *cpl_rowptr = nullptr; // nnodes + 2
-    int32_t *cpl_col = nullptr;    // ncpl
-    int32_t *cpl_rows = nullptr;   // non-empty block rows (heap indices)
-    int64_t n_cpl_rows = 0;
-    void *S = nullptr;             // ncpl * k * k
-    int64_t *dns_rowptr = nullptr; // nleaves + 1
-    int32_t *dns_col = nullptr;    // ndns
-    int64_t *dns_off = nullptr;    // ndns + 1
-    void *D = nullptr;
+    // layout
+    int kx = 0, mp = 0, L = 0, Lb = 0;
+    int64_t kkp = 0;
     int max_leaf_rows = 0;
+    bool root_row = false;  // the root has coupling blocks
+    // views into the arena
+    int32_t *perm = nullptr, *leaf_lo = nullptr;
+    int64_t *cpl_rowptr = nullptr;
+    void *U = nullptr, *Ut = nullptr, *E = nullptr, *Et = nullptr;
+    unsigned char *vals = nullptr;  // coupling blocks, then dense blocks
+    h2s::StreamDesc *desc_bottom = nullptr, *desc_top = nullptr;
+    int64_t *chunks_bottom = nullptr, *chunks_top = nullptr;  // (first << 16) | count
+    int grid_bottom = 0, grid_top = 0;
+    int64_t n_chunks_bottom = 0, n_chunks_top = 0;
+    int *err = nullptr;  // device error flag (a bounded wait ran out)
+    // execution resources
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_up = nullptr, ev_top = nullptr;
     // handle-owned workspace for h2_matvec
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -71,7 +88,6 @@ struct h2_device {
         }
         return e;
     }
-    // Opens a phase on stream st; returns the start event (null when timing is off).
     cudaEvent_t begin(cudaStream_t st)
     {
         if (!timing) return nullptr;
@@ -103,6 +119,9 @@ struct h2_device {
     {
         drain();
         for (auto e : event_pool) cudaEventDestroy(e);
+        if (ev_up) cudaEventDestroy(ev_up);
+        if (ev_top) cudaEventDestroy(ev_top);
+        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -110,21 +129,26 @@ namespace {
 
 struct Workspace {
     void *xt, *yd, *xh, *yh;
+    int *tickets;
 };
 
-size_t ws_layout(const h2_op &op, size_t esize, int nv, Workspace *w, void *base)
+// Workspace: permuted input and dense result ([leaf][v][mp]), coefficient trees xhat and
+// yhat ([node][v][kx]) for one chunk of at most kChunk vectors, and the scheduling tickets.
+size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, void *base)
 {
-    nv = std::min(nv, 32);  // products run in chunks of at most 32 vectors
-    const size_t vec = align_up(size_t(op.n) * nv * esize);
-    const size_t tree = align_up(size_t(op.nnodes + 1) * op.k * nv * esize);
+    nv = std::min(nv, kChunk);
+    const size_t es = dv.esize;
+    const size_t vec = align_up(size_t(op.nleaves()) * nv * dv.mp * es);
+    const size_t tree = align_up(size_t(op.nnodes + 1) * nv * dv.kx * es);
     if (w) {
         char *p = static_cast<char *>(base);
         w->xt = p;
         w->yd = p + vec;
         w->xh = p + 2 * vec;
         w->yh = p + 2 * vec + tree;
+        w->tickets = reinterpret_cast<int *>(p + 2 * vec + 2 * tree);
     }
-    return 2 * vec + 2 * tree;
+    return 2 * vec + 2 * tree + kAlign;
 }
 
 int cuda_status(cudaError_t e)
@@ -134,89 +158,190 @@ int cuda_status(cudaError_t e)
     return H2_ECUDA;
 }
 
-// Vectors are processed in chunks of at most kMaxChunk columns per pass.
-constexpr int kMaxChunk = 32;
-
 template <typename T>
-void raise_smem_limits()
+h2s::Op<T> make_op(const h2_op &op, const h2_device &dv)
 {
-    static bool done = false;  // attributes are per device function; set once per process
-    if (done) return;
-    const int lim = 160 * 1024;
-    cudaFuncSetAttribute(h2k::downsweep_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(h2k::leaf_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(h2k::upsweep_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(h2k::leaf_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    done = true;
+    h2s::Op<T> o;
+    o.n = op.n;
+    o.nleaves = op.nleaves();
+    o.first_leaf = op.first_leaf();
+    o.k = op.k;
+    o.kx = dv.kx;
+    o.mp = dv.mp;
+    o.q = op.q;
+    o.Lb = dv.Lb;
+    o.L = dv.L;
+    o.perm = dv.perm;
+    o.leaf_lo = dv.leaf_lo;
+    o.U = static_cast<const T *>(dv.U);
+    o.Ut = static_cast<const T *>(dv.Ut);
+    o.E = static_cast<const T *>(dv.E);
+    o.Et = static_cast<const T *>(dv.Et);
+    o.vals = dv.vals;
+    return o;
 }
 
-template <typename T>
-int launch_matvec(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
-                  const Workspace &w, cudaStream_t st)
+// Stage sizing for a kernel: as many stages as fit in `budget` bytes of shared memory.
+template <typename T, int NVMAX>
+h2s::Pipe make_pipe(uint32_t tile_bytes, uint32_t x_bytes, int sub_nodes, int kx, bool chunks, size_t budget,
+                    int max_ns)
 {
-    using namespace h2k;
-    raise_smem_limits<T>();
-    const int k = op.k;
-    const int64_t n = op.n, first_leaf = op.first_leaf(), nleaves = op.nleaves();
-    const T *U = static_cast<const T *>(dv.U);
-    const T *E = static_cast<const T *>(dv.E);
-    T *xt = static_cast<T *>(w.xt), *yd = static_cast<T *>(w.yd);
-    T *xh = static_cast<T *>(w.xh), *yh = static_cast<T *>(w.yh);
+    h2s::Pipe p{1, tile_bytes, x_bytes};
+    for (int ns = max_ns; ns >= 1; --ns) {
+        p.ns = ns;
+        if (h2s::smem_bytes<T, NVMAX>(p, sub_nodes, kx, chunks) <= budget) break;
+    }
+    return p;
+}
 
-    // upsweep (Alg 1)
+template <typename T, int NVMAX>
+int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
+                 const Workspace &w, cudaStream_t st)
+{
+    using namespace h2s;
+    const uint32_t es = sizeof(T);
+    const int k = op.k, kx = dv.kx, mp = dv.mp;
+    Op<T> o = make_op<T>(op, dv);
+    Vec<T> v{X, Y, nv, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd), static_cast<T *>(w.xh),
+             static_cast<T *>(w.yh), w.tickets, dv.err};
+    const int sub_nodes = 2 << dv.L;
+    const int64_t nsub = int64_t(1) << dv.Lb;
+
+    // shared-memory plans
+    const uint32_t tile_sub = uint32_t(std::max({size_t(mp) * kx, size_t(k) * kx, size_t(k) * mp}) * es);
+    const uint32_t x_sub = uint32_t(2 * std::max(mp, kx) * NVMAX * es);  // two vector segments per stage
+    const Pipe p_sub = make_pipe<T, NVMAX>(tile_sub, x_sub, sub_nodes, kx, false, 100 * 1024, 8);
+    const size_t sm_sub = smem_bytes<T, NVMAX>(p_sub, sub_nodes, kx, false);
+    const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * k, size_t(dv.max_leaf_rows) * dv.max_leaf_rows) *
+                                         es) + 15) / 16 * 16);
+    const uint32_t x_str = uint32_t(std::max(mp, kx) * NVMAX * es);
+    const Pipe p_bot = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
+    const Pipe p_top = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
+    const size_t sm_bot = smem_bytes<T, NVMAX>(p_bot, 0, kx, true), sm_top = smem_bytes<T, NVMAX>(p_top, 0, kx, true);
+    static bool attr_done = false;  // per template instance
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_up_bottom<T, NVMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_down_bottom<T, NVMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_stream<T, NVMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        // ask for the largest shared-memory carveout, so that the side stream's kernels can
+        // still become resident next to the persistent streaming kernel
+        cudaFuncSetAttribute(k_stream<T, NVMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_up_bottom<T, NVMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_down_bottom<T, NVMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr_done = true;
+    }
+    const int grid_sub = int(std::min<int64_t>(nsub, int64_t(dv.num_sms) * 2));
+
+    // ---- stream A: gather + bottom upsweep
     cudaEvent_t ev = dv.begin(st);
-    leaf_project<T><<<unsigned(nleaves), 64, op.m * sizeof(T), st>>>(X, n, nv, dv.perm, dv.leaf_lo, U, k, first_leaf,
-                                                                      xt, xh);
-    for (int l = op.q; l >= 1; --l) {
-        const int64_t parents = int64_t(1) << (l - 1);
-        upsweep_level<T><<<unsigned(parents), 64, 2 * k * nv * sizeof(T), st>>>(parents, E, xh, k, nv);
+    k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
+    k_up_bottom<T, NVMAX><<<grid_sub, kThreads, sm_sub, st>>>(o, v, p_sub, nsub);
+    dv.end(0, ev, st, 2);
+    const bool top = dv.Lb >= 1;
+    if (top) {
+        cudaEventRecord(dv.ev_up, st);
+        cudaStreamWaitEvent(dv.side, dv.ev_up, 0);
     }
-    dv.end(0, ev, st, 1 + op.q);
-    // tree multiply on all levels (Alg 4)
+    // ---- stream A: coupling rows of the lower levels + dense rows
     ev = dv.begin(st);
-    if (dv.n_cpl_rows > 0)
-        coupling_rows<T><<<unsigned(dv.n_cpl_rows), 128, 128 * sizeof(T), st>>>(
-            dv.cpl_rows, dv.cpl_rowptr, dv.cpl_col, static_cast<const T *>(dv.S), xh, yh, k, nv);
-    dv.end(1, ev, st, dv.n_cpl_rows > 0 ? 1 : 0);
-    // dense near field
+    if (dv.n_chunks_bottom > 0)
+        k_stream<T, NVMAX><<<dv.grid_bottom, kThreads, sm_bot, st>>>(o, v, p_bot, dv.desc_bottom, dv.chunks_bottom,
+                                                                     dv.n_chunks_bottom, 0);
+    dv.end(1, ev, st, dv.n_chunks_bottom > 0 ? 1 : 0);
+    // ---- stream B: top levels
+    if (top) {
+        cudaStream_t sb = dv.side;
+        cudaEvent_t eb = dv.begin(sb);
+        int launches = 0;
+        for (int lev = dv.Lb; lev >= 1; --lev) {
+            const int64_t cnt = int64_t(1) << (lev - 1);
+            k_up_level<T><<<unsigned(std::min<int64_t>(cnt, 4096)), 64, 0, sb>>>(o, v, cnt, cnt);
+            ++launches;
+        }
+        if (dv.n_chunks_top > 0) {
+            k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
+                                                                      dv.n_chunks_top, 1);
+            ++launches;
+        }
+        for (int lev = 1; lev < dv.Lb; ++lev) {
+            const int64_t cnt = int64_t(1) << lev;
+            k_down_level<T><<<unsigned(std::min<int64_t>(cnt, 4096)), 64, 0, sb>>>(o, v, cnt, cnt);
+            ++launches;
+        }
+        dv.end(2, eb, sb, launches);
+        cudaEventRecord(dv.ev_top, sb);
+        cudaStreamWaitEvent(st, dv.ev_top, 0);
+    }
+    // ---- stream A: bottom downsweep + leaf expansion + epilogue
     ev = dv.begin(st);
-    {
-        const int threads = std::max(128, (dv.max_leaf_rows + 31) / 32 * 32);
-        dense_rows<T><<<unsigned(nleaves), threads, threads * sizeof(T), st>>>(
-            dv.dns_rowptr, dv.dns_col, dv.dns_off, static_cast<const T *>(dv.D), dv.leaf_lo, xt, yd, n, nv);
-    }
-    dv.end(2, ev, st, 1);
-    // downsweep (Alg 6)
-    ev = dv.begin(st);
-    for (int l = 1; l <= op.q; ++l) {
-        const int64_t nodes = int64_t(1) << l;
-        const size_t sm = (size_t(k) * (k + 1) + size_t(k) * nv) * sizeof(T);
-        downsweep_level<T><<<unsigned(nodes), 64, sm, st>>>(nodes, E, yh, dv.cpl_rowptr, k, nv, l == 1);
-    }
-    // leaf expansion + dense + epilogue
-    {
-        const bool yh_valid = op.q > 0 || op.cpl_rowptr[2] > op.cpl_rowptr[1];
-        const size_t sm = (64 * size_t(k + 1) + size_t(k) * nv) * sizeof(T);
-        leaf_expand<T><<<unsigned(nleaves), 128, sm, st>>>(U, yh, yd, dv.perm, dv.leaf_lo, first_leaf, k, nv, n,
-                                                           yh_valid, T(alpha), T(beta), Y);
-    }
-    dv.end(3, ev, st, op.q + 1);
+    k_down_bottom<T, NVMAX><<<grid_sub, kThreads, sm_sub, st>>>(o, v, p_sub, nsub);
+    dv.end(3, ev, st, 1);
     return cuda_status(cudaGetLastError());
 }
 
 template <typename T>
+int launch_product(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
+                   const Workspace &w, cudaStream_t st)
+{
+    for (int v0 = 0; v0 < nv; v0 += kChunk) {
+        const int c = std::min(kChunk, nv - v0);
+        const size_t o = size_t(v0) * op.n;
+        const int rc = c == 1 ? launch_chunk<T, 1>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                              : launch_chunk<T, kChunk>(op, dv, X + o, Y + o, c, alpha, beta, w, st);
+        if (rc != H2_OK) return rc;
+    }
+    return H2_OK;
+}
+
+template <typename T>
 int generate_blocks(const h2_op &op, h2_device &dv, const int32_t *d_cpl_row, const int32_t *d_dns_row,
-                    const double *d_cheb, const double *d_pts_tree, cudaStream_t st)
+                    const int32_t *d_dns_col, const int64_t *d_dns_off, const int32_t *d_cpl_col,
+                    const double *d_cheb, const double *d_pts_tree, size_t d_region, cudaStream_t st)
 {
     h2k::KernelFn f{int(op.ker.kind), op.ker.a, op.ker.b, op.ker.deg};
     const int64_t ncpl = int64_t(op.cpl_col.size()), ndns = int64_t(op.dns_col.size());
     if (ncpl > 0)
         h2k::gen_coupling<T><<<unsigned(std::min<int64_t>(ncpl, 1 << 20)), 256, 0, st>>>(
-            static_cast<T *>(dv.S), d_cpl_row, dv.cpl_col, ncpl, d_cheb, op.dim, op.p, op.k, f);
+            reinterpret_cast<T *>(dv.vals), d_cpl_row, d_cpl_col, ncpl, d_cheb, op.dim, op.p, op.k, dv.kkp, f);
     if (ndns > 0)
         h2k::gen_dense<T><<<unsigned(std::min<int64_t>(ndns, 1 << 20)), 256, 0, st>>>(
-            static_cast<T *>(dv.D), dv.dns_off, d_dns_row, dv.dns_col, ndns, dv.leaf_lo, d_pts_tree, op.dim, f);
+            reinterpret_cast<T *>(dv.vals + d_region), d_dns_off, d_dns_row, d_dns_col, ndns, dv.leaf_lo,
+            d_pts_tree, op.dim, f);
     return cuda_status(cudaGetLastError());
+}
+
+// Group a descriptor list (whole block rows, in order) into scheduling chunks of about
+// `target` bytes and at most kChunkDesc descriptors: record = (first << 16) | count.
+// Returns false if a single row has more than kChunkDesc blocks.
+bool make_chunks(const std::vector<h2s::StreamDesc> &d, const std::vector<uint64_t> &bytes, uint64_t target,
+                 std::vector<int64_t> &out)
+{
+    out.clear();
+    size_t first = 0, row_first = 0;
+    uint64_t acc = 0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        acc += bytes[i];
+        if (!(d[i].flags & h2s::kLast)) continue;
+        const size_t row_end = i + 1;
+        if (row_end - row_first > size_t(h2s::kChunkDesc)) return false;
+        if (row_end - first > size_t(h2s::kChunkDesc)) {  // close the chunk before this row
+            out.push_back(int64_t(first) << 16 | int64_t(row_first - first));
+            first = row_first;
+            acc = 0;
+            for (size_t j = row_first; j < row_end; ++j) acc += bytes[j];
+        }
+        if (acc >= target) {
+            out.push_back(int64_t(first) << 16 | int64_t(row_end - first));
+            first = row_end;
+            acc = 0;
+        }
+        row_first = row_end;
+    }
+    if (first < d.size()) out.push_back(int64_t(first) << 16 | int64_t(d.size() - first));
+    return true;
 }
 
 }  // namespace
@@ -229,9 +354,9 @@ void h2_device_free(h2_op *op)
     if (op->dev->device >= 0) cudaSetDevice(op->dev->device);
     if (op->dev->arena) cudaFree(op->dev->arena);
     if (op->dev->ws) cudaFree(op->dev->ws);
-    if (prev >= 0) cudaSetDevice(prev);
     delete op->dev;
     op->dev = nullptr;
+    if (prev >= 0) cudaSetDevice(prev);
 }
 
 extern "C" {
@@ -247,57 +372,126 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     if (!dv) return H2_ENOMEM;
     op.dev = dv;
     cudaGetDevice(&dv->device);
+    cudaDeviceGetAttribute(&dv->num_sms, cudaDevAttrMultiProcessorCount, dv->device);
     dv->prec = prec;
     dv->esize = prec == H2_FP64 ? 8 : 4;
     const size_t es = dv->esize;
     const int k = op.k;
-    const int64_t nleaves = op.nleaves(), ncpl = int64_t(op.cpl_col.size()), ndns = int64_t(op.dns_col.size());
+    const int64_t nleaves = op.nleaves(), first_leaf = op.first_leaf(), ncpl = int64_t(op.cpl_col.size()),
+                  ndns = int64_t(op.dns_col.size());
 
-    // host-side index arrays
-    std::vector<int32_t> perm32(op.n), leaf_lo(nleaves + 1), cpl_rows, cpl_row(ncpl), dns_row(ndns);
-    std::vector<int64_t> dns_off(ndns + 1);
+    // ---- layout constants
+    std::vector<int32_t> perm32(op.n), leaf_lo(nleaves + 1);
     for (int64_t i = 0; i < op.n; ++i) perm32[i] = int32_t(op.perm[i]);
-    for (int64_t t = 0; t < nleaves; ++t) leaf_lo[t] = int32_t(op.lo[op.first_leaf() + t]);
+    for (int64_t t = 0; t < nleaves; ++t) leaf_lo[t] = int32_t(op.lo[first_leaf + t]);
     leaf_lo[nleaves] = int32_t(op.n);
-    dv->max_leaf_rows = 0;
     for (int64_t t = 0; t < nleaves; ++t) dv->max_leaf_rows = std::max(dv->max_leaf_rows, leaf_lo[t + 1] - leaf_lo[t]);
-    for (int64_t t = 1; t <= op.nnodes; ++t) {
-        if (op.cpl_rowptr[t + 1] > op.cpl_rowptr[t]) cpl_rows.push_back(int32_t(t));
-        for (int64_t b = op.cpl_rowptr[t]; b < op.cpl_rowptr[t + 1]; ++b) cpl_row[b] = int32_t(t);
+    if (dv->max_leaf_rows > kMaxLeaf) {
+        h2_device_free(&op);
+        return H2_EINVAL;
     }
-    dv->n_cpl_rows = int64_t(cpl_rows.size());
-    const int64_t blk_align = 32;  // each dense block starts on a 128-byte boundary (FP32)
+    dv->kx = round4(k);
+    dv->mp = round4(dv->max_leaf_rows);
+    dv->kkp = (int64_t(k) * k + 3) / 4 * 4;
+    dv->L = std::min(op.q, 4);
+    dv->Lb = op.q - dv->L;
+    dv->root_row = op.cpl_rowptr[2] > op.cpl_rowptr[1];
+    const int kx = dv->kx, mp = dv->mp;
+
+    // ---- per-block metadata
+    std::vector<int32_t> cpl_row(ncpl), dns_row(ndns);
+    std::vector<int64_t> dns_off(ndns + 1);
+    for (int64_t t = 1; t <= op.nnodes; ++t)
+        for (int64_t b = op.cpl_rowptr[t]; b < op.cpl_rowptr[t + 1]; ++b) cpl_row[b] = int32_t(t);
     dns_off[0] = 0;
     for (int64_t t = 0; t < nleaves; ++t)
         for (int64_t b = op.dns_rowptr[t]; b < op.dns_rowptr[t + 1]; ++b) {
             dns_row[b] = int32_t(t);
             const int64_t s = op.dns_col[b];
             const int64_t cnt = int64_t(leaf_lo[t + 1] - leaf_lo[t]) * (leaf_lo[s + 1] - leaf_lo[s]);
-            dns_off[b + 1] = dns_off[b] + (cnt + blk_align - 1) / blk_align * blk_align;
+            dns_off[b + 1] = dns_off[b] + (cnt + 31) / 32 * 32;  // 128-byte aligned blocks
         }
-    std::vector<double> pts_tree(op.n * op.dim);
-    for (int64_t i = 0; i < op.n; ++i)
-        for (int d = 0; d < op.dim; ++d) pts_tree[i * op.dim + d] = op.pts[op.perm[i] * op.dim + d];
+    const size_t s_bytes = align_up(size_t(ncpl) * dv->kkp * es);
+    const size_t d_bytes = align_up(size_t(dns_off[ndns]) * es);
 
-    // arena layout: persistent part
+    // ---- stream descriptors: coupling rows of levels >= Lb and all dense rows (bottom),
+    //      coupling rows of levels < Lb (top)
+    std::vector<h2s::StreamDesc> db, dt;
+    std::vector<uint64_t> bb, bt;
+    auto level_of = [](int64_t t) {
+        int l = 0;
+        for (; t > 1; t >>= 1) ++l;
+        return l;
+    };
+    for (int64_t t = 1; t <= op.nnodes; ++t) {
+        const int64_t b0 = op.cpl_rowptr[t], b1 = op.cpl_rowptr[t + 1];
+        const bool is_top = level_of(t) < dv->Lb;
+        if (b0 == b1) {  // empty block row: its yhat row is written as zeros
+            h2s::StreamDesc d{};
+            d.out_node = int32_t(t);
+            d.rows = int16_t(k);
+            d.flags = h2s::kZero | h2s::kLast;
+            (is_top ? dt : db).push_back(d);
+            (is_top ? bt : bb).push_back(uint64_t(k) * es);
+        }
+        for (int64_t b = b0; b < b1; ++b) {
+            h2s::StreamDesc d{};
+            d.src = uint64_t(b) * dv->kkp * es;
+            d.x_node = op.cpl_col[b];
+            d.out_node = int32_t(t);
+            d.rows = int16_t(k);
+            d.cols = int16_t(k);
+            d.flags = b + 1 == b1 ? h2s::kLast : 0;
+            (is_top ? dt : db).push_back(d);
+            (is_top ? bt : bb).push_back(uint64_t(k) * k * es);
+        }
+    }
+    for (int64_t t = 0; t < nleaves; ++t) {
+        const int64_t b0 = op.dns_rowptr[t], b1 = op.dns_rowptr[t + 1];
+        for (int64_t b = b0; b < b1; ++b) {
+            const int64_t s = op.dns_col[b];
+            h2s::StreamDesc d{};
+            d.src = s_bytes + uint64_t(dns_off[b]) * es;
+            d.x_node = int32_t(s);
+            d.out_node = int32_t(t);
+            d.rows = int16_t(leaf_lo[t + 1] - leaf_lo[t]);
+            d.cols = int16_t(leaf_lo[s + 1] - leaf_lo[s]);
+            d.flags = h2s::kDense | (b + 1 == b1 ? h2s::kLast : 0);
+            db.push_back(d);
+            bb.push_back(uint64_t(d.rows) * d.cols * es);
+        }
+    }
+    std::vector<int64_t> pb, pt;
+    if (!make_chunks(db, bb, 512 * 1024, pb) || !make_chunks(dt, bt, 128 * 1024, pt)) {
+        h2_device_free(&op);
+        return H2_EINVAL;  // a block row longer than one scheduling chunk
+    }
+    dv->n_chunks_bottom = int64_t(pb.size());
+    dv->n_chunks_top = int64_t(pt.size());
+    dv->grid_bottom = int(std::max<int64_t>(1, std::min<int64_t>(dv->num_sms, dv->n_chunks_bottom)));
+    dv->grid_top = int(std::max<int64_t>(1, std::min<int64_t>(32, dv->n_chunks_top)));
+
+    // ---- arena layout
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
         off += align_up(std::max<size_t>(bytes, 1));
         return o;
     };
-    const size_t o_perm = take(op.n * 4), o_leaf = take((nleaves + 1) * 4);
-    const size_t o_U = take(size_t(op.n) * k * es), o_E = take(size_t(op.nnodes + 1) * k * k * es);
-    const size_t o_cptr = take((op.nnodes + 2) * 8), o_ccol = take(ncpl * 4), o_crows = take(cpl_rows.size() * 4);
-    const size_t o_S = take(size_t(ncpl) * k * k * es);
-    const size_t o_dptr = take((nleaves + 1) * 8), o_dcol = take(ndns * 4), o_doff = take((ndns + 1) * 8);
-    const size_t o_D = take(size_t(dns_off[ndns]) * es);
+    const size_t o_perm = take(op.n * 4), o_leaf = take((nleaves + 1) * 4), o_cptr = take((op.nnodes + 2) * 8);
+    const size_t o_U = take(size_t(nleaves) * mp * kx * es), o_Ut = take(size_t(nleaves) * kx * mp * es);
+    const size_t o_E = take(size_t(op.nnodes + 1) * k * kx * es), o_Et = take(size_t(op.nnodes + 1) * k * kx * es);
+    const size_t o_vals = take(s_bytes + d_bytes);
+    const size_t o_db = take(db.size() * sizeof(h2s::StreamDesc)), o_dt = take(dt.size() * sizeof(h2s::StreamDesc));
+    const size_t o_pb = take(pb.size() * 8), o_pt = take(pt.size() * 8), o_err = take(16);
     const size_t persistent = off;
-    // temporaries for generation (freed after upload)
-    const size_t t_cheb = op.cheb.size() * 8, t_pts = pts_tree.size() * 8, t_crow = ncpl * 4, t_drow = ndns * 4;
-    const size_t tmp_bytes = align_up(t_cheb) + align_up(t_pts) + align_up(t_crow) + align_up(t_drow) + 4 * kAlign;
+    // temporaries for generation
+    const size_t t_cheb = align_up(op.cheb.size() * 8), t_pts = align_up(size_t(op.n) * op.dim * 8);
+    const size_t t_crow = align_up(ncpl * 4 + 4), t_ccol = align_up(ncpl * 4 + 4), t_drow = align_up(ndns * 4 + 4),
+                 t_dcol = align_up(ndns * 4 + 4), t_doff = align_up((ndns + 1) * 8);
+    const size_t tmp_bytes = t_cheb + t_pts + t_crow + t_ccol + t_drow + t_dcol + t_doff;
 
-    char *arena = nullptr;
+    char *arena = nullptr, *tmp = nullptr;
     if (cudaMalloc(&arena, persistent) != cudaSuccess) {
         cudaGetLastError();
         h2_device_free(&op);
@@ -305,7 +499,6 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     }
     dv->arena = arena;
     dv->arena_bytes = persistent;
-    char *tmp = nullptr;
     if (cudaMalloc(&tmp, tmp_bytes) != cudaSuccess) {
         cudaGetLastError();
         h2_device_free(&op);
@@ -313,54 +506,92 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     }
     dv->perm = reinterpret_cast<int32_t *>(arena + o_perm);
     dv->leaf_lo = reinterpret_cast<int32_t *>(arena + o_leaf);
-    dv->U = arena + o_U;
-    dv->E = arena + o_E;
     dv->cpl_rowptr = reinterpret_cast<int64_t *>(arena + o_cptr);
-    dv->cpl_col = reinterpret_cast<int32_t *>(arena + o_ccol);
-    dv->cpl_rows = reinterpret_cast<int32_t *>(arena + o_crows);
-    dv->S = arena + o_S;
-    dv->dns_rowptr = reinterpret_cast<int64_t *>(arena + o_dptr);
-    dv->dns_col = reinterpret_cast<int32_t *>(arena + o_dcol);
-    dv->dns_off = reinterpret_cast<int64_t *>(arena + o_doff);
-    dv->D = arena + o_D;
-    double *d_cheb = reinterpret_cast<double *>(tmp);
-    double *d_pts = reinterpret_cast<double *>(tmp + align_up(t_cheb));
-    int32_t *d_crow = reinterpret_cast<int32_t *>(tmp + align_up(t_cheb) + align_up(t_pts));
-    int32_t *d_drow = reinterpret_cast<int32_t *>(tmp + align_up(t_cheb) + align_up(t_pts) + align_up(t_crow));
+    dv->U = arena + o_U;
+    dv->Ut = arena + o_Ut;
+    dv->E = arena + o_E;
+    dv->Et = arena + o_Et;
+    dv->vals = reinterpret_cast<unsigned char *>(arena + o_vals);
+    dv->desc_bottom = reinterpret_cast<h2s::StreamDesc *>(arena + o_db);
+    dv->desc_top = reinterpret_cast<h2s::StreamDesc *>(arena + o_dt);
+    dv->chunks_bottom = reinterpret_cast<int64_t *>(arena + o_pb);
+    dv->chunks_top = reinterpret_cast<int64_t *>(arena + o_pt);
+    dv->err = reinterpret_cast<int *>(arena + o_err);
+    char *tp = tmp;
+    double *d_cheb = reinterpret_cast<double *>(tp);
+    tp += t_cheb;
+    double *d_pts = reinterpret_cast<double *>(tp);
+    tp += t_pts;
+    int32_t *d_crow = reinterpret_cast<int32_t *>(tp);
+    tp += t_crow;
+    int32_t *d_ccol = reinterpret_cast<int32_t *>(tp);
+    tp += t_ccol;
+    int32_t *d_drow = reinterpret_cast<int32_t *>(tp);
+    tp += t_drow;
+    int32_t *d_dcol = reinterpret_cast<int32_t *>(tp);
+    tp += t_dcol;
+    int64_t *d_doff = reinterpret_cast<int64_t *>(tp);
 
-    // bases in the target precision
-    std::vector<unsigned char> Ubuf(size_t(op.n) * k * es), Ebuf(size_t(op.nnodes + 1) * k * k * es);
-    if (es == 8) {
-        std::memcpy(Ubuf.data(), op.U.data(), Ubuf.size());
-        std::memcpy(Ebuf.data(), op.E.data(), Ebuf.size());
-    } else {
-        float *u = reinterpret_cast<float *>(Ubuf.data()), *e = reinterpret_cast<float *>(Ebuf.data());
-        for (size_t i = 0; i < op.U.size(); ++i) u[i] = float(op.U[i]);
-        for (size_t i = 0; i < op.E.size(); ++i) e[i] = float(op.E[i]);
-    }
+    // ---- bases and transfers in the target precision and tile layouts
+    std::vector<unsigned char> Ub(size_t(nleaves) * mp * kx * es, 0), Utb(size_t(nleaves) * kx * mp * es, 0);
+    std::vector<unsigned char> Eb(size_t(op.nnodes + 1) * k * kx * es, 0), Etb(size_t(op.nnodes + 1) * k * kx * es, 0);
+    auto put = [&](std::vector<unsigned char> &buf, size_t idx, double v) {
+        if (es == 8) reinterpret_cast<double *>(buf.data())[idx] = v;
+        else reinterpret_cast<float *>(buf.data())[idx] = float(v);
+    };
+    for (int64_t t = 0; t < nleaves; ++t)
+        for (int i = 0; i < leaf_lo[t + 1] - leaf_lo[t]; ++i)
+            for (int nu = 0; nu < k; ++nu) {
+                const double u = op.U[(int64_t(leaf_lo[t]) + i) * k + nu];
+                put(Ub, (size_t(t) * mp + i) * kx + nu, u);
+                put(Utb, (size_t(t) * kx + nu) * mp + i, u);
+            }
+    for (int64_t c = 2; c <= op.nnodes; ++c)
+        for (int mu = 0; mu < k; ++mu)
+            for (int nu = 0; nu < k; ++nu) {
+                const double e = op.E[(size_t(c) * k + mu) * k + nu];
+                put(Eb, (size_t(c) * k + mu) * kx + nu, e);
+                put(Etb, (size_t(c) * k + nu) * kx + mu, e);
+            }
+    std::vector<double> pts_tree(size_t(op.n) * op.dim);
+    for (int64_t i = 0; i < op.n; ++i)
+        for (int d = 0; d < op.dim; ++d) pts_tree[i * op.dim + d] = op.pts[op.perm[i] * op.dim + d];
+
     int rc = H2_OK;
     auto cp = [&](void *dst, const void *src, size_t bytes) {
         if (rc == H2_OK && bytes) rc = cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
     };
     cp(dv->perm, perm32.data(), op.n * 4);
     cp(dv->leaf_lo, leaf_lo.data(), (nleaves + 1) * 4);
-    cp(dv->U, Ubuf.data(), Ubuf.size());
-    cp(dv->E, Ebuf.data(), Ebuf.size());
     cp(dv->cpl_rowptr, op.cpl_rowptr.data(), (op.nnodes + 2) * 8);
-    cp(dv->cpl_col, op.cpl_col.data(), ncpl * 4);
-    cp(dv->cpl_rows, cpl_rows.data(), cpl_rows.size() * 4);
-    cp(dv->dns_rowptr, op.dns_rowptr.data(), (nleaves + 1) * 8);
-    cp(dv->dns_col, op.dns_col.data(), ndns * 4);
-    cp(dv->dns_off, dns_off.data(), (ndns + 1) * 8);
-    cp(d_cheb, op.cheb.data(), t_cheb);
-    cp(d_pts, pts_tree.data(), t_pts);
-    cp(d_crow, cpl_row.data(), t_crow);
-    cp(d_drow, dns_row.data(), t_drow);
+    cp(dv->U, Ub.data(), Ub.size());
+    cp(dv->Ut, Utb.data(), Utb.size());
+    cp(dv->E, Eb.data(), Eb.size());
+    cp(dv->Et, Etb.data(), Etb.size());
+    cp(dv->desc_bottom, db.data(), db.size() * sizeof(h2s::StreamDesc));
+    cp(dv->desc_top, dt.data(), dt.size() * sizeof(h2s::StreamDesc));
+    cp(dv->chunks_bottom, pb.data(), pb.size() * 8);
+    cp(dv->chunks_top, pt.data(), pt.size() * 8);
+    cp(d_cheb, op.cheb.data(), op.cheb.size() * 8);
+    cp(d_pts, pts_tree.data(), pts_tree.size() * 8);
+    cp(d_crow, cpl_row.data(), ncpl * 4);
+    cp(d_ccol, op.cpl_col.data(), ncpl * 4);
+    cp(d_drow, dns_row.data(), ndns * 4);
+    cp(d_dcol, op.dns_col.data(), ndns * 4);
+    cp(d_doff, dns_off.data(), (ndns + 1) * 8);
+    if (rc == H2_OK) rc = cuda_status(cudaMemsetAsync(dv->err, 0, 16, st));
     if (rc == H2_OK)
-        rc = es == 8 ? generate_blocks<double>(op, *dv, d_crow, d_drow, d_cheb, d_pts, st)
-                     : generate_blocks<float>(op, *dv, d_crow, d_drow, d_cheb, d_pts, st);
+        rc = es == 8 ? generate_blocks<double>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st)
+                     : generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st);
     if (rc == H2_OK) rc = cuda_status(cudaStreamSynchronize(st));
     cudaFree(tmp);
+    if (rc == H2_OK) {
+        int lo_prio = 0, hi_prio = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        rc = cuda_status(cudaStreamCreateWithPriority(&dv->side, cudaStreamNonBlocking, hi_prio));
+        if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&dv->ev_up, cudaEventDisableTiming));
+        if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&dv->ev_top, cudaEventDisableTiming));
+    }
     if (rc != H2_OK) h2_device_free(&op);
     return rc;
 }
@@ -368,7 +599,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
 size_t h2_workspace_bytes(h2_handle h, int nv)
 {
     if (!h || !h->dev || nv < 1) return 0;
-    return ws_layout(*h, h->dev->esize, nv, nullptr, nullptr);
+    return ws_layout(*h, *h->dev, nv, nullptr, nullptr);
 }
 
 int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *workspace,
@@ -376,25 +607,18 @@ int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, doub
 {
     if (!h || !X || !Y || nv < 1 || !workspace) return H2_EINVAL;
     if (!h->dev) return H2_ESTATE;
-    const h2_device &dv = *h->dev;
-    if (ws_bytes < ws_layout(*h, dv.esize, nv, nullptr, nullptr)) return H2_EINVAL;
+    h2_device &dv = *h->dev;
+    if (ws_bytes < ws_layout(*h, dv, nv, nullptr, nullptr)) return H2_EINVAL;
     if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return H2_EINVAL;
     Workspace w;
-    ws_layout(*h, dv.esize, nv, &w, workspace);
+    ws_layout(*h, dv, nv, &w, workspace);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    h2_device &dvm = *h->dev;
-    dvm.products += 1;
-    for (int v0 = 0; v0 < nv; v0 += kMaxChunk) {
-        const int c = std::min(kMaxChunk, nv - v0);
-        const size_t o = size_t(v0) * h->n;
-        const int rc = dv.esize == 8
-                           ? launch_matvec<double>(*h, dvm, static_cast<const double *>(X) + o,
-                                                   static_cast<double *>(Y) + o, c, alpha, beta, w, st)
-                           : launch_matvec<float>(*h, dvm, static_cast<const float *>(X) + o,
-                                                  static_cast<float *>(Y) + o, c, alpha, beta, w, st);
-        if (rc != H2_OK) return rc;
-    }
-    return H2_OK;
+    dv.products += 1;
+    if (dv.esize == 8)
+        return launch_product<double>(*h, dv, static_cast<const double *>(X), static_cast<double *>(Y), nv, alpha,
+                                      beta, w, st);
+    return launch_product<float>(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w,
+                                 st);
 }
 
 int h2_matvec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *cuda_stream)
@@ -402,7 +626,7 @@ int h2_matvec(h2_handle h, const void *X, void *Y, int nv, double alpha, double 
     if (!h || !X || !Y || nv < 1) return H2_EINVAL;
     if (!h->dev) return H2_ESTATE;
     h2_device &dv = *h->dev;
-    const size_t need = ws_layout(*h, dv.esize, nv, nullptr, nullptr);
+    const size_t need = ws_layout(*h, dv, nv, nullptr, nullptr);
     if (dv.ws_bytes < need) {
         if (dv.ws) {
             cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
@@ -442,7 +666,9 @@ int h2_get_timing(h2_handle h, double *phase_ms, int64_t *phase_launches, int64_
     }
     if (products) *products = dv.products;
     dv.products = 0;
-    return cuda_status(cudaGetLastError());
+    int flag = 0;
+    if (cudaMemcpy(&flag, dv.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ECUDA;
+    return flag ? H2_ETIMEOUT : H2_OK;
 }
 
 int h2_destroy(h2_handle h)
@@ -458,6 +684,7 @@ int h2_build(const double *points, int64_t n, int dim, h2_kernel kernel, int lea
 {
     if (!out) return H2_EINVAL;
     *out = nullptr;
+    if (leaf_size > kMaxLeaf) return H2_EINVAL;
     h2_op *op = new (std::nothrow) h2_op;
     if (!op) return H2_ENOMEM;
     const int rc = h2_host_build(op, points, n, dim, kernel, leaf_size, cheb_order, eta);

@@ -1,0 +1,678 @@
+// h2_stream.cuh -- pipelined kernels of the H^2 product (FP64 / FP32 entries, nv <= NVMAX).
+//
+// Every matrix tile (coupling block, dense block, leaf basis, transfer) streams from HBM
+// into a ring of shared-memory stages through 1-D bulk copies issued by one producer
+// thread (warp 4); four consumer warps (128 threads) multiply each tile with a vector
+// segment and reduce in a fixed order (deterministic, no atomics on data).
+//
+//   k_up_bottom   leaf projection xhat^q_t = U_t^T x_t and the lowest L upsweep levels
+//                 xhat^{l-1}_p = sum_c E_c^T xhat^l_c for one CTA-resident subtree of 2^L
+//                 leaves at a time (Sec. 3.1, Alg 1);
+//   k_stream      block rows of coupling blocks (yhat^l_t = sum_s S_ts xhat^l_s, Sec. 3.2,
+//                 Alg 4) and of dense blocks (A_de x, Sec. 3) from one flat descriptor list,
+//                 handed out to persistent CTAs in chunks of whole rows by an atomic ticket;
+//                 an empty block row is written as zeros, so every yhat row is defined;
+//   k_down_bottom the lowest downsweep levels yhat^l_c = E_c yhat^{l-1}_p + yhat^l_c, the leaf
+//                 expansion y_t = U_t yhat^q_t (Sec. 3.3, Alg 6), the dense partial result and
+//                 the epilogue Y[perm] = alpha y + beta Y, for one subtree at a time.
+//
+// Tile layouts (element type T, ld = leading dimension): the consumer always computes
+// out[o] = sum_j tile[j * ld + o] * x[j], so each tile is stored with the output index
+// contiguous: U_t as [i][nu] (ld kx) for the upsweep, U_t^T as [nu][i] (ld mp) for the
+// expansion, E_c as [mu][nu] (ld kx) for the upsweep, E_c^T as [nu][mu] (ld kx) for the
+// downsweep, S_ts^T as [mu][nu] (ld k) and D_ts^T as [j][i] (ld rows_t).
+// Vector trees: xh, yh as [node][v][kx]; permuted input xt and dense result yd as
+// [leaf][v][mp]; kx = k rounded up to 4, mp = largest leaf rounded up to 4, so every
+// segment starts on a 16-byte boundary.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "h2_pipe.cuh"
+
+namespace h2s {
+
+constexpr int kConsumers = 128;  // 4 consumer warps
+constexpr int kThreads = 160;    // + 1 producer warp
+constexpr int kChunkDesc = 256;  // most descriptors in one scheduling chunk
+constexpr int kRedElems = 512;   // group-exchange buffer per vector (elements of T)
+
+struct alignas(16) StreamDesc {
+    uint64_t src;     // byte offset of the tile in the value buffer
+    int32_t x_node;   // heap index (coupling) or leaf index (dense) of the input segment
+    int32_t out_node; // heap index (coupling) or leaf index (dense) of the output segment
+    int16_t rows, cols;
+    int16_t flags;    // kDense | kLast | kZero | kEnd
+    int16_t pad0;
+    int32_t pad1;
+};
+constexpr int16_t kDense = 1;  // dense block (else coupling block)
+constexpr int16_t kLast = 2;   // last block of its row: reduce and store the row
+constexpr int16_t kZero = 4;   // empty row: no data, store zeros
+constexpr int16_t kEnd = 8;    // no more work (consumers stop)
+
+template <typename T>
+struct Op {
+    int64_t n, nleaves, first_leaf;
+    int k, kx, mp, q, Lb, L;
+    const int32_t *perm, *leaf_lo;
+    const T *U, *Ut, *E, *Et;
+    const unsigned char *vals;
+};
+
+template <typename T>
+struct Vec {
+    const T *X;
+    T *Y;
+    int nv;
+    T alpha, beta;
+    T *xt, *yd, *xh, *yh;
+    int *tickets;  // [0] bottom stream, [1] top stream (zeroed by k_gather)
+    int *err;
+};
+
+struct Pipe {
+    int ns;               // stages
+    uint32_t tile_bytes;  // bytes of one tile slot
+    uint32_t x_bytes;     // bytes of one vector slot
+};
+
+__host__ __device__ constexpr int rpad(int r) { return r <= 32 ? 32 : (r <= 64 ? 64 : 128); }
+
+template <typename T>
+struct Smem {
+    unsigned char *tiles, *xs;
+    StreamDesc *desc;
+    uint64_t *full, *empty;
+    T *red, *sub;
+    StreamDesc *dbuf;  // [2][kChunkDesc] (k_stream only)
+    uint64_t *dbar;    // [2]
+    int *abort_flag;
+};
+
+template <typename T, int NVMAX>
+__host__ __device__ inline size_t smem_bytes(const Pipe &p, int sub_nodes, int kx, bool chunks)
+{
+    size_t b = size_t(p.ns) * (p.tile_bytes + p.x_bytes);
+    b += size_t(p.ns) * sizeof(StreamDesc);
+    b += size_t(2 * p.ns) * sizeof(uint64_t);
+    b += size_t(kRedElems) * NVMAX * sizeof(T);
+    b += size_t(sub_nodes) * kx * NVMAX * sizeof(T);
+    if (chunks) b += 2 * kChunkDesc * sizeof(StreamDesc) + 2 * sizeof(uint64_t);
+    b += 16;
+    return b;
+}
+
+template <typename T, int NVMAX>
+__device__ inline Smem<T> carve(unsigned char *base, const Pipe &p, int sub_nodes, int kx, bool chunks)
+{
+    Smem<T> s;
+    unsigned char *c = base;
+    s.tiles = c;
+    c += size_t(p.ns) * p.tile_bytes;
+    s.xs = c;
+    c += size_t(p.ns) * p.x_bytes;
+    s.desc = reinterpret_cast<StreamDesc *>(c);
+    c += size_t(p.ns) * sizeof(StreamDesc);
+    s.full = reinterpret_cast<uint64_t *>(c);
+    s.empty = s.full + p.ns;
+    c += size_t(2 * p.ns) * sizeof(uint64_t);
+    s.red = reinterpret_cast<T *>(c);
+    c += size_t(kRedElems) * NVMAX * sizeof(T);
+    s.sub = reinterpret_cast<T *>(c);
+    c += size_t(sub_nodes) * kx * NVMAX * sizeof(T);
+    s.dbuf = nullptr;
+    s.dbar = nullptr;
+    if (chunks) {
+        s.dbuf = reinterpret_cast<StreamDesc *>(c);
+        c += 2 * kChunkDesc * sizeof(StreamDesc);
+        s.dbar = reinterpret_cast<uint64_t *>(c);
+        c += 2 * sizeof(uint64_t);
+    }
+    s.abort_flag = reinterpret_cast<int *>(c);
+    return s;
+}
+
+template <typename T>
+__device__ inline void init_pipe(Smem<T> &s, const Pipe &p)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < p.ns; ++i) {
+            h2p::mbar_init(&s.full[i], 1);
+            h2p::mbar_init(&s.empty[i], kConsumers / 32);
+        }
+        if (s.dbar) {
+            h2p::mbar_init(&s.dbar[0], 1);
+            h2p::mbar_init(&s.dbar[1], 1);
+        }
+        *s.abort_flag = 0;
+        h2p::fence_barrier_init();
+    }
+    __syncthreads();
+}
+
+// Ring position shared by the producer and the consumers (they walk the same sequence).
+struct Ring {
+    int stage = 0;
+    uint32_t phase = 0;
+    int ns;
+    uint32_t issued = 0;  // producer only: stages that received a copy (bit per stage)
+    uint32_t parity = 0;  // producer only: phase parity of each stage's last copy
+    __device__ explicit Ring(int n) : ns(n) {}
+    __device__ void next()
+    {
+        if (++stage == ns) {
+            stage = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+// Producer epilogue: after an abort, wait (bounded, about a second per stage) until every
+// copy this CTA started has landed, so that no bulk copy is still writing into shared
+// memory when the CTA exits.
+template <typename T>
+__device__ inline void drain_on_abort(Smem<T> &s, const Ring &r)
+{
+    if (!*s.abort_flag) return;
+    for (int i = 0; i < r.ns; ++i) {
+        if (!(r.issued >> i & 1u)) continue;
+        const uint32_t par = r.parity >> i & 1u;
+        const long long t0 = clock64();
+        while (!h2p::mbar_try_wait(&s.full[i], par) && clock64() - t0 < h2p::kWaitCycles) {
+        }
+    }
+}
+
+// Producer side: claim the next stage and start copying a tile and up to two vector
+// segments (into the first and the second half of the stage's vector slot). Returns false
+// if the pipeline aborted.
+template <typename T>
+__device__ inline bool produce(Smem<T> &s, const Pipe &p, Ring &r, const void *tile, uint32_t tile_bytes,
+                               const void *x, uint32_t x_bytes, const void *x2, uint32_t x2_bytes,
+                               const StreamDesc *d, int *err)
+{
+    if (!h2p::mbar_wait(&s.empty[r.stage], r.phase ^ 1u, s.abort_flag, err)) return false;
+    if (d) s.desc[r.stage] = *d;
+    unsigned char *xs = s.xs + size_t(r.stage) * p.x_bytes;
+    h2p::mbar_arrive_expect_tx(&s.full[r.stage], tile_bytes + x_bytes + x2_bytes);
+    if (tile_bytes) h2p::bulk_g2s(s.tiles + size_t(r.stage) * p.tile_bytes, tile, tile_bytes, &s.full[r.stage]);
+    if (x_bytes) h2p::bulk_g2s(xs, x, x_bytes, &s.full[r.stage]);
+    if (x2_bytes) h2p::bulk_g2s(xs + p.x_bytes / 2, x2, x2_bytes, &s.full[r.stage]);
+    r.issued |= 1u << r.stage;
+    r.parity = (r.parity & ~(1u << r.stage)) | (r.phase << r.stage);
+    r.next();
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ const T *stage_tile(const Smem<T> &s, const Pipe &p, int stage)
+{
+    return reinterpret_cast<const T *>(s.tiles + size_t(stage) * p.tile_bytes);
+}
+template <typename T>
+__device__ __forceinline__ const T *stage_x(const Smem<T> &s, const Pipe &p, int stage, int half = 0)
+{
+    return reinterpret_cast<const T *>(s.xs + size_t(stage) * p.x_bytes + (half ? p.x_bytes / 2 : 0));
+}
+
+// Consumer: release a stage once this warp is done reading it.
+__device__ __forceinline__ void release(uint64_t *empty, int lane)
+{
+    __syncwarp();
+    if (lane == 0) h2p::mbar_arrive(empty);
+}
+
+// Consumer accumulator: out[o] = sum_j tile[j*ld + o] * x[v*xld + j] over the tiles of one
+// output. The 128 consumer threads are split into `lanes` output lanes x G column groups
+// (both powers of two). With ld a multiple of VEC (16 bytes of T) each lane owns VEC
+// consecutive outputs and reads them with one 16-byte shared-memory load per column;
+// otherwise it owns one output (scalar path). Column group g takes j = g, g+G, ...; the
+// groups are summed in a fixed order, so the result is deterministic.
+template <typename T, int NVMAX>
+struct Acc {
+    static constexpr int VEC = 16 / int(sizeof(T));
+    T a[NVMAX][VEC];
+    int per, shift, g, G, o0, Rp;
+
+    __device__ __forceinline__ void setup(int R, int ld, int tid)
+    {
+        Rp = rpad(R);
+        per = (ld % VEC == 0) ? VEC : 1;
+        const int lanes = Rp / per;
+        shift = __ffs(lanes) - 1;
+        g = tid >> shift;
+        G = kConsumers >> shift;
+        o0 = (tid & (lanes - 1)) * per;
+    }
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int v = 0; v < NVMAX; ++v)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) a[v][e] = T(0);
+    }
+    __device__ __forceinline__ void gemv(const T *__restrict__ tile, int ld, int R, int C, const T *__restrict__ x,
+                                         int xld, int nv)
+    {
+        if (o0 >= R) return;
+        if (per == VEC) {
+            using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+#pragma unroll 4
+            for (int j = g; j < C; j += G) {
+                T t[VEC];
+                *reinterpret_cast<VT *>(t) = *reinterpret_cast<const VT *>(tile + j * ld + o0);
+#pragma unroll
+                for (int v = 0; v < NVMAX; ++v)
+                    if (v < nv) {
+                        const T xv = x[v * xld + j];
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) a[v][e] += t[e] * xv;
+                    }
+            }
+        } else {
+#pragma unroll 4
+            for (int j = g; j < C; j += G) {
+                const T t = tile[j * ld + o0];
+#pragma unroll
+                for (int v = 0; v < NVMAX; ++v)
+                    if (v < nv) a[v][0] += t * x[v * xld + j];
+            }
+        }
+    }
+    // Sum the column groups; true for the threads (g == 0, o0 < R) holding final values.
+    __device__ __forceinline__ bool reduce(int R, int nv, T *red)
+    {
+        if (G > 1) {
+            if (g > 0 && o0 < R) {
+#pragma unroll
+                for (int v = 0; v < NVMAX; ++v)
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e)
+                        if (v < nv && e < per) red[((g - 1) * NVMAX + v) * Rp + o0 + e] = a[v][e];
+            }
+            h2p::consumer_sync(kConsumers);
+            if (g == 0 && o0 < R)
+                for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+                    for (int v = 0; v < NVMAX; ++v)
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e)
+                            if (v < nv && e < per) a[v][e] += red[((gg - 1) * NVMAX + v) * Rp + o0 + e];
+        }
+        return g == 0 && o0 < R;
+    }
+    // Store the held outputs o0 .. o0+per-1 (< R) of every vector v < nv at dst[v*ld + o].
+    __device__ __forceinline__ void store(T *dst, int ld, int nv, int R) const
+    {
+#pragma unroll
+        for (int v = 0; v < NVMAX; ++v)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (v < nv && e < per && o0 + e < R) dst[v * ld + o0 + e] = a[v][e];
+    }
+    __device__ __forceinline__ void add(const T *src, int ld, int nv, int R)
+    {
+#pragma unroll
+        for (int v = 0; v < NVMAX; ++v)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (v < nv && e < per && o0 + e < R) a[v][e] += src[v * ld + o0 + e];
+    }
+};
+
+// ------------------------------------------------------------------ gather
+
+// xt[leaf][v][i] = X[v*n + perm[leaf_lo[leaf] + i]]: one CTA per leaf (grid-stride). Also
+// resets the scheduling tickets of this product.
+template <typename T>
+__global__ void k_gather(Op<T> op, Vec<T> vec)
+{
+    if (blockIdx.x == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
+    for (int64_t leaf = blockIdx.x; leaf < op.nleaves; leaf += gridDim.x) {
+        const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
+        for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+            const int i = e % R, v = e / R;
+            vec.xt[(leaf * vec.nv + v) * op.mp + i] = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ bottom upsweep
+
+template <typename T, int NVMAX>
+__global__ void __launch_bounds__(kThreads) k_up_bottom(Op<T> op, Vec<T> vec, Pipe pp, int64_t nsub)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int L = op.L, sub_nodes = 2 << L;
+    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, sub_nodes, op.kx, false);
+    init_pipe(s, pp);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv;
+    const uint32_t es = sizeof(T);
+    Ring ring(pp.ns);
+
+    if (warp == 4) {  // producer: fixed-size tiles, so no per-leaf metadata is needed
+        if (lane == 0) {
+            bool ok = true;
+            for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x) {
+                const int64_t leaf0 = st << L;
+                for (int j = 0; ok && j < (1 << L); ++j) {
+                    const int64_t leaf = leaf0 + j;
+                    ok = produce(s, pp, ring, op.U + leaf * mp * kx, mp * kx * es, vec.xt + leaf * mp * nv,
+                                 mp * nv * es, nullptr, 0, nullptr, vec.err);
+                }
+                for (int lev = op.q; ok && lev > op.Lb; --lev) {
+                    const int64_t cnt = int64_t(1) << (lev - op.Lb);
+                    const int64_t c0 = (int64_t(1) << lev) + st * cnt;
+                    for (int64_t c = c0; ok && c < c0 + cnt; ++c)
+                        ok = produce(s, pp, ring, op.E + c * k * kx, k * kx * es, nullptr, 0, nullptr, 0, nullptr,
+                                     vec.err);
+                }
+            }
+            drain_on_abort(s, ring);
+        }
+        return;
+    }
+
+    const int tid = threadIdx.x;
+    Acc<T, NVMAX> acc;
+    acc.setup(k, kx, tid);
+    const int wstride = kx * NVMAX;
+    for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x) {
+        const int64_t leaf0 = st << L;
+        // leaf projections into local slots 2^L + j
+        for (int j = 0; j < (1 << L); ++j) {
+            const int64_t leaf = leaf0 + j;
+            const int R = op.leaf_lo[leaf + 1] - op.leaf_lo[leaf];
+            acc.zero();
+            if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
+            acc.gemv(stage_tile(s, pp, ring.stage), kx, k, R, stage_x(s, pp, ring.stage), mp, nv);
+            release(&s.empty[ring.stage], lane);
+            ring.next();
+            if (acc.reduce(k, nv, s.red)) {
+                acc.store(s.sub + ((1 << L) + j) * wstride, kx, nv, k);
+                acc.store(vec.xh + (op.first_leaf + leaf) * kx * nv, kx, nv, k);
+            }
+            h2p::consumer_sync(kConsumers);
+        }
+        // transfers, level by level
+        for (int lev = op.q; lev > op.Lb; --lev) {
+            const int rel = lev - op.Lb;
+            const int64_t cnt = int64_t(1) << rel;
+            for (int64_t pi = 0; pi < cnt / 2; ++pi) {
+                acc.zero();
+                for (int c = 0; c < 2; ++c) {
+                    const int child_slot = (1 << rel) + int(2 * pi + c);
+                    if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
+                    acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, s.sub + child_slot * wstride, kx, nv);
+                    release(&s.empty[ring.stage], lane);
+                    ring.next();
+                }
+                if (acc.reduce(k, nv, s.red)) {
+                    const int pslot = (1 << (rel - 1)) + int(pi);
+                    const int64_t par = (int64_t(1) << (lev - 1)) + st * (cnt / 2) + pi;
+                    acc.store(s.sub + pslot * wstride, kx, nv, k);
+                    acc.store(vec.xh + par * kx * nv, kx, nv, k);
+                }
+                h2p::consumer_sync(kConsumers);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ block-row stream
+
+// chunks[c] = (first descriptor << 16) | descriptor count: whole rows, in order.
+template <typename T, int NVMAX>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_stream(Op<T> op, Vec<T> vec, Pipe pp, const StreamDesc *__restrict__ desc, const int64_t *__restrict__ chunks,
+             int64_t nchunks, int ticket_index)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, 0, op.kx, true);
+    init_pipe(s, pp);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int kx = op.kx, mp = op.mp, nv = vec.nv;
+    const uint32_t es = sizeof(T);
+    Ring ring(pp.ns);
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int *ticket = vec.tickets + ticket_index;
+            // a chunk's descriptors are bulk-copied into one of two shared-memory slots while
+            // the previous chunk is being issued; tickets are fetched one chunk ahead
+            auto fetch_desc = [&](int slot, int64_t rec) {
+                const int64_t b0 = rec >> 16;
+                const uint32_t bytes = uint32_t(rec & 0xffff) * uint32_t(sizeof(StreamDesc));
+                h2p::fence_proxy_async_shared();
+                h2p::mbar_arrive_expect_tx(&s.dbar[slot], bytes);
+                h2p::bulk_g2s(s.dbuf + slot * kChunkDesc, desc + b0, bytes, &s.dbar[slot]);
+            };
+            int64_t tA = atomicAdd(ticket, 1);
+            int64_t tB = atomicAdd(ticket, 1);
+            int64_t recA = tA < nchunks ? chunks[tA] : 0;
+            int slot = 0;
+            uint32_t dphase = 0;  // bit per slot
+            bool ok = true;
+            if (tA < nchunks) fetch_desc(0, recA);
+            while (ok && tA < nchunks) {
+                const int64_t recB = tB < nchunks ? chunks[tB] : 0;
+                const int64_t tC = atomicAdd(ticket, 1);
+                ok = h2p::mbar_wait(&s.dbar[slot], dphase >> slot & 1u, s.abort_flag, vec.err);
+                dphase ^= 1u << slot;
+                const int cnt = int(recA & 0xffff);
+                const int pre = cnt - 1 < 4 ? cnt - 1 : 4;
+                for (int i = 0; ok && i < cnt; ++i) {
+                    if (i == pre && tB < nchunks) fetch_desc(slot ^ 1, recB);
+                    const StreamDesc d = s.dbuf[slot * kChunkDesc + i];
+                    if (d.flags & kZero) {
+                        ok = produce(s, pp, ring, nullptr, 0, nullptr, 0, nullptr, 0, &d, vec.err);
+                    } else {
+                        const bool dense = d.flags & kDense;
+                        const uint32_t tb = (uint32_t(d.rows) * d.cols * es + 15u) & ~15u;
+                        const T *x = dense ? vec.xt + int64_t(d.x_node) * mp * nv : vec.xh + int64_t(d.x_node) * kx * nv;
+                        const uint32_t xb = (dense ? mp : kx) * nv * es;
+                        ok = produce(s, pp, ring, op.vals + d.src, tb, x, xb, nullptr, 0, &d, vec.err);
+                    }
+                }
+                slot ^= 1;
+                tA = tB;
+                recA = recB;
+                tB = tC;
+            }
+            if (ok && h2p::mbar_wait(&s.empty[ring.stage], ring.phase ^ 1u, s.abort_flag, vec.err)) {
+                s.desc[ring.stage].flags = kEnd;  // sentinel: completes the stage with no data
+                h2p::mbar_arrive(&s.full[ring.stage]);
+            }
+            drain_on_abort(s, ring);
+        }
+        return;
+    }
+
+    const int tid = threadIdx.x;
+    Acc<T, NVMAX> acc;
+    bool fresh = true;
+    for (;;) {
+        if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
+        const StreamDesc d = s.desc[ring.stage];
+        if (d.flags & kEnd) break;
+        const bool dense = d.flags & kDense;
+        const int xld = dense ? mp : kx;
+        if (fresh) {
+            acc.setup(d.rows, d.rows, tid);
+            acc.zero();
+            fresh = false;
+        }
+        if (!(d.flags & kZero))
+            acc.gemv(stage_tile(s, pp, ring.stage), d.rows, d.rows, d.cols, stage_x(s, pp, ring.stage), xld, nv);
+        release(&s.empty[ring.stage], lane);
+        ring.next();
+        if (d.flags & kLast) {
+            if (acc.reduce(d.rows, nv, s.red)) {
+                T *out = dense ? vec.yd + int64_t(d.out_node) * mp * nv : vec.yh + int64_t(d.out_node) * kx * nv;
+                acc.store(out, xld, nv, d.rows);
+            }
+            h2p::consumer_sync(kConsumers);
+            fresh = true;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ bottom downsweep
+
+template <typename T, int NVMAX>
+__global__ void __launch_bounds__(kThreads) k_down_bottom(Op<T> op, Vec<T> vec, Pipe pp, int64_t nsub)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int L = op.L, sub_nodes = 2 << L;
+    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, sub_nodes, op.kx, false);
+    init_pipe(s, pp);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, Lb = op.Lb;
+    const uint32_t es = sizeof(T);
+    const uint32_t vb = kx * nv * es;  // bytes of one node's coefficient vector
+    Ring ring(pp.ns);
+
+    // every yhat row is defined (empty rows were written as zeros), so each node's own
+    // coupling vector travels with its transfer tile in the second half of the vector slot
+    if (warp == 4) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x) {
+                const int64_t r = (int64_t(1) << Lb) + st;
+                if (Lb >= 1)
+                    ok = produce(s, pp, ring, op.Et + r * k * kx, k * kx * es, vec.yh + (r / 2) * kx * nv, vb,
+                                 vec.yh + r * kx * nv, vb, nullptr, vec.err);
+                else
+                    ok = produce(s, pp, ring, nullptr, 0, nullptr, 0, vec.yh + r * kx * nv, vb, nullptr, vec.err);
+                for (int lev = Lb + 1; ok && lev <= op.q; ++lev) {
+                    const int64_t cnt = int64_t(1) << (lev - Lb);
+                    const int64_t c0 = (int64_t(1) << lev) + st * cnt;
+                    for (int64_t c = c0; ok && c < c0 + cnt; ++c)
+                        ok = produce(s, pp, ring, op.Et + c * k * kx, k * kx * es, nullptr, 0, vec.yh + c * kx * nv,
+                                     vb, nullptr, vec.err);
+                }
+                const int64_t leaf0 = st << L;
+                for (int j = 0; ok && j < (1 << L); ++j) {
+                    const int64_t leaf = leaf0 + j;
+                    ok = produce(s, pp, ring, op.Ut + leaf * kx * mp, k * mp * es, vec.yd + leaf * mp * nv,
+                                 mp * nv * es, nullptr, 0, nullptr, vec.err);
+                }
+            }
+            drain_on_abort(s, ring);
+        }
+        return;
+    }
+
+    const int tid = threadIdx.x;
+    const int wstride = kx * NVMAX;
+    Acc<T, NVMAX> acc;
+    for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x) {
+        // subtree root: E_r yhat_parent + own
+        acc.setup(k, kx, tid);
+        acc.zero();
+        if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
+        if (Lb >= 1) acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, stage_x(s, pp, ring.stage), kx, nv);
+        if (acc.reduce(k, nv, s.red)) {
+            acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
+            acc.store(s.sub + 1 * wstride, kx, nv, k);
+        }
+        release(&s.empty[ring.stage], lane);
+        ring.next();
+        h2p::consumer_sync(kConsumers);
+        for (int lev = Lb + 1; lev <= op.q; ++lev) {
+            const int rel = lev - Lb;
+            const int64_t cnt = int64_t(1) << rel;
+            for (int64_t ci = 0; ci < cnt; ++ci) {
+                const int slot = (1 << rel) + int(ci);
+                acc.zero();
+                if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
+                acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, s.sub + (slot / 2) * wstride, kx, nv);
+                if (acc.reduce(k, nv, s.red)) {
+                    acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
+                    acc.store(s.sub + slot * wstride, kx, nv, k);
+                }
+                release(&s.empty[ring.stage], lane);
+                ring.next();
+                h2p::consumer_sync(kConsumers);
+            }
+        }
+        // leaves: y = U_t yhat_t + yd_t; Y[perm] = alpha y + beta Y
+        const int64_t leaf0 = st << L;
+        for (int j = 0; j < (1 << L); ++j) {
+            const int64_t leaf = leaf0 + j;
+            const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
+            acc.setup(R, mp, tid);
+            acc.zero();
+            // output indices, fetched while the tile is in flight
+            int64_t u[Acc<T, NVMAX>::VEC];
+#pragma unroll
+            for (int e = 0; e < Acc<T, NVMAX>::VEC; ++e)
+                u[e] = (acc.g == 0 && e < acc.per && acc.o0 + e < R) ? op.perm[r0 + acc.o0 + e] : 0;
+            if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
+            acc.gemv(stage_tile(s, pp, ring.stage), mp, R, k, s.sub + ((1 << L) + j) * wstride, kx, nv);
+            if (acc.reduce(R, nv, s.red)) {
+                acc.add(stage_x(s, pp, ring.stage), mp, nv, R);
+#pragma unroll
+                for (int e = 0; e < Acc<T, NVMAX>::VEC; ++e)
+                    if (e < acc.per && acc.o0 + e < R) {
+#pragma unroll
+                        for (int v = 0; v < NVMAX; ++v)
+                            if (v < nv) {
+                                T *dst = vec.Y + int64_t(v) * op.n + u[e];
+                                const T y = acc.a[v][e];
+                                *dst = (vec.beta == T(0)) ? vec.alpha * y : vec.alpha * y + vec.beta * *dst;
+                            }
+                    }
+            }
+            release(&s.empty[ring.stage], lane);
+            ring.next();
+            h2p::consumer_sync(kConsumers);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ top levels
+
+// One upsweep level above the subtrees: xhat_p = sum_c E_c^T xhat_c (direct loads, E as [mu][nu]).
+template <typename T>
+__global__ void k_up_level(Op<T> op, Vec<T> vec, int64_t first_parent, int64_t count)
+{
+    const int k = op.k, kx = op.kx, nv = vec.nv;
+    for (int64_t pi = blockIdx.x; pi < count; pi += gridDim.x) {
+        const int64_t p = first_parent + pi;
+        for (int e = threadIdx.x; e < k * nv; e += blockDim.x) {
+            const int nu = e % k, v = e / k;
+            T acc = 0;
+            for (int c = 0; c < 2; ++c) {
+                const T *Ec = op.E + (2 * p + c) * k * kx + nu;
+                const T *x = vec.xh + (2 * p + c) * kx * nv + v * kx;
+                for (int mu = 0; mu < k; ++mu) acc += Ec[mu * kx] * x[mu];
+            }
+            vec.xh[p * kx * nv + v * kx + nu] = acc;
+        }
+    }
+}
+
+// One downsweep level above the subtrees: yhat_c = E_c yhat_p + yhat_c (E^T as [nu][mu]).
+template <typename T>
+__global__ void k_down_level(Op<T> op, Vec<T> vec, int64_t first_node, int64_t count)
+{
+    const int k = op.k, kx = op.kx, nv = vec.nv;
+    for (int64_t ci = blockIdx.x; ci < count; ci += gridDim.x) {
+        const int64_t c = first_node + ci;
+        for (int e = threadIdx.x; e < k * nv; e += blockDim.x) {
+            const int mu = e % k, v = e / k;
+            T acc = 0;
+            const T *Et = op.Et + c * k * kx + mu;
+            const T *y = vec.yh + (c / 2) * kx * nv + v * kx;
+            for (int nu = 0; nu < k; ++nu) acc += Et[nu * kx] * y[nu];
+            T *dst = vec.yh + c * kx * nv + v * kx + mu;
+            *dst = acc + *dst;
+        }
+    }
+}
+
+}  // namespace h2s
