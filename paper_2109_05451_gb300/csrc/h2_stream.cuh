@@ -253,10 +253,36 @@ struct Acc {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) a[v][e] = T(0);
     }
+    // Square tiles with RC rows = columns = leading dimension, all shapes known at compile
+    // time: fully unrolled, constant offsets (the common case: rank 64 with leaf size 64).
+    template <int RC>
+    __device__ __forceinline__ void gemv_fixed(const T *__restrict__ tile, const T *__restrict__ x, int xld, int nv)
+    {
+        using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        constexpr int LANES = rpad(RC) / VEC, GG = kConsumers / LANES, ITER = RC / GG;
+        const T *tb = tile + g * RC + o0;
+        const T *xb = x + g;
+#pragma unroll
+        for (int i = 0; i < ITER; ++i) {
+            T t[VEC];
+            *reinterpret_cast<VT *>(t) = *reinterpret_cast<const VT *>(tb + i * GG * RC);
+#pragma unroll
+            for (int v = 0; v < NVMAX; ++v)
+                if (v < nv) {
+                    const T xv = xb[v * xld + i * GG];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) a[v][e] += t[e] * xv;
+                }
+        }
+    }
     __device__ __forceinline__ void gemv(const T *__restrict__ tile, int ld, int R, int C, const T *__restrict__ x,
                                          int xld, int nv)
     {
         if (o0 >= R) return;
+        if (R == 64 && C == 64 && ld == 64 && per == VEC) {
+            gemv_fixed<64>(tile, x, xld, nv);
+            return;
+        }
         if (per == VEC) {
             using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
 #pragma unroll 4
