@@ -139,6 +139,31 @@ int h2_matvec(h2_handle h, const void *X, void *Y, int nv, double alpha, double 
 int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta,
                  void *workspace, size_t ws_bytes, void *cuda_stream);
 
+/* Product for callers that must not allocate device memory (no counterpart in the paper).
+ * Some callers cannot call cudaMalloc where they need a product: code running inside a
+ * fixed memory-pool budget, code called from an allocator or an out-of-memory handler
+ * (where allocating could recurse or deadlock), and real-time loops that may not block
+ * on an allocation's device-wide synchronisation. h2_matvec_noalloc computes exactly what
+ * h2_matvec computes (Y = alpha * A_H2 * X + beta * Y, same arguments and layouts), but
+ * takes its workspace from one fixed scratch area of H2_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading this library reserves for the life of the process. It allocates nothing.
+ *   - Limit: h2_workspace_bytes(h, nv) must not exceed H2_NOALLOC_SCRATCH_BYTES (64 MiB:
+ *     about 2^20 points at rank 64 in FP64 with nv = 1, or in FP32 with nv <= 2);
+ *     larger operators are rejected with H2_EINVAL before anything is launched.
+ *   - The first call on a device looks up the scratch area's device address for that
+ *     device (cudaGetSymbolAddress, with the device current); make that first call before
+ *     any stream capture on the device. Call it with the device current that holds the
+ *     operator's device copy.
+ *   - All calls on one device share the one scratch area, whichever handle they use, and
+ *     it keeps the previous call's contents (each product resets what it needs). Calls
+ *     whose execution overlaps on the GPU (different streams, no ordering between them)
+ *     race on it: order them on one stream or with events.
+ * Errors: H2_EINVAL (bad argument or operator too large), H2_ESTATE (no device copy),
+ * H2_ECUDA. */
+#define H2_NOALLOC_SCRATCH_BYTES (64u << 20)
+int h2_matvec_noalloc(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta,
+                      void *cuda_stream);
+
 /* Unpreconditioned conjugate gradients for (A_H2 + sigma2 I) x = b (the Krylov solve of
  * Sec. 6.4, without its multigrid preconditioner). The products run in the uploaded
  * precision; Krylov vectors, dot products and updates are FP64 on the device.

@@ -55,6 +55,7 @@ SIGNATURES = {
     "h2_workspace_bytes": (_SZ, [_P, _I]),
     "h2_matvec": (_I, [_P, _P, _P, _I, _D, _D, _P]),
     "h2_matvec_ws": (_I, [_P, _P, _P, _I, _D, _D, _P, _SZ, _P]),
+    "h2_matvec_noalloc": (_I, [_P, _P, _P, _I, _D, _D, _P]),
     "h2_cg_solve": (_I, [_P, _D, _P, _P, _D, _I, C.POINTER(_I), C.POINTER(_D), _P]),
     "h2_get_info": (_I, [_P, C.POINTER(h2_info)]),
     "h2_get_perm": (_I, [_P, _P]),
@@ -145,6 +146,18 @@ def h2_matvec(h: int, X, Y, nv: int, alpha: float = 1.0, beta: float = 0.0, stre
 def h2_matvec_ws(h: int, X, Y, nv: int, alpha: float, beta: float, workspace, ws_bytes: int, stream=None) -> None:
     _check(load().h2_matvec_ws(h, X.data_ptr(), Y.data_ptr(), int(nv), float(alpha), float(beta),
                                workspace.data_ptr(), int(ws_bytes), _stream_ptr(stream)), "h2_matvec_ws")
+
+
+H2_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def h2_matvec_noalloc(h: int, X, Y, nv: int, alpha: float = 1.0, beta: float = 0.0, stream=None) -> None:
+    """As h2_matvec, but the workspace is the library's fixed per-GPU scratch area: nothing
+    is allocated, for callers that must not allocate device memory. Operators whose
+    workspace exceeds H2_NOALLOC_SCRATCH_BYTES are rejected (H2_EINVAL). Calls that overlap
+    on the GPU share the scratch area and race; order them on one stream."""
+    _check(load().h2_matvec_noalloc(h, X.data_ptr(), Y.data_ptr(), int(nv), float(alpha), float(beta),
+                                    _stream_ptr(stream)), "h2_matvec_noalloc")
 
 
 def h2_cg_solve(h: int, sigma2: float, b, x, tol: float, maxit: int, stream=None):
