@@ -169,8 +169,6 @@ h2s::Op<T> make_op(const h2_op &op, const h2_device &dv)
     o.kx = dv.kx;
     o.mp = dv.mp;
     o.q = op.q;
-    o.Lb = dv.Lb;
-    o.L = dv.L;
     o.perm = dv.perm;
     o.leaf_lo = dv.leaf_lo;
     o.U = static_cast<const T *>(dv.U);
@@ -204,14 +202,21 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     Op<T> o = make_op<T>(op, dv);
     Vec<T> v{X, Y, nv, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd), static_cast<T *>(w.xh),
              static_cast<T *>(w.yh), w.tickets, dv.err};
-    const int sub_nodes = 2 << dv.L;
-    const int64_t nsub = int64_t(1) << dv.Lb;
+    const int Lbot = dv.L, Lb = dv.Lb;
+    const int64_t nsub = int64_t(1) << Lb;
+    // levels per launch above the bottom subtrees: as many as keep the subtree's vectors
+    // within 16 KB of shared memory (at most 5)
+    int Ltop = 1;
+    while (Ltop < 5 && (size_t(4) << Ltop) * kx * NVMAX * es <= 16 * 1024) ++Ltop;
 
-    // shared-memory plans
+    // shared-memory plans: the bottom subtree kernels run two CTAs per SM; the streaming
+    // kernel one CTA per SM, leaving room for one side-stream CTA next to it
     const uint32_t tile_sub = uint32_t(std::max({size_t(mp) * kx, size_t(k) * kx, size_t(k) * mp}) * es);
     const uint32_t x_sub = uint32_t(2 * std::max(mp, kx) * NVMAX * es);  // two vector segments per stage
-    const Pipe p_sub = make_pipe<T, NVMAX>(tile_sub, x_sub, sub_nodes, kx, false, 100 * 1024, 8);
-    const size_t sm_sub = smem_bytes<T, NVMAX>(p_sub, sub_nodes, kx, false);
+    const Pipe p_bsub = make_pipe<T, NVMAX>(tile_sub, x_sub, 2 << Lbot, kx, false, 100 * 1024, 8);
+    const Pipe p_tsub = make_pipe<T, NVMAX>(tile_sub, x_sub, 2 << Ltop, kx, false, 64 * 1024, 4);
+    const size_t sm_bsub = smem_bytes<T, NVMAX>(p_bsub, 2 << Lbot, kx, false);
+    const size_t sm_tsub = smem_bytes<T, NVMAX>(p_tsub, 2 << Ltop, kx, false);
     const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * k, size_t(dv.max_leaf_rows) * dv.max_leaf_rows) *
                                          es) + 15) / 16 * 16);
     const uint32_t x_str = uint32_t(std::max(mp, kx) * NVMAX * es);
@@ -220,27 +225,23 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     const size_t sm_bot = smem_bytes<T, NVMAX>(p_bot, 0, kx, true), sm_top = smem_bytes<T, NVMAX>(p_top, 0, kx, true);
     static bool attr_done = false;  // per template instance
     if (!attr_done) {
-        cudaFuncSetAttribute(k_up_bottom<T, NVMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_down_bottom<T, NVMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_stream<T, NVMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        // ask for the largest shared-memory carveout, so that the side stream's kernels can
-        // still become resident next to the persistent streaming kernel
-        cudaFuncSetAttribute(k_stream<T, NVMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_up_bottom<T, NVMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_down_bottom<T, NVMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+        for (const void *f : {(const void *)k_up_sub<T, NVMAX>, (const void *)k_down_sub<T, NVMAX>,
+                              (const void *)k_stream<T, NVMAX>}) {
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            // the largest shared-memory carveout lets the side stream's kernels become
+            // resident next to the persistent streaming kernel
+            cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        }
         attr_done = true;
     }
-    const int grid_sub = int(std::min<int64_t>(nsub, int64_t(dv.num_sms) * 2));
+    const int grid_bsub = int(std::min<int64_t>(nsub, int64_t(dv.num_sms) * 2));
 
-    // ---- stream A: gather + bottom upsweep
+    // ---- stream A: gather + bottom upsweep (leaf projections and the lowest Lbot levels)
     cudaEvent_t ev = dv.begin(st);
     k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
-    k_up_bottom<T, NVMAX><<<grid_sub, kThreads, sm_sub, st>>>(o, v, p_sub, nsub);
+    k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
     dv.end(0, ev, st, 2);
-    const bool top = dv.Lb >= 1;
+    const bool top = Lb >= 1;
     if (top) {
         cudaEventRecord(dv.ev_up, st);
         cudaStreamWaitEvent(dv.side, dv.ev_up, 0);
@@ -251,25 +252,31 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
         k_stream<T, NVMAX><<<dv.grid_bottom, kThreads, sm_bot, st>>>(o, v, p_bot, dv.desc_bottom, dv.chunks_bottom,
                                                                      dv.n_chunks_bottom, 0);
     dv.end(1, ev, st, dv.n_chunks_bottom > 0 ? 1 : 0);
-    // ---- stream B: top levels
+    // ---- stream B: the levels above the bottom subtrees
     if (top) {
         cudaStream_t sb = dv.side;
         cudaEvent_t eb = dv.begin(sb);
         int launches = 0;
-        for (int lev = dv.Lb; lev >= 1; --lev) {
-            const int64_t cnt = int64_t(1) << (lev - 1);
-            k_up_level<T><<<unsigned(std::min<int64_t>(cnt, 4096)), 64, 0, sb>>>(o, v, cnt, cnt);
+        for (int lin = Lb; lin > 0;) {
+            const int L = std::min(Ltop, lin), lr = lin - L;
+            const int64_t ns = int64_t(1) << lr;
+            k_up_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, sb>>>(
+                o, v, p_tsub, lr, L, ns, 0);
             ++launches;
+            lin = lr;
         }
         if (dv.n_chunks_top > 0) {
             k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
                                                                       dv.n_chunks_top, 1);
             ++launches;
         }
-        for (int lev = 1; lev < dv.Lb; ++lev) {
-            const int64_t cnt = int64_t(1) << lev;
-            k_down_level<T><<<unsigned(std::min<int64_t>(cnt, 4096)), 64, 0, sb>>>(o, v, cnt, cnt);
+        for (int lr = 0; lr <= Lb - 1;) {
+            const int L = std::min(Ltop, Lb - 1 - lr);
+            const int64_t ns = int64_t(1) << lr;
+            k_down_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, sb>>>(
+                o, v, p_tsub, lr, L, ns, 0);
             ++launches;
+            lr += L + 1;
         }
         dv.end(2, eb, sb, launches);
         cudaEventRecord(dv.ev_top, sb);
@@ -277,7 +284,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     }
     // ---- stream A: bottom downsweep + leaf expansion + epilogue
     ev = dv.begin(st);
-    k_down_bottom<T, NVMAX><<<grid_sub, kThreads, sm_sub, st>>>(o, v, p_sub, nsub);
+    k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
     dv.end(3, ev, st, 1);
     return cuda_status(cudaGetLastError());
 }
@@ -469,7 +476,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     dv->n_chunks_bottom = int64_t(pb.size());
     dv->n_chunks_top = int64_t(pt.size());
     dv->grid_bottom = int(std::max<int64_t>(1, std::min<int64_t>(dv->num_sms, dv->n_chunks_bottom)));
-    dv->grid_top = int(std::max<int64_t>(1, std::min<int64_t>(32, dv->n_chunks_top)));
+    dv->grid_top = int(std::max<int64_t>(1, std::min<int64_t>(dv->num_sms, dv->n_chunks_top)));
 
     // ---- arena layout
     size_t off = 0;

@@ -5,16 +5,17 @@
 // thread (warp 4); four consumer warps (128 threads) multiply each tile with a vector
 // segment and reduce in a fixed order (deterministic, no atomics on data).
 //
-//   k_up_bottom   leaf projection xhat^q_t = U_t^T x_t and the lowest L upsweep levels
-//                 xhat^{l-1}_p = sum_c E_c^T xhat^l_c for one CTA-resident subtree of 2^L
-//                 leaves at a time (Sec. 3.1, Alg 1);
+//   k_up_sub      upsweep xhat^{l-1}_p = sum_c E_c^T xhat^l_c over CTA-resident subtrees of a
+//                 few levels, starting from the leaf projections xhat^q_t = U_t^T x_t or from
+//                 a level computed by an earlier launch (Sec. 3.1, Alg 1);
 //   k_stream      block rows of coupling blocks (yhat^l_t = sum_s S_ts xhat^l_s, Sec. 3.2,
 //                 Alg 4) and of dense blocks (A_de x, Sec. 3) from one flat descriptor list,
 //                 handed out to persistent CTAs in chunks of whole rows by an atomic ticket;
 //                 an empty block row is written as zeros, so every yhat row is defined;
-//   k_down_bottom the lowest downsweep levels yhat^l_c = E_c yhat^{l-1}_p + yhat^l_c, the leaf
-//                 expansion y_t = U_t yhat^q_t (Sec. 3.3, Alg 6), the dense partial result and
-//                 the epilogue Y[perm] = alpha y + beta Y, for one subtree at a time.
+//   k_down_sub    downsweep yhat^l_c = E_c yhat^{l-1}_p + yhat^l_c over CTA-resident subtrees
+//                 of a few levels, ending either in a level handed to the next launch or in
+//                 the leaf expansion y_t = U_t yhat^q_t (Sec. 3.3, Alg 6), the dense partial
+//                 result and the epilogue Y[perm] = alpha y + beta Y.
 //
 // Tile layouts (element type T, ld = leading dimension): the consumer always computes
 // out[o] = sum_j tile[j * ld + o] * x[j], so each tile is stored with the output index
@@ -55,7 +56,7 @@ constexpr int16_t kEnd = 8;    // no more work (consumers stop)
 template <typename T>
 struct Op {
     int64_t n, nleaves, first_leaf;
-    int k, kx, mp, q, Lb, L;
+    int k, kx, mp, q;
     const int32_t *perm, *leaf_lo;
     const T *U, *Ut, *E, *Et;
     const unsigned char *vals;
@@ -365,17 +366,23 @@ __global__ void k_gather(Op<T> op, Vec<T> vec)
     }
 }
 
-// ------------------------------------------------------------------ bottom upsweep
+// ------------------------------------------------------------------ subtree upsweep
 
+// Upsweep of subtrees rooted at level Lr with depth L (inputs on level Lr+L). With leaf
+// input (Lr+L = q) the inputs are the leaf projections xhat^q_t = U_t^T x_t; otherwise they
+// are the coefficient vectors of level Lr+L computed by an earlier launch. Writes xhat for
+// levels Lr .. Lr+L (the input level only with leaf input).
 template <typename T, int NVMAX>
-__global__ void __launch_bounds__(kThreads) k_up_bottom(Op<T> op, Vec<T> vec, Pipe pp, int64_t nsub)
+__global__ void __launch_bounds__(kThreads)
+    k_up_sub(Op<T> op, Vec<T> vec, Pipe pp, int Lr, int L, int64_t nsub, int leaf_input)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int L = op.L, sub_nodes = 2 << L;
+    const int sub_nodes = 2 << L;
     Smem<T> s = carve<T, NVMAX>(smem_raw, pp, sub_nodes, op.kx, false);
     init_pipe(s, pp);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv;
+    const int Lin = Lr + L;
     const uint32_t es = sizeof(T);
     Ring ring(pp.ns);
 
@@ -383,14 +390,16 @@ __global__ void __launch_bounds__(kThreads) k_up_bottom(Op<T> op, Vec<T> vec, Pi
         if (lane == 0) {
             bool ok = true;
             for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x) {
-                const int64_t leaf0 = st << L;
-                for (int j = 0; ok && j < (1 << L); ++j) {
-                    const int64_t leaf = leaf0 + j;
-                    ok = produce(s, pp, ring, op.U + leaf * mp * kx, mp * kx * es, vec.xt + leaf * mp * nv,
-                                 mp * nv * es, nullptr, 0, nullptr, vec.err);
+                if (leaf_input) {
+                    const int64_t leaf0 = st << L;
+                    for (int j = 0; ok && j < (1 << L); ++j) {
+                        const int64_t leaf = leaf0 + j;
+                        ok = produce(s, pp, ring, op.U + leaf * mp * kx, mp * kx * es, vec.xt + leaf * mp * nv,
+                                     mp * nv * es, nullptr, 0, nullptr, vec.err);
+                    }
                 }
-                for (int lev = op.q; ok && lev > op.Lb; --lev) {
-                    const int64_t cnt = int64_t(1) << (lev - op.Lb);
+                for (int lev = Lin; ok && lev > Lr; --lev) {
+                    const int64_t cnt = int64_t(1) << (lev - Lr);
                     const int64_t c0 = (int64_t(1) << lev) + st * cnt;
                     for (int64_t c = c0; ok && c < c0 + cnt; ++c)
                         ok = produce(s, pp, ring, op.E + c * k * kx, k * kx * es, nullptr, 0, nullptr, 0, nullptr,
@@ -407,25 +416,35 @@ __global__ void __launch_bounds__(kThreads) k_up_bottom(Op<T> op, Vec<T> vec, Pi
     acc.setup(k, kx, tid);
     const int wstride = kx * NVMAX;
     for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x) {
-        const int64_t leaf0 = st << L;
-        // leaf projections into local slots 2^L + j
-        for (int j = 0; j < (1 << L); ++j) {
-            const int64_t leaf = leaf0 + j;
-            const int R = op.leaf_lo[leaf + 1] - op.leaf_lo[leaf];
-            acc.zero();
-            if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
-            acc.gemv(stage_tile(s, pp, ring.stage), kx, k, R, stage_x(s, pp, ring.stage), mp, nv);
-            release(&s.empty[ring.stage], lane);
-            ring.next();
-            if (acc.reduce(k, nv, s.red)) {
-                acc.store(s.sub + ((1 << L) + j) * wstride, kx, nv, k);
-                acc.store(vec.xh + (op.first_leaf + leaf) * kx * nv, kx, nv, k);
+        if (leaf_input) {
+            // leaf projections into local slots 2^L + j
+            const int64_t leaf0 = st << L;
+            for (int j = 0; j < (1 << L); ++j) {
+                const int64_t leaf = leaf0 + j;
+                const int R = op.leaf_lo[leaf + 1] - op.leaf_lo[leaf];
+                acc.zero();
+                if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
+                acc.gemv(stage_tile(s, pp, ring.stage), kx, k, R, stage_x(s, pp, ring.stage), mp, nv);
+                release(&s.empty[ring.stage], lane);
+                ring.next();
+                if (acc.reduce(k, nv, s.red)) {
+                    acc.store(s.sub + ((1 << L) + j) * wstride, kx, nv, k);
+                    acc.store(vec.xh + (op.first_leaf + leaf) * kx * nv, kx, nv, k);
+                }
+                h2p::consumer_sync(kConsumers);
+            }
+        } else {
+            // input level computed by an earlier launch
+            const int64_t c0 = (int64_t(1) << Lin) + (st << L);
+            for (int e = tid; e < (kx * nv) << L; e += kConsumers) {
+                const int j = e / (kx * nv), r = e % (kx * nv);
+                s.sub[((1 << L) + j) * wstride + r] = vec.xh[(c0 + j) * kx * nv + r];
             }
             h2p::consumer_sync(kConsumers);
         }
         // transfers, level by level
-        for (int lev = op.q; lev > op.Lb; --lev) {
-            const int rel = lev - op.Lb;
+        for (int lev = Lin; lev > Lr; --lev) {
+            const int rel = lev - Lr;
             const int64_t cnt = int64_t(1) << rel;
             for (int64_t pi = 0; pi < cnt / 2; ++pi) {
                 acc.zero();
@@ -546,45 +565,55 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// ------------------------------------------------------------------ bottom downsweep
+// ------------------------------------------------------------------ subtree downsweep
 
+// Downsweep of subtrees rooted at level Lr with depth L: yhat^l_c = E_c yhat^{l-1}_p + own_c
+// for levels Lr .. Lr+L, where own_c is node c's coupling row (every row is defined: empty
+// rows were written as zeros) and the parent total of a root at level Lr >= 1 comes from
+// an earlier launch. With leaf output (Lr+L = q) it finishes with the leaf expansion
+// y_t = U_t yhat^q_t, the dense partial result and Y[perm] = alpha y + beta Y; otherwise it
+// writes the totals of level Lr+L over their coupling rows, for the next launch.
 template <typename T, int NVMAX>
-__global__ void __launch_bounds__(kThreads) k_down_bottom(Op<T> op, Vec<T> vec, Pipe pp, int64_t nsub)
+__global__ void __launch_bounds__(kThreads)
+    k_down_sub(Op<T> op, Vec<T> vec, Pipe pp, int Lr, int L, int64_t nsub, int leaf_output)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int L = op.L, sub_nodes = 2 << L;
+    const int sub_nodes = 2 << L;
     Smem<T> s = carve<T, NVMAX>(smem_raw, pp, sub_nodes, op.kx, false);
     init_pipe(s, pp);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, Lb = op.Lb;
+    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv;
+    const int Lo = Lr + L;
     const uint32_t es = sizeof(T);
     const uint32_t vb = kx * nv * es;  // bytes of one node's coefficient vector
     Ring ring(pp.ns);
 
-    // every yhat row is defined (empty rows were written as zeros), so each node's own
-    // coupling vector travels with its transfer tile in the second half of the vector slot
+    // each node's own coupling vector travels with its transfer tile in the second half of
+    // the stage's vector slot; the root's parent total in the first half
     if (warp == 4) {
         if (lane == 0) {
             bool ok = true;
             for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x) {
-                const int64_t r = (int64_t(1) << Lb) + st;
-                if (Lb >= 1)
+                const int64_t r = (int64_t(1) << Lr) + st;
+                if (Lr >= 1)
                     ok = produce(s, pp, ring, op.Et + r * k * kx, k * kx * es, vec.yh + (r / 2) * kx * nv, vb,
                                  vec.yh + r * kx * nv, vb, nullptr, vec.err);
                 else
                     ok = produce(s, pp, ring, nullptr, 0, nullptr, 0, vec.yh + r * kx * nv, vb, nullptr, vec.err);
-                for (int lev = Lb + 1; ok && lev <= op.q; ++lev) {
-                    const int64_t cnt = int64_t(1) << (lev - Lb);
+                for (int lev = Lr + 1; ok && lev <= Lo; ++lev) {
+                    const int64_t cnt = int64_t(1) << (lev - Lr);
                     const int64_t c0 = (int64_t(1) << lev) + st * cnt;
                     for (int64_t c = c0; ok && c < c0 + cnt; ++c)
                         ok = produce(s, pp, ring, op.Et + c * k * kx, k * kx * es, nullptr, 0, vec.yh + c * kx * nv,
                                      vb, nullptr, vec.err);
                 }
-                const int64_t leaf0 = st << L;
-                for (int j = 0; ok && j < (1 << L); ++j) {
-                    const int64_t leaf = leaf0 + j;
-                    ok = produce(s, pp, ring, op.Ut + leaf * kx * mp, k * mp * es, vec.yd + leaf * mp * nv,
-                                 mp * nv * es, nullptr, 0, nullptr, vec.err);
+                if (leaf_output) {
+                    const int64_t leaf0 = st << L;
+                    for (int j = 0; ok && j < (1 << L); ++j) {
+                        const int64_t leaf = leaf0 + j;
+                        ok = produce(s, pp, ring, op.Ut + leaf * kx * mp, k * mp * es, vec.yd + leaf * mp * nv,
+                                     mp * nv * es, nullptr, 0, nullptr, vec.err);
+                    }
                 }
             }
             drain_on_abort(s, ring);
@@ -600,16 +629,17 @@ __global__ void __launch_bounds__(kThreads) k_down_bottom(Op<T> op, Vec<T> vec, 
         acc.setup(k, kx, tid);
         acc.zero();
         if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
-        if (Lb >= 1) acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, stage_x(s, pp, ring.stage), kx, nv);
+        if (Lr >= 1) acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, stage_x(s, pp, ring.stage), kx, nv);
         if (acc.reduce(k, nv, s.red)) {
             acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
             acc.store(s.sub + 1 * wstride, kx, nv, k);
+            if (L == 0 && !leaf_output) acc.store(vec.yh + ((int64_t(1) << Lr) + st) * kx * nv, kx, nv, k);
         }
         release(&s.empty[ring.stage], lane);
         ring.next();
         h2p::consumer_sync(kConsumers);
-        for (int lev = Lb + 1; lev <= op.q; ++lev) {
-            const int rel = lev - Lb;
+        for (int lev = Lr + 1; lev <= Lo; ++lev) {
+            const int rel = lev - Lr;
             const int64_t cnt = int64_t(1) << rel;
             for (int64_t ci = 0; ci < cnt; ++ci) {
                 const int slot = (1 << rel) + int(ci);
@@ -619,12 +649,15 @@ __global__ void __launch_bounds__(kThreads) k_down_bottom(Op<T> op, Vec<T> vec, 
                 if (acc.reduce(k, nv, s.red)) {
                     acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
                     acc.store(s.sub + slot * wstride, kx, nv, k);
+                    if (lev == Lo && !leaf_output)
+                        acc.store(vec.yh + ((int64_t(1) << lev) + st * cnt + ci) * kx * nv, kx, nv, k);
                 }
                 release(&s.empty[ring.stage], lane);
                 ring.next();
                 h2p::consumer_sync(kConsumers);
             }
         }
+        if (!leaf_output) continue;
         // leaves: y = U_t yhat_t + yd_t; Y[perm] = alpha y + beta Y
         const int64_t leaf0 = st << L;
         for (int j = 0; j < (1 << L); ++j) {
@@ -656,47 +689,6 @@ __global__ void __launch_bounds__(kThreads) k_down_bottom(Op<T> op, Vec<T> vec, 
             release(&s.empty[ring.stage], lane);
             ring.next();
             h2p::consumer_sync(kConsumers);
-        }
-    }
-}
-
-// ------------------------------------------------------------------ top levels
-
-// One upsweep level above the subtrees: xhat_p = sum_c E_c^T xhat_c (direct loads, E as [mu][nu]).
-template <typename T>
-__global__ void k_up_level(Op<T> op, Vec<T> vec, int64_t first_parent, int64_t count)
-{
-    const int k = op.k, kx = op.kx, nv = vec.nv;
-    for (int64_t pi = blockIdx.x; pi < count; pi += gridDim.x) {
-        const int64_t p = first_parent + pi;
-        for (int e = threadIdx.x; e < k * nv; e += blockDim.x) {
-            const int nu = e % k, v = e / k;
-            T acc = 0;
-            for (int c = 0; c < 2; ++c) {
-                const T *Ec = op.E + (2 * p + c) * k * kx + nu;
-                const T *x = vec.xh + (2 * p + c) * kx * nv + v * kx;
-                for (int mu = 0; mu < k; ++mu) acc += Ec[mu * kx] * x[mu];
-            }
-            vec.xh[p * kx * nv + v * kx + nu] = acc;
-        }
-    }
-}
-
-// One downsweep level above the subtrees: yhat_c = E_c yhat_p + yhat_c (E^T as [nu][mu]).
-template <typename T>
-__global__ void k_down_level(Op<T> op, Vec<T> vec, int64_t first_node, int64_t count)
-{
-    const int k = op.k, kx = op.kx, nv = vec.nv;
-    for (int64_t ci = blockIdx.x; ci < count; ci += gridDim.x) {
-        const int64_t c = first_node + ci;
-        for (int e = threadIdx.x; e < k * nv; e += blockDim.x) {
-            const int mu = e % k, v = e / k;
-            T acc = 0;
-            const T *Et = op.Et + c * k * kx + mu;
-            const T *y = vec.yh + (c / 2) * kx * nv + v * kx;
-            for (int nu = 0; nu < k; ++nu) acc += Et[nu * kx] * y[nu];
-            T *dst = vec.yh + c * kx * nv + v * kx + mu;
-            *dst = acc + *dst;
         }
     }
 }
