@@ -114,6 +114,22 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_traffic(grid: int):
+    """DRAM bytes per launch of the streaming kernel from the committed ncu capture, or
+    None when the capture was of another workload or the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_stream_traffic_grid1024_fp32.json")
+    if grid != 1024 or not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for f in rec["source_files"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest()[:16] != rec["source_sha256_16"]:
+        return None
+    return rec["traffic_bytes_per_launch"]
+
+
 def cpu_baseline(steps: int = 0):
     """The oracle (plain FP64 C, 1 thread) on a bounded sample: the same workload family
     at N = 2^16 (256 x 256 grid, same kernel, rank, leaf size and eta), blocks stored."""
@@ -251,10 +267,7 @@ def main():
     cpl_bytes = 4 * (info.coupling_entries + info.dense_entries + 2 * (info.n_nodes + 1) * info.rank + 2 * n)
     cpl_ms = float(res["phase_ms"][1])
     cpl_gbs = cpl_bytes / (cpl_ms * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "coupling_traffic.json")
-    if os.path.exists(prof):
-        traffic = json.load(open(prof)).get("fp32_bytes_per_launch")
+    traffic = kernel_traffic(args.grid)
 
     # end to end through the public API: pinned host X -> device, product, Y -> host
     X = res["X"]
