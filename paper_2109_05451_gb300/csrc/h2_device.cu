@@ -792,12 +792,4 @@ const char *h2_status_str(int status)
     }
 }
 
-int h2_cg_solve(h2_handle h, double sigma2, const double *b, double *x, double tol, int maxit, int *iters,
-                double *true_relres, void *cuda_stream)
-{
-    (void)sigma2; (void)b; (void)x; (void)tol; (void)maxit; (void)iters; (void)true_relres; (void)cuda_stream;
-    if (!h) return H2_EINVAL;
-    return H2_ESTATE;  // provided by the solver module
-}
-
 }  // extern "C"
