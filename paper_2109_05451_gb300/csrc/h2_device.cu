@@ -24,6 +24,7 @@
 #include "h2_internal.h"
 #include "h2_kernels.cuh"
 #include "h2_stream.cuh"
+#include "h2_tcstream.cuh"
 
 namespace {
 
@@ -49,6 +50,7 @@ struct h2_device {
     int64_t kkp = 0;
     int max_leaf_rows = 0;
     bool root_row = false;  // the root has coupling blocks
+    bool tc = false;        // split-BF16 blocks for the tensor-core stream (H2_BF16X2)
     // views into the arena
     int32_t *perm = nullptr, *leaf_lo = nullptr;
     int64_t *cpl_rowptr = nullptr;
@@ -130,12 +132,42 @@ namespace {
 struct Workspace {
     void *xt, *yd, *xh, *yh;
     int *tickets;
+    // tensor-core path (H2_BF16X2): chunked FP32 trees and the split-BF16 vector tiles
+    unsigned char *xb = nullptr, *xtb = nullptr;
+    int64_t xt_chunk = 0, xh_chunk = 0;  // elements between 4-vector chunks
+    int np = 0;                          // padded vectors per pass
 };
+
+constexpr int kTcPass = 64;  // vectors per tensor-core pass
+
+inline int pad16(int x) { return (x + 15) / 16 * 16; }
 
 // Workspace: permuted input and dense result ([leaf][v][mp]), coefficient trees xhat and
 // yhat ([node][v][kx]) for one chunk of at most kChunk vectors, and the scheduling tickets.
 size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, void *base)
 {
+    if (dv.tc) {
+        // per pass of up to kTcPass vectors: nch chunk trees of 4 vectors (FP32) for the
+        // permuted input, the dense result and both coefficient trees, plus the vector tiles
+        const int npass = std::min(nv, kTcPass), nch = (npass + 3) / 4, np = pad16(npass);
+        const int64_t xt_chunk = op.nleaves() * 4 * dv.mp, xh_chunk = (op.nnodes + 1) * 4 * int64_t(dv.kx);
+        const size_t vec = align_up(size_t(nch) * xt_chunk * 4), tree = align_up(size_t(nch) * xh_chunk * 4);
+        const size_t xb = align_up(size_t(op.nnodes + 1) * 2 * np * 128), xtb = align_up(size_t(op.nleaves()) * 2 * np * 128);
+        if (w) {
+            char *p = static_cast<char *>(base);
+            w->xt = p;
+            w->yd = p + vec;
+            w->xh = p + 2 * vec;
+            w->yh = p + 2 * vec + tree;
+            w->xb = reinterpret_cast<unsigned char *>(p + 2 * vec + 2 * tree);
+            w->xtb = w->xb + xb;
+            w->tickets = reinterpret_cast<int *>(w->xtb + xtb);
+            w->xt_chunk = xt_chunk;
+            w->xh_chunk = xh_chunk;
+            w->np = np;
+        }
+        return 2 * vec + 2 * tree + xb + xtb + kAlign;
+    }
     nv = std::min(nv, kChunk);
     const size_t es = dv.esize;
     const size_t vec = align_up(size_t(op.nleaves()) * nv * dv.mp * es);
@@ -200,7 +232,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     const uint32_t es = sizeof(T);
     const int k = op.k, kx = dv.kx, mp = dv.mp;
     Op<T> o = make_op<T>(op, dv);
-    Vec<T> v{X, Y, nv, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd), static_cast<T *>(w.xh),
+    Vec<T> v{X, Y, nv, nv, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd), static_cast<T *>(w.xh),
              static_cast<T *>(w.yh), w.tickets, dv.err};
     const int Lbot = dv.L, Lb = dv.Lb;
     const int64_t nsub = int64_t(1) << Lb;
@@ -289,6 +321,136 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     return cuda_status(cudaGetLastError());
 }
 
+// Tensor-core product (H2_BF16X2): the upsweep and downsweep run in FP32 on the pipelined
+// subtree kernels in chunks of 4 vectors; the coupling and dense rows of every level run in
+// one pass of the tensor-core stream for up to kTcPass vectors.
+template <int NP>
+int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npass, cudaStream_t st)
+{
+    using namespace h2s;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_stream_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_stream_tc<NP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr_done = true;
+    }
+    int ns = 8;
+    while (ns > 2 && tc_smem_bytes(NP, ns) > 200 * 1024) --ns;
+    const int64_t nodes = op.nnodes + 1;
+    const unsigned g1 = unsigned(std::min<int64_t>((nodes * NP * 64 + 255) / 256, 65535));
+    const unsigned g2 = unsigned(std::min<int64_t>((op.nleaves() * NP * 64 + 255) / 256, 65535));
+    k_vec_tiles<NP><<<g1, 256, 0, st>>>(static_cast<const float *>(w.xh), nodes, dv.kx, w.xh_chunk, op.k, npass,
+                                        nullptr, w.xb);
+    k_vec_tiles<NP><<<g2, 256, 0, st>>>(static_cast<const float *>(w.xt), op.nleaves(), dv.mp, w.xt_chunk, 0, npass,
+                                        dv.leaf_lo, w.xtb);
+    TcArgs a;
+    a.vals = dv.vals;
+    a.desc = dv.desc_bottom;
+    a.chunks = dv.chunks_bottom;
+    a.nchunks = dv.n_chunks_bottom;
+    a.xb = w.xb;
+    a.xtb = w.xtb;
+    a.yh = static_cast<float *>(w.yh);
+    a.yd = static_cast<float *>(w.yd);
+    a.nv = npass;
+    a.kx = dv.kx;
+    a.mp = dv.mp;
+    a.yh_chunk = w.xh_chunk;
+    a.yd_chunk = w.xt_chunk;
+    a.ticket = w.tickets + 2;
+    a.err = dv.err;
+    a.ns = ns;
+    if (dv.n_chunks_bottom > 0)
+        k_stream_tc<NP><<<dv.grid_bottom, kTcThreads, tc_smem_bytes(NP, ns), st>>>(a);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_tc(const h2_op &op, h2_device &dv, const float *X, float *Y, int nv, double alpha, double beta,
+              const Workspace &w, cudaStream_t st)
+{
+    using namespace h2s;
+    using T = float;
+    constexpr int NVMAX = kChunk;
+    const int k = op.k, kx = dv.kx, mp = dv.mp;
+    const uint32_t es = 4;
+    const int Lbot = dv.L, Lb = dv.Lb;
+    const int64_t nsub = int64_t(1) << Lb;
+    int Ltop = 1;
+    while (Ltop < 5 && (size_t(4) << Ltop) * kx * NVMAX * es <= 16 * 1024) ++Ltop;
+    const uint32_t tile_sub = uint32_t(std::max({size_t(mp) * kx, size_t(k) * kx, size_t(k) * mp}) * es);
+    const uint32_t x_sub = uint32_t(2 * std::max(mp, kx) * NVMAX * es);
+    const Pipe p_bsub = make_pipe<T, NVMAX>(tile_sub, x_sub, 2 << Lbot, kx, false, 100 * 1024, 8);
+    const Pipe p_tsub = make_pipe<T, NVMAX>(tile_sub, x_sub, 2 << Ltop, kx, false, 100 * 1024, 8);
+    const size_t sm_bsub = smem_bytes<T, NVMAX>(p_bsub, 2 << Lbot, kx, false);
+    const size_t sm_tsub = smem_bytes<T, NVMAX>(p_tsub, 2 << Ltop, kx, false);
+    static bool attr_done = false;
+    if (!attr_done) {
+        for (const void *f : {(const void *)k_up_sub<T, NVMAX>, (const void *)k_down_sub<T, NVMAX>}) {
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        }
+        attr_done = true;
+    }
+    const int grid_bsub = int(std::min<int64_t>(nsub, int64_t(dv.num_sms) * 2));
+    for (int v0 = 0; v0 < nv; v0 += kTcPass) {
+        const int npass = std::min(kTcPass, nv - v0), nch = (npass + 3) / 4;
+        auto chunk_vec = [&](int c) {
+            Vec<T> v{X + size_t(v0 + 4 * c) * op.n, Y + size_t(v0 + 4 * c) * op.n, std::min(4, npass - 4 * c), 4,
+                     T(alpha), T(beta), static_cast<T *>(w.xt) + c * w.xt_chunk,
+                     static_cast<T *>(w.yd) + c * w.xt_chunk, static_cast<T *>(w.xh) + c * w.xh_chunk,
+                     static_cast<T *>(w.yh) + c * w.xh_chunk, w.tickets, dv.err};
+            return v;
+        };
+        const Op<T> o = make_op<T>(op, dv);
+        // upsweep of every chunk
+        cudaEvent_t ev = dv.begin(st);
+        int launches = 0;
+        for (int c = 0; c < nch; ++c) {
+            const Vec<T> v = chunk_vec(c);
+            k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
+            k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
+            launches += 2;
+            for (int lin = Lb; lin > 0;) {
+                const int L = std::min(Ltop, lin), lr = lin - L;
+                const int64_t ns = int64_t(1) << lr;
+                k_up_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, st>>>(
+                    o, v, p_tsub, lr, L, ns, 0);
+                ++launches;
+                lin = lr;
+            }
+        }
+        dv.end(0, ev, st, launches);
+        // tensor-core stream over all coupling rows and dense rows
+        ev = dv.begin(st);
+        const int np = pad16(npass);
+        int rc = np <= 16 ? launch_tc_stream<16>(op, dv, w, npass, st)
+               : np <= 32 ? launch_tc_stream<32>(op, dv, w, npass, st)
+               : np <= 48 ? launch_tc_stream<48>(op, dv, w, npass, st)
+                          : launch_tc_stream<64>(op, dv, w, npass, st);
+        dv.end(1, ev, st, 3);
+        if (rc != H2_OK) return rc;
+        // downsweep + expansion + epilogue of every chunk
+        ev = dv.begin(st);
+        launches = 0;
+        for (int c = 0; c < nch; ++c) {
+            const Vec<T> v = chunk_vec(c);
+            for (int lr = 0; lr <= Lb - 1;) {
+                const int L = std::min(Ltop, Lb - 1 - lr);
+                const int64_t ns = int64_t(1) << lr;
+                k_down_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, st>>>(
+                    o, v, p_tsub, lr, L, ns, 0);
+                ++launches;
+                lr += L + 1;
+            }
+            k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
+            ++launches;
+        }
+        dv.end(3, ev, st, launches);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
 template <typename T>
 int launch_product(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
                    const Workspace &w, cudaStream_t st)
@@ -317,6 +479,21 @@ int generate_blocks(const h2_op &op, h2_device &dv, const int32_t *d_cpl_row, co
         h2k::gen_dense<T><<<unsigned(std::min<int64_t>(ndns, 1 << 20)), 256, 0, st>>>(
             reinterpret_cast<T *>(dv.vals + d_region), d_dns_off, d_dns_row, d_dns_col, ndns, dv.leaf_lo,
             d_pts_tree, op.dim, f);
+    return cuda_status(cudaGetLastError());
+}
+
+int generate_tc_blocks(const h2_op &op, h2_device &dv, const int32_t *d_cpl_row, const int32_t *d_dns_row,
+                       const int32_t *d_dns_col, const int32_t *d_cpl_col, const double *d_cheb, const double *d_pts_tree,
+                       size_t d_region, cudaStream_t st)
+{
+    h2k::KernelFn f{int(op.ker.kind), op.ker.a, op.ker.b, op.ker.deg};
+    const int64_t ncpl = int64_t(op.cpl_col.size()), ndns = int64_t(op.dns_col.size());
+    if (ncpl > 0)
+        h2k::gen_coupling_tc<<<unsigned(std::min<int64_t>(ncpl, 1 << 20)), 256, 0, st>>>(
+            dv.vals, d_cpl_row, d_cpl_col, ncpl, d_cheb, op.dim, op.p, op.k, f);
+    if (ndns > 0)
+        h2k::gen_dense_tc<<<unsigned(std::min<int64_t>(ndns, 1 << 20)), 256, 0, st>>>(
+            dv.vals + d_region, d_dns_row, d_dns_col, ndns, dv.leaf_lo, d_pts_tree, op.dim, f);
     return cuda_status(cudaGetLastError());
 }
 
@@ -371,7 +548,7 @@ extern "C" {
 int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
 {
     if (!h) return H2_EINVAL;
-    if (prec != H2_FP64 && prec != H2_FP32) return H2_EINVAL;  // split-BF16: multi-RHS module
+    if (prec != H2_FP64 && prec != H2_FP32 && prec != H2_BF16X2) return H2_EINVAL;
     h2_op &op = *h;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     h2_device_free(&op);
@@ -381,7 +558,8 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     cudaGetDevice(&dv->device);
     cudaDeviceGetAttribute(&dv->num_sms, cudaDevAttrMultiProcessorCount, dv->device);
     dv->prec = prec;
-    dv->esize = prec == H2_FP64 ? 8 : 4;
+    dv->esize = prec == H2_FP64 ? 8 : 4;  // bases and transfers: FP32 for H2_BF16X2
+    dv->tc = prec == H2_BF16X2;
     const size_t es = dv->esize;
     const int k = op.k;
     const int64_t nleaves = op.nleaves(), first_leaf = op.first_leaf(), ncpl = int64_t(op.cpl_col.size()),
@@ -394,6 +572,10 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     leaf_lo[nleaves] = int32_t(op.n);
     for (int64_t t = 0; t < nleaves; ++t) dv->max_leaf_rows = std::max(dv->max_leaf_rows, leaf_lo[t + 1] - leaf_lo[t]);
     if (dv->max_leaf_rows > kMaxLeaf) {
+        h2_device_free(&op);
+        return H2_EINVAL;
+    }
+    if (dv->tc && (k > 64 || dv->max_leaf_rows > 64)) {  // tensor tiles are 64 x 64
         h2_device_free(&op);
         return H2_EINVAL;
     }
@@ -418,8 +600,9 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
             const int64_t cnt = int64_t(leaf_lo[t + 1] - leaf_lo[t]) * (leaf_lo[s + 1] - leaf_lo[s]);
             dns_off[b + 1] = dns_off[b] + (cnt + 31) / 32 * 32;  // 128-byte aligned blocks
         }
-    const size_t s_bytes = align_up(size_t(ncpl) * dv->kkp * es);
-    const size_t d_bytes = align_up(size_t(dns_off[ndns]) * es);
+    const size_t tcb = h2s::kTcTileBytes;  // split-BF16 tile of one block
+    const size_t s_bytes = dv->tc ? size_t(ncpl) * tcb : align_up(size_t(ncpl) * dv->kkp * es);
+    const size_t d_bytes = dv->tc ? size_t(ndns) * tcb : align_up(size_t(dns_off[ndns]) * es);
 
     // ---- stream descriptors: coupling rows of levels >= Lb and all dense rows (bottom),
     //      coupling rows of levels < Lb (top)
@@ -432,7 +615,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     };
     for (int64_t t = 1; t <= op.nnodes; ++t) {
         const int64_t b0 = op.cpl_rowptr[t], b1 = op.cpl_rowptr[t + 1];
-        const bool is_top = level_of(t) < dv->Lb;
+        const bool is_top = !dv->tc && level_of(t) < dv->Lb;  // tensor path: one stream
         if (b0 == b1) {  // empty block row: its yhat row is written as zeros
             h2s::StreamDesc d{};
             d.out_node = int32_t(t);
@@ -443,14 +626,14 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
         }
         for (int64_t b = b0; b < b1; ++b) {
             h2s::StreamDesc d{};
-            d.src = uint64_t(b) * dv->kkp * es;
+            d.src = dv->tc ? uint64_t(b) * tcb : uint64_t(b) * dv->kkp * es;
             d.x_node = op.cpl_col[b];
             d.out_node = int32_t(t);
             d.rows = int16_t(k);
             d.cols = int16_t(k);
             d.flags = b + 1 == b1 ? h2s::kLast : 0;
             (is_top ? dt : db).push_back(d);
-            (is_top ? bt : bb).push_back(uint64_t(k) * k * es);
+            (is_top ? bt : bb).push_back(dv->tc ? tcb : uint64_t(k) * k * es);
         }
     }
     for (int64_t t = 0; t < nleaves; ++t) {
@@ -458,14 +641,14 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
         for (int64_t b = b0; b < b1; ++b) {
             const int64_t s = op.dns_col[b];
             h2s::StreamDesc d{};
-            d.src = s_bytes + uint64_t(dns_off[b]) * es;
+            d.src = dv->tc ? uint64_t(ncpl + b) * tcb : s_bytes + uint64_t(dns_off[b]) * es;
             d.x_node = int32_t(s);
             d.out_node = int32_t(t);
             d.rows = int16_t(leaf_lo[t + 1] - leaf_lo[t]);
             d.cols = int16_t(leaf_lo[s + 1] - leaf_lo[s]);
             d.flags = h2s::kDense | (b + 1 == b1 ? h2s::kLast : 0);
             db.push_back(d);
-            bb.push_back(uint64_t(d.rows) * d.cols * es);
+            bb.push_back(dv->tc ? tcb : uint64_t(d.rows) * d.cols * es);
         }
     }
     std::vector<int64_t> pb, pt;
@@ -588,8 +771,9 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     cp(d_doff, dns_off.data(), (ndns + 1) * 8);
     if (rc == H2_OK) rc = cuda_status(cudaMemsetAsync(dv->err, 0, 16, st));
     if (rc == H2_OK)
-        rc = es == 8 ? generate_blocks<double>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st)
-                     : generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st);
+        rc = dv->tc ? generate_tc_blocks(op, *dv, d_crow, d_drow, d_dcol, d_ccol, d_cheb, d_pts, s_bytes, st)
+             : es == 8 ? generate_blocks<double>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st)
+                       : generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st);
     if (rc == H2_OK) rc = cuda_status(cudaStreamSynchronize(st));
     cudaFree(tmp);
     if (rc == H2_OK) {
@@ -621,6 +805,8 @@ int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, doub
     ws_layout(*h, dv, nv, &w, workspace);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     dv.products += 1;
+    if (dv.tc)
+        return launch_tc(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w, st);
     if (dv.esize == 8)
         return launch_product<double>(*h, dv, static_cast<const double *>(X), static_cast<double *>(Y), nv, alpha,
                                       beta, w, st);

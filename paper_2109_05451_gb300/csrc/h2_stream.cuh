@@ -66,7 +66,8 @@ template <typename T>
 struct Vec {
     const T *X;
     T *Y;
-    int nv;
+    int nv;  // vectors in this pass
+    int vs;  // vectors per node in the tree layouts (>= nv)
     T alpha, beta;
     T *xt, *yd, *xh, *yh;
     int *tickets;  // [0] bottom stream, [1] top stream (zeroed by k_gather)
@@ -361,7 +362,7 @@ __global__ void k_gather(Op<T> op, Vec<T> vec)
         const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
         for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
             const int i = e % R, v = e / R;
-            vec.xt[(leaf * vec.nv + v) * op.mp + i] = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
+            vec.xt[(leaf * vec.vs + v) * op.mp + i] = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
         }
     }
 }
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(kThreads)
     Smem<T> s = carve<T, NVMAX>(smem_raw, pp, sub_nodes, op.kx, false);
     init_pipe(s, pp);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv;
+    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
     const int Lin = Lr + L;
     const uint32_t es = sizeof(T);
     Ring ring(pp.ns);
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kThreads)
                     const int64_t leaf0 = st << L;
                     for (int j = 0; ok && j < (1 << L); ++j) {
                         const int64_t leaf = leaf0 + j;
-                        ok = produce(s, pp, ring, op.U + leaf * mp * kx, mp * kx * es, vec.xt + leaf * mp * nv,
+                        ok = produce(s, pp, ring, op.U + leaf * mp * kx, mp * kx * es, vec.xt + leaf * mp * vs,
                                      mp * nv * es, nullptr, 0, nullptr, vec.err);
                     }
                 }
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kThreads)
                 ring.next();
                 if (acc.reduce(k, nv, s.red)) {
                     acc.store(s.sub + ((1 << L) + j) * wstride, kx, nv, k);
-                    acc.store(vec.xh + (op.first_leaf + leaf) * kx * nv, kx, nv, k);
+                    acc.store(vec.xh + (op.first_leaf + leaf) * kx * vs, kx, nv, k);
                 }
                 h2p::consumer_sync(kConsumers);
             }
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(kThreads)
             const int64_t c0 = (int64_t(1) << Lin) + (st << L);
             for (int e = tid; e < (kx * nv) << L; e += kConsumers) {
                 const int j = e / (kx * nv), r = e % (kx * nv);
-                s.sub[((1 << L) + j) * wstride + r] = vec.xh[(c0 + j) * kx * nv + r];
+                s.sub[((1 << L) + j) * wstride + r] = vec.xh[(c0 + j) * kx * vs + r];
             }
             h2p::consumer_sync(kConsumers);
         }
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(kThreads)
                     const int pslot = (1 << (rel - 1)) + int(pi);
                     const int64_t par = (int64_t(1) << (lev - 1)) + st * (cnt / 2) + pi;
                     acc.store(s.sub + pslot * wstride, kx, nv, k);
-                    acc.store(vec.xh + par * kx * nv, kx, nv, k);
+                    acc.store(vec.xh + par * kx * vs, kx, nv, k);
                 }
                 h2p::consumer_sync(kConsumers);
             }
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     Smem<T> s = carve<T, NVMAX>(smem_raw, pp, 0, op.kx, true);
     init_pipe(s, pp);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int kx = op.kx, mp = op.mp, nv = vec.nv;
+    const int kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
     const uint32_t es = sizeof(T);
     Ring ring(pp.ns);
 
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {
                         const bool dense = d.flags & kDense;
                         const uint32_t tb = (uint32_t(d.rows) * d.cols * es + 15u) & ~15u;
-                        const T *x = dense ? vec.xt + int64_t(d.x_node) * mp * nv : vec.xh + int64_t(d.x_node) * kx * nv;
+                        const T *x = dense ? vec.xt + int64_t(d.x_node) * mp * vs : vec.xh + int64_t(d.x_node) * kx * vs;
                         const uint32_t xb = (dense ? mp : kx) * nv * es;
                         ok = produce(s, pp, ring, op.vals + d.src, tb, x, xb, nullptr, 0, &d, vec.err);
                     }
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ring.next();
         if (d.flags & kLast) {
             if (acc.reduce(d.rows, nv, s.red)) {
-                T *out = dense ? vec.yd + int64_t(d.out_node) * mp * nv : vec.yh + int64_t(d.out_node) * kx * nv;
+                T *out = dense ? vec.yd + int64_t(d.out_node) * mp * vs : vec.yh + int64_t(d.out_node) * kx * vs;
                 acc.store(out, xld, nv, d.rows);
             }
             h2p::consumer_sync(kConsumers);
@@ -582,7 +583,7 @@ __global__ void __launch_bounds__(kThreads)
     Smem<T> s = carve<T, NVMAX>(smem_raw, pp, sub_nodes, op.kx, false);
     init_pipe(s, pp);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv;
+    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
     const int Lo = Lr + L;
     const uint32_t es = sizeof(T);
     const uint32_t vb = kx * nv * es;  // bytes of one node's coefficient vector
@@ -596,22 +597,22 @@ __global__ void __launch_bounds__(kThreads)
             for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x) {
                 const int64_t r = (int64_t(1) << Lr) + st;
                 if (Lr >= 1)
-                    ok = produce(s, pp, ring, op.Et + r * k * kx, k * kx * es, vec.yh + (r / 2) * kx * nv, vb,
-                                 vec.yh + r * kx * nv, vb, nullptr, vec.err);
+                    ok = produce(s, pp, ring, op.Et + r * k * kx, k * kx * es, vec.yh + (r / 2) * kx * vs, vb,
+                                 vec.yh + r * kx * vs, vb, nullptr, vec.err);
                 else
-                    ok = produce(s, pp, ring, nullptr, 0, nullptr, 0, vec.yh + r * kx * nv, vb, nullptr, vec.err);
+                    ok = produce(s, pp, ring, nullptr, 0, nullptr, 0, vec.yh + r * kx * vs, vb, nullptr, vec.err);
                 for (int lev = Lr + 1; ok && lev <= Lo; ++lev) {
                     const int64_t cnt = int64_t(1) << (lev - Lr);
                     const int64_t c0 = (int64_t(1) << lev) + st * cnt;
                     for (int64_t c = c0; ok && c < c0 + cnt; ++c)
-                        ok = produce(s, pp, ring, op.Et + c * k * kx, k * kx * es, nullptr, 0, vec.yh + c * kx * nv,
+                        ok = produce(s, pp, ring, op.Et + c * k * kx, k * kx * es, nullptr, 0, vec.yh + c * kx * vs,
                                      vb, nullptr, vec.err);
                 }
                 if (leaf_output) {
                     const int64_t leaf0 = st << L;
                     for (int j = 0; ok && j < (1 << L); ++j) {
                         const int64_t leaf = leaf0 + j;
-                        ok = produce(s, pp, ring, op.Ut + leaf * kx * mp, k * mp * es, vec.yd + leaf * mp * nv,
+                        ok = produce(s, pp, ring, op.Ut + leaf * kx * mp, k * mp * es, vec.yd + leaf * mp * vs,
                                      mp * nv * es, nullptr, 0, nullptr, vec.err);
                     }
                 }
@@ -633,7 +634,7 @@ __global__ void __launch_bounds__(kThreads)
         if (acc.reduce(k, nv, s.red)) {
             acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
             acc.store(s.sub + 1 * wstride, kx, nv, k);
-            if (L == 0 && !leaf_output) acc.store(vec.yh + ((int64_t(1) << Lr) + st) * kx * nv, kx, nv, k);
+            if (L == 0 && !leaf_output) acc.store(vec.yh + ((int64_t(1) << Lr) + st) * kx * vs, kx, nv, k);
         }
         release(&s.empty[ring.stage], lane);
         ring.next();
@@ -650,7 +651,7 @@ __global__ void __launch_bounds__(kThreads)
                     acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
                     acc.store(s.sub + slot * wstride, kx, nv, k);
                     if (lev == Lo && !leaf_output)
-                        acc.store(vec.yh + ((int64_t(1) << lev) + st * cnt + ci) * kx * nv, kx, nv, k);
+                        acc.store(vec.yh + ((int64_t(1) << lev) + st * cnt + ci) * kx * vs, kx, nv, k);
                 }
                 release(&s.empty[ring.stage], lane);
                 ring.next();

@@ -1,0 +1,92 @@
+// h2_tc.cuh -- 5th-generation tensor-core (tcgen05) helpers for sm_103a.
+//
+// Operand tiles are K-major bf16 with 64 K-elements (128 bytes) per row in the 128-byte
+// swizzled canonical layout: byte offset o = r*128 + 2k, stored at o ^ (((o >> 7) & 7) << 4)
+// (the 16-byte chunk index is XORed with the row index modulo 8). Eight rows form a 1 KB
+// swizzle atom; tiles start on 1 KB boundaries. The layout is produced in HBM once (blocks at
+// upload, vectors per product), so a 1-D bulk copy lands the exact shared-memory image that
+// the MMA reads.
+//
+// Accumulators live in tensor memory (TMEM). For M = 64 with one CTA, row 16w + i of D is in
+// TMEM lane 32w + i (w = 0..3, i = 0..15): warp w reads rows 16w .. 16w+15 with its lanes 0-15.
+#pragma once
+
+#include <cstdint>
+
+#include "h2_pipe.cuh"
+
+namespace h2t {
+
+__host__ __device__ inline uint32_t sw128_offset(int r, int k)
+{
+    const uint32_t o = uint32_t(r) * 128u + uint32_t(k) * 2u;
+    return o ^ (((o >> 7) & 7u) << 4);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1 KB apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *tile)
+{
+    const uint32_t a = h2p::smem_addr(tile);
+    uint64_t d = uint64_t((a >> 4) & 0x3FFFu);
+    d |= uint64_t(1) << 16;          // leading byte offset (not used by swizzled K-major)
+    d |= uint64_t(1024 >> 4) << 32;  // stride byte offset: 8 rows x 128 bytes
+    d |= uint64_t(1) << 46;          // descriptor version
+    d |= uint64_t(2) << 61;          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: bf16 x bf16 -> fp32, both operands K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(h2p::smem_addr(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T with one K = 16 step; accumulate selects D += vs D =.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on an mbarrier once every earlier tcgen05 operation of this thread has completed.
+__device__ __forceinline__ void commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     h2p::smem_addr(bar))
+                 : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this warp's 32 lanes into v[0..15].
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+}  // namespace h2t

@@ -144,3 +144,52 @@ def test_full_size_grid1024_sampled_leaves(grid1024, prec):
     assert np.all(np.isfinite(got))
     assert relerr(got[rows], ref) <= TOL[prec]
     op.upload("fp32")  # leave the cheaper copy resident for later tests
+
+
+# ---------------------------------------------------------------- split-BF16 tensor-core path
+
+@pytest.mark.parametrize("nv", [1, 7, 32])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_bf16x2_tensor_path_matches_oracle(built, name, nv):
+    """Blocks as bf16 hi + lo, three MMA terms, FP32 accumulation in tensor memory (<= 1e-4)."""
+    pts, ker, orc, op = built(name)
+    op.upload("bf16x2")
+    X = si.gaussian_vectors(len(pts), nv, 2)
+    got = gpu_matvec(op, X, "fp32")
+    assert np.all(np.isfinite(got))
+    assert relerr(got, orc.matvec(X)) <= 1e-4
+
+
+def test_bf16x2_alpha_beta_and_repeatability(built):
+    pts, ker, orc, op = built("cloud3d_k64")
+    op.upload("bf16x2")
+    X = si.gaussian_vectors(len(pts), 20, 3)
+    Y0 = si.gaussian_vectors(len(pts), 20, 4)
+    got = gpu_matvec(op, X, "fp32", 1.5, -0.5, Y0)
+    assert relerr(got, orc.matvec(X, 1.5, -0.5, Y0)) <= 1e-4
+    assert np.array_equal(gpu_matvec(op, X, "fp32", 1.5, -0.5, Y0), got)
+
+
+@pytest.fixture(scope="module")
+def cloud3d_medium():
+    """The 3D multi-RHS workload's distribution at N = 2^17 (uniform cloud, exp(-r/0.2),
+    leaf 64, tri-cubic rank 64, eta 0.7, 32 vectors)."""
+    w = si.cloud3d(2 ** 17)
+    pts = w.make_points()
+    orc = oracle.OracleH2(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    op = h2.H2Operator(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    X = w.make_x(len(pts))
+    rng = np.random.default_rng(5)
+    first = 2 ** orc.depth
+    leaves = np.unique(np.concatenate([[first, orc.nnodes], rng.integers(first, orc.nnodes + 1, 14)]))
+    rows, ref = orc.matvec_leaves(X, leaves)
+    return op, X, rows, ref
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x2", 1e-4), ("fp32", 1e-5)])
+def test_cloud3d_multi_rhs_sampled_leaves(cloud3d_medium, prec, tol):
+    op, X, rows, ref = cloud3d_medium
+    op.upload(prec)
+    got = gpu_matvec(op, X, "fp32")
+    assert np.all(np.isfinite(got))
+    assert relerr(got[rows], ref) <= tol
