@@ -132,55 +132,48 @@ namespace {
 struct Workspace {
     void *xt, *yd, *xh, *yh;
     int *tickets;
-    // tensor-core path (H2_BF16X2): chunked FP32 trees and the split-BF16 vector tiles
+    // tensor-core path (H2_BF16X2): split-BF16 vector tiles of the coefficient tree and of
+    // the permuted input
     unsigned char *xb = nullptr, *xtb = nullptr;
-    int64_t xt_chunk = 0, xh_chunk = 0;  // elements between 4-vector chunks
-    int np = 0;                          // padded vectors per pass
 };
 
-constexpr int kTcPass = 64;  // vectors per tensor-core pass
+constexpr int kWidePass = 32;  // vectors per pass of the wide kernels and of the tensor-core stream
 
 inline int pad16(int x) { return (x + 15) / 16 * 16; }
 
-// Workspace: permuted input and dense result ([leaf][v][mp]), coefficient trees xhat and
-// yhat ([node][v][kx]) for one chunk of at most kChunk vectors, and the scheduling tickets.
+// The wide accumulator holds tiles of at most 64 outputs.
+inline bool wide_ok(const h2_device &dv) { return dv.kx <= 64 && dv.mp <= 64; }
+
+// Vectors per pass: up to kWidePass on the tensor-core path and, for more than kChunk
+// vectors, on the wide kernels; otherwise kChunk.
+inline int pass_vectors(const h2_device &dv, int nv)
+{
+    if (dv.tc || (nv > kChunk && wide_ok(dv))) return std::min(nv, kWidePass);
+    return std::min(nv, kChunk);
+}
+
+// Workspace for one pass of vp vectors: permuted input and dense result ([leaf][v][mp]),
+// coefficient trees xhat and yhat ([node][v][kx]), the split-BF16 vector tiles of the
+// tensor-core path, and the scheduling tickets.
 size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, void *base)
 {
-    if (dv.tc) {
-        // per pass of up to kTcPass vectors: nch chunk trees of 4 vectors (FP32) for the
-        // permuted input, the dense result and both coefficient trees, plus the vector tiles
-        const int npass = std::min(nv, kTcPass), nch = (npass + 3) / 4, np = pad16(npass);
-        const int64_t xt_chunk = op.nleaves() * 4 * dv.mp, xh_chunk = (op.nnodes + 1) * 4 * int64_t(dv.kx);
-        const size_t vec = align_up(size_t(nch) * xt_chunk * 4), tree = align_up(size_t(nch) * xh_chunk * 4);
-        const size_t xb = align_up(size_t(op.nnodes + 1) * 2 * np * 128), xtb = align_up(size_t(op.nleaves()) * 2 * np * 128);
-        if (w) {
-            char *p = static_cast<char *>(base);
-            w->xt = p;
-            w->yd = p + vec;
-            w->xh = p + 2 * vec;
-            w->yh = p + 2 * vec + tree;
-            w->xb = reinterpret_cast<unsigned char *>(p + 2 * vec + 2 * tree);
-            w->xtb = w->xb + xb;
-            w->tickets = reinterpret_cast<int *>(w->xtb + xtb);
-            w->xt_chunk = xt_chunk;
-            w->xh_chunk = xh_chunk;
-            w->np = np;
-        }
-        return 2 * vec + 2 * tree + xb + xtb + kAlign;
-    }
-    nv = std::min(nv, kChunk);
+    const int vp = pass_vectors(dv, nv), np = pad16(vp);
     const size_t es = dv.esize;
-    const size_t vec = align_up(size_t(op.nleaves()) * nv * dv.mp * es);
-    const size_t tree = align_up(size_t(op.nnodes + 1) * nv * dv.kx * es);
+    const size_t vec = align_up(size_t(op.nleaves()) * vp * dv.mp * es);
+    const size_t tree = align_up(size_t(op.nnodes + 1) * vp * dv.kx * es);
+    const size_t xb = dv.tc ? align_up(size_t(op.nnodes + 1) * 2 * np * 128) : 0;
+    const size_t xtb = dv.tc ? align_up(size_t(op.nleaves()) * 2 * np * 128) : 0;
     if (w) {
         char *p = static_cast<char *>(base);
         w->xt = p;
         w->yd = p + vec;
         w->xh = p + 2 * vec;
         w->yh = p + 2 * vec + tree;
-        w->tickets = reinterpret_cast<int *>(p + 2 * vec + 2 * tree);
+        w->xb = dv.tc ? reinterpret_cast<unsigned char *>(p + 2 * vec + 2 * tree) : nullptr;
+        w->xtb = dv.tc ? w->xb + xb : nullptr;
+        w->tickets = reinterpret_cast<int *>(p + 2 * vec + 2 * tree + xb + xtb);
     }
-    return 2 * vec + 2 * tree + kAlign;
+    return 2 * vec + 2 * tree + xb + xtb + kAlign;
 }
 
 int cuda_status(cudaError_t e)
@@ -225,6 +218,21 @@ h2s::Pipe make_pipe(uint32_t tile_bytes, uint32_t x_bytes, int sub_nodes, int kx
 }
 
 template <typename T, int NVMAX>
+void set_kernel_attributes()
+{
+    static bool done = false;  // per template instance
+    if (done) return;
+    for (const void *f : {(const void *)h2s::k_up_sub<T, NVMAX>, (const void *)h2s::k_down_sub<T, NVMAX>,
+                          (const void *)h2s::k_stream<T, NVMAX>}) {
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        // the largest shared-memory carveout lets the side stream's kernels become
+        // resident next to the persistent streaming kernel
+        cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    }
+    done = true;
+}
+
+template <typename T, int NVMAX>
 int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
                  const Workspace &w, cudaStream_t st)
 {
@@ -255,17 +263,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     const Pipe p_bot = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
     const Pipe p_top = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
     const size_t sm_bot = smem_bytes<T, NVMAX>(p_bot, 0, kx, true), sm_top = smem_bytes<T, NVMAX>(p_top, 0, kx, true);
-    static bool attr_done = false;  // per template instance
-    if (!attr_done) {
-        for (const void *f : {(const void *)k_up_sub<T, NVMAX>, (const void *)k_down_sub<T, NVMAX>,
-                              (const void *)k_stream<T, NVMAX>}) {
-            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            // the largest shared-memory carveout lets the side stream's kernels become
-            // resident next to the persistent streaming kernel
-            cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        }
-        attr_done = true;
-    }
+    set_kernel_attributes<T, NVMAX>();
     const int grid_bsub = int(std::min<int64_t>(nsub, int64_t(dv.num_sms) * 2));
 
     // ---- stream A: gather + bottom upsweep (leaf projections and the lowest Lbot levels)
@@ -321,9 +319,139 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     return cuda_status(cudaGetLastError());
 }
 
-// Tensor-core product (H2_BF16X2): the upsweep and downsweep run in FP32 on the pipelined
-// subtree kernels in chunks of 4 vectors; the coupling and dense rows of every level run in
-// one pass of the tensor-core stream for up to kTcPass vectors.
+// ---------------------------------------------------------------- passes of many vectors
+
+// Shared-memory plan of the subtree kernels for one pass width: leaf subtrees of depth Lw
+// (as deep as two CTAs per SM with at least two stages allow, else one CTA per SM), then
+// launches of at most Ltop levels up to the root.
+template <typename T, int NVMAX>
+struct SweepPlan {
+    int Lw = 0, Ltop = 1;
+    h2s::Pipe bsub, tsub;
+    size_t sm_bsub = 0, sm_tsub = 0;
+    int64_t nsub = 1;
+    unsigned grid_bsub = 1;
+};
+
+template <typename T, int NVMAX>
+SweepPlan<T, NVMAX> make_sweep_plan(const h2_op &op, const h2_device &dv)
+{
+    using namespace h2s;
+    SweepPlan<T, NVMAX> sp;
+    const size_t es = sizeof(T);
+    const int k = op.k, kx = dv.kx, mp = dv.mp;
+    while (sp.Ltop < 5 && (size_t(4) << sp.Ltop) * kx * NVMAX * es <= 16 * 1024) ++sp.Ltop;
+    const uint32_t tile = uint32_t(std::max({size_t(mp) * kx, size_t(k) * kx, size_t(k) * mp}) * es);
+    const uint32_t xseg = uint32_t(2 * std::max(mp, kx) * NVMAX * es);
+    size_t budget = 0;
+    for (size_t b : {size_t(100) * 1024, size_t(200) * 1024}) {
+        for (sp.Lw = dv.L; sp.Lw >= 0; --sp.Lw) {
+            const Pipe p = make_pipe<T, NVMAX>(tile, xseg, 2 << sp.Lw, kx, false, b, 8);
+            if (p.ns >= 2 && smem_bytes<T, NVMAX>(p, 2 << sp.Lw, kx, false) <= b) break;
+        }
+        budget = b;
+        if (sp.Lw >= 0) break;
+    }
+    if (sp.Lw < 0) sp.Lw = 0;
+    sp.bsub = make_pipe<T, NVMAX>(tile, xseg, 2 << sp.Lw, kx, false, budget, 8);
+    sp.tsub = make_pipe<T, NVMAX>(tile, xseg, 2 << sp.Ltop, kx, false, 100 * 1024, 8);
+    sp.sm_bsub = smem_bytes<T, NVMAX>(sp.bsub, 2 << sp.Lw, kx, false);
+    sp.sm_tsub = smem_bytes<T, NVMAX>(sp.tsub, 2 << sp.Ltop, kx, false);
+    sp.nsub = int64_t(1) << (op.q - sp.Lw);
+    const int per_sm = sp.sm_bsub <= 100 * 1024 ? 2 : 1;
+    sp.grid_bsub = unsigned(std::min<int64_t>(sp.nsub, int64_t(dv.num_sms) * per_sm));
+    return sp;
+}
+
+template <typename T, int NVMAX>
+unsigned top_grid(const SweepPlan<T, NVMAX> &sp, const h2_device &dv, int64_t ns)
+{
+    const int per_sm = sp.sm_tsub <= 100 * 1024 ? 2 : 1;
+    return unsigned(std::min<int64_t>(ns, int64_t(dv.num_sms) * per_sm));
+}
+
+// Gather + the whole upsweep on one stream: leaf subtrees, then Ltop levels per launch.
+template <typename T, int NVMAX>
+int up_all(const h2_op &op, const h2_device &dv, const h2s::Op<T> &o, const h2s::Vec<T> &v,
+           const SweepPlan<T, NVMAX> &sp, cudaStream_t st)
+{
+    using namespace h2s;
+    k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
+    k_up_sub<T, NVMAX><<<sp.grid_bsub, kThreads, sp.sm_bsub, st>>>(o, v, sp.bsub, op.q - sp.Lw, sp.Lw, sp.nsub, 1);
+    int launches = 2;
+    for (int lin = op.q - sp.Lw; lin > 0;) {
+        const int L = std::min(sp.Ltop, lin), lr = lin - L;
+        const int64_t ns = int64_t(1) << lr;
+        k_up_sub<T, NVMAX><<<top_grid(sp, dv, ns), kThreads, sp.sm_tsub, st>>>(o, v, sp.tsub, lr, L, ns, 0);
+        ++launches;
+        lin = lr;
+    }
+    return launches;
+}
+
+// The whole downsweep on one stream, ending in the leaf expansion and the epilogue.
+template <typename T, int NVMAX>
+int down_all(const h2_op &op, const h2_device &dv, const h2s::Op<T> &o, const h2s::Vec<T> &v,
+             const SweepPlan<T, NVMAX> &sp, cudaStream_t st)
+{
+    using namespace h2s;
+    int launches = 0;
+    const int Lr0 = op.q - sp.Lw;
+    for (int lr = 0; lr <= Lr0 - 1;) {
+        const int L = std::min(sp.Ltop, Lr0 - 1 - lr);
+        const int64_t ns = int64_t(1) << lr;
+        k_down_sub<T, NVMAX><<<top_grid(sp, dv, ns), kThreads, sp.sm_tsub, st>>>(o, v, sp.tsub, lr, L, ns, 0);
+        ++launches;
+        lr += L + 1;
+    }
+    k_down_sub<T, NVMAX><<<sp.grid_bsub, kThreads, sp.sm_bsub, st>>>(o, v, sp.bsub, Lr0, sp.Lw, sp.nsub, 1);
+    return launches + 1;
+}
+
+// One pass of 8 < nv <= NVMAX vectors on the wide kernels, all on one stream: upsweep,
+// coupling and dense rows of every level (bottom, then top descriptor list), downsweep.
+template <typename T, int NVMAX>
+int launch_wide(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
+                const Workspace &w, cudaStream_t st)
+{
+    using namespace h2s;
+    const uint32_t es = sizeof(T);
+    const int k = op.k, kx = dv.kx, mp = dv.mp;
+    const Op<T> o = make_op<T>(op, dv);
+    const Vec<T> v{X, Y, nv, nv, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd),
+                   static_cast<T *>(w.xh), static_cast<T *>(w.yh), w.tickets, dv.err};
+    const SweepPlan<T, NVMAX> sp = make_sweep_plan<T, NVMAX>(op, dv);
+    const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * k, size_t(dv.max_leaf_rows) * dv.max_leaf_rows) *
+                                         es) + 15) / 16 * 16);
+    const uint32_t x_str = uint32_t(std::max(mp, kx) * NVMAX * es);
+    const Pipe p_str = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 200 * 1024, 12);
+    const size_t sm_str = smem_bytes<T, NVMAX>(p_str, 0, kx, true);
+    set_kernel_attributes<T, NVMAX>();
+
+    cudaEvent_t ev = dv.begin(st);
+    const int lu = up_all(op, dv, o, v, sp, st);
+    dv.end(0, ev, st, lu);
+    ev = dv.begin(st);
+    int ls = 0;
+    if (dv.n_chunks_bottom > 0) {
+        k_stream<T, NVMAX><<<dv.grid_bottom, kThreads, sm_str, st>>>(o, v, p_str, dv.desc_bottom, dv.chunks_bottom,
+                                                                     dv.n_chunks_bottom, 0);
+        ++ls;
+    }
+    if (dv.n_chunks_top > 0) {
+        k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_str, st>>>(o, v, p_str, dv.desc_top, dv.chunks_top,
+                                                                  dv.n_chunks_top, 1);
+        ++ls;
+    }
+    dv.end(1, ev, st, ls);
+    ev = dv.begin(st);
+    const int ld = down_all(op, dv, o, v, sp, st);
+    dv.end(3, ev, st, ld);
+    return cuda_status(cudaGetLastError());
+}
+
+// Tensor-core stream of one pass (H2_BF16X2): split-BF16 tiles of the input vectors, then
+// the coupling and dense rows of every level; NP = vectors padded to a multiple of 16.
 template <int NP>
 int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npass, cudaStream_t st)
 {
@@ -340,10 +468,9 @@ int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npa
     const int64_t nodes = op.nnodes + 1;
     const unsigned g1 = unsigned(std::min<int64_t>((nodes * NP * 64 + 255) / 256, 65535));
     const unsigned g2 = unsigned(std::min<int64_t>((op.nleaves() * NP * 64 + 255) / 256, 65535));
-    k_vec_tiles<NP><<<g1, 256, 0, st>>>(static_cast<const float *>(w.xh), nodes, dv.kx, w.xh_chunk, op.k, npass,
-                                        nullptr, w.xb);
-    k_vec_tiles<NP><<<g2, 256, 0, st>>>(static_cast<const float *>(w.xt), op.nleaves(), dv.mp, w.xt_chunk, 0, npass,
-                                        dv.leaf_lo, w.xtb);
+    k_vec_tiles<NP><<<g1, 256, 0, st>>>(static_cast<const float *>(w.xh), nodes, dv.kx, npass, op.k, nullptr, w.xb);
+    k_vec_tiles<NP><<<g2, 256, 0, st>>>(static_cast<const float *>(w.xt), op.nleaves(), dv.mp, npass, 0, dv.leaf_lo,
+                                        w.xtb);
     TcArgs a;
     a.vals = dv.vals;
     a.desc = dv.desc_bottom;
@@ -356,8 +483,6 @@ int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npa
     a.nv = npass;
     a.kx = dv.kx;
     a.mp = dv.mp;
-    a.yh_chunk = w.xh_chunk;
-    a.yd_chunk = w.xt_chunk;
     a.ticket = w.tickets + 2;
     a.err = dv.err;
     a.ns = ns;
@@ -366,100 +491,62 @@ int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npa
     return cuda_status(cudaGetLastError());
 }
 
-int launch_tc(const h2_op &op, h2_device &dv, const float *X, float *Y, int nv, double alpha, double beta,
-              const Workspace &w, cudaStream_t st)
+// Tensor-core product (H2_BF16X2), per pass of up to kWidePass vectors: FP32 upsweep on the
+// subtree kernels, the coupling and dense rows of every level on the tensor-core stream,
+// FP32 downsweep with the leaf expansion and the epilogue.
+template <int NVMAX>
+int launch_tc_pass(const h2_op &op, h2_device &dv, const float *X, float *Y, int npass, double alpha, double beta,
+                   const Workspace &w, cudaStream_t st)
 {
     using namespace h2s;
     using T = float;
-    constexpr int NVMAX = kChunk;
-    const int k = op.k, kx = dv.kx, mp = dv.mp;
-    const uint32_t es = 4;
-    const int Lbot = dv.L, Lb = dv.Lb;
-    const int64_t nsub = int64_t(1) << Lb;
-    int Ltop = 1;
-    while (Ltop < 5 && (size_t(4) << Ltop) * kx * NVMAX * es <= 16 * 1024) ++Ltop;
-    const uint32_t tile_sub = uint32_t(std::max({size_t(mp) * kx, size_t(k) * kx, size_t(k) * mp}) * es);
-    const uint32_t x_sub = uint32_t(2 * std::max(mp, kx) * NVMAX * es);
-    const Pipe p_bsub = make_pipe<T, NVMAX>(tile_sub, x_sub, 2 << Lbot, kx, false, 100 * 1024, 8);
-    const Pipe p_tsub = make_pipe<T, NVMAX>(tile_sub, x_sub, 2 << Ltop, kx, false, 100 * 1024, 8);
-    const size_t sm_bsub = smem_bytes<T, NVMAX>(p_bsub, 2 << Lbot, kx, false);
-    const size_t sm_tsub = smem_bytes<T, NVMAX>(p_tsub, 2 << Ltop, kx, false);
-    static bool attr_done = false;
-    if (!attr_done) {
-        for (const void *f : {(const void *)k_up_sub<T, NVMAX>, (const void *)k_down_sub<T, NVMAX>}) {
-            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        }
-        attr_done = true;
-    }
-    const int grid_bsub = int(std::min<int64_t>(nsub, int64_t(dv.num_sms) * 2));
-    for (int v0 = 0; v0 < nv; v0 += kTcPass) {
-        const int npass = std::min(kTcPass, nv - v0), nch = (npass + 3) / 4;
-        auto chunk_vec = [&](int c) {
-            Vec<T> v{X + size_t(v0 + 4 * c) * op.n, Y + size_t(v0 + 4 * c) * op.n, std::min(4, npass - 4 * c), 4,
-                     T(alpha), T(beta), static_cast<T *>(w.xt) + c * w.xt_chunk,
-                     static_cast<T *>(w.yd) + c * w.xt_chunk, static_cast<T *>(w.xh) + c * w.xh_chunk,
-                     static_cast<T *>(w.yh) + c * w.xh_chunk, w.tickets, dv.err};
-            return v;
-        };
-        const Op<T> o = make_op<T>(op, dv);
-        // upsweep of every chunk
-        cudaEvent_t ev = dv.begin(st);
-        int launches = 0;
-        for (int c = 0; c < nch; ++c) {
-            const Vec<T> v = chunk_vec(c);
-            k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
-            k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
-            launches += 2;
-            for (int lin = Lb; lin > 0;) {
-                const int L = std::min(Ltop, lin), lr = lin - L;
-                const int64_t ns = int64_t(1) << lr;
-                k_up_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, st>>>(
-                    o, v, p_tsub, lr, L, ns, 0);
-                ++launches;
-                lin = lr;
-            }
-        }
-        dv.end(0, ev, st, launches);
-        // tensor-core stream over all coupling rows and dense rows
-        ev = dv.begin(st);
-        const int np = pad16(npass);
-        int rc = np <= 16 ? launch_tc_stream<16>(op, dv, w, npass, st)
-               : np <= 32 ? launch_tc_stream<32>(op, dv, w, npass, st)
-               : np <= 48 ? launch_tc_stream<48>(op, dv, w, npass, st)
-                          : launch_tc_stream<64>(op, dv, w, npass, st);
-        dv.end(1, ev, st, 3);
-        if (rc != H2_OK) return rc;
-        // downsweep + expansion + epilogue of every chunk
-        ev = dv.begin(st);
-        launches = 0;
-        for (int c = 0; c < nch; ++c) {
-            const Vec<T> v = chunk_vec(c);
-            for (int lr = 0; lr <= Lb - 1;) {
-                const int L = std::min(Ltop, Lb - 1 - lr);
-                const int64_t ns = int64_t(1) << lr;
-                k_down_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, st>>>(
-                    o, v, p_tsub, lr, L, ns, 0);
-                ++launches;
-                lr += L + 1;
-            }
-            k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
-            ++launches;
-        }
-        dv.end(3, ev, st, launches);
-    }
+    const Op<T> o = make_op<T>(op, dv);
+    const Vec<T> v{X, Y, npass, npass, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd),
+                   static_cast<T *>(w.xh), static_cast<T *>(w.yh), w.tickets, dv.err};
+    const SweepPlan<T, NVMAX> sp = make_sweep_plan<T, NVMAX>(op, dv);
+    set_kernel_attributes<T, NVMAX>();
+    cudaEvent_t ev = dv.begin(st);
+    const int lu = up_all(op, dv, o, v, sp, st);
+    dv.end(0, ev, st, lu);
+    ev = dv.begin(st);
+    const int rc = pad16(npass) <= 16 ? launch_tc_stream<16>(op, dv, w, npass, st)
+                                      : launch_tc_stream<32>(op, dv, w, npass, st);
+    dv.end(1, ev, st, 3);
+    if (rc != H2_OK) return rc;
+    ev = dv.begin(st);
+    const int ld = down_all(op, dv, o, v, sp, st);
+    dv.end(3, ev, st, ld);
     return cuda_status(cudaGetLastError());
+}
+
+int launch_tc(const h2_op &op, h2_device &dv, const float *X, float *Y, int nv, double alpha, double beta,
+              const Workspace &w, cudaStream_t st)
+{
+    for (int v0 = 0; v0 < nv; v0 += kWidePass) {
+        const int c = std::min(kWidePass, nv - v0);
+        const size_t o = size_t(v0) * op.n;
+        const int rc = c <= kChunk ? launch_tc_pass<kChunk>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                     : c <= 8      ? launch_tc_pass<8>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                     : c <= 16     ? launch_tc_pass<16>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                                   : launch_tc_pass<32>(op, dv, X + o, Y + o, c, alpha, beta, w, st);
+        if (rc != H2_OK) return rc;
+    }
+    return H2_OK;
 }
 
 template <typename T>
 int launch_product(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
                    const Workspace &w, cudaStream_t st)
 {
-    for (int v0 = 0; v0 < nv; v0 += kChunk) {
-        const int c = std::min(kChunk, nv - v0);
+    const int vp = pass_vectors(dv, nv);
+    for (int v0 = 0; v0 < nv; v0 += vp) {
+        const int c = std::min(vp, nv - v0);
         const size_t o = size_t(v0) * op.n;
-        const int rc = c == 1 ? launch_chunk<T, 1>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
-                              : launch_chunk<T, kChunk>(op, dv, X + o, Y + o, c, alpha, beta, w, st);
+        const int rc = c == 1       ? launch_chunk<T, 1>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                     : c <= kChunk  ? launch_chunk<T, kChunk>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                     : c <= 8       ? launch_wide<T, 8>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                     : c <= 16      ? launch_wide<T, 16>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                                    : launch_wide<T, 32>(op, dv, X + o, Y + o, c, alpha, beta, w, st);
         if (rc != H2_OK) return rc;
     }
     return H2_OK;

@@ -93,13 +93,23 @@ struct Smem {
     int *abort_flag;
 };
 
+// Vectors per pass from which the wide accumulator (AccW) replaces the group-reduced one.
+constexpr int kWideMin = 8;
+
+// Elements of the column-group exchange buffer per vector (the wide accumulator has none).
+template <int NVMAX>
+__host__ __device__ constexpr int red_elems()
+{
+    return NVMAX >= kWideMin ? 0 : kRedElems;
+}
+
 template <typename T, int NVMAX>
 __host__ __device__ inline size_t smem_bytes(const Pipe &p, int sub_nodes, int kx, bool chunks)
 {
     size_t b = size_t(p.ns) * (p.tile_bytes + p.x_bytes);
     b += size_t(p.ns) * sizeof(StreamDesc);
     b += size_t(2 * p.ns) * sizeof(uint64_t);
-    b += size_t(kRedElems) * NVMAX * sizeof(T);
+    b += size_t(red_elems<NVMAX>()) * NVMAX * sizeof(T);
     b += size_t(sub_nodes) * kx * NVMAX * sizeof(T);
     if (chunks) b += 2 * kChunkDesc * sizeof(StreamDesc) + 2 * sizeof(uint64_t);
     b += 16;
@@ -121,7 +131,7 @@ __device__ inline Smem<T> carve(unsigned char *base, const Pipe &p, int sub_node
     s.empty = s.full + p.ns;
     c += size_t(2 * p.ns) * sizeof(uint64_t);
     s.red = reinterpret_cast<T *>(c);
-    c += size_t(kRedElems) * NVMAX * sizeof(T);
+    c += size_t(red_elems<NVMAX>()) * NVMAX * sizeof(T);
     s.sub = reinterpret_cast<T *>(c);
     c += size_t(sub_nodes) * kx * NVMAX * sizeof(T);
     s.dbuf = nullptr;
@@ -348,7 +358,189 @@ struct Acc {
             for (int e = 0; e < VEC; ++e)
                 if (v < nv && e < per && o0 + e < R) a[v][e] += src[v * ld + o0 + e];
     }
+    // Leaf epilogue: user-order rows of the held outputs (fetched before the tile arrives),
+    // then Y[v*n + row] = alpha y + beta Y for the threads holding final values.
+    int64_t u[VEC];
+    __device__ __forceinline__ void fetch_rows(const int32_t *perm, int r0, int R)
+    {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) u[e] = (g == 0 && e < per && o0 + e < R) ? perm[r0 + o0 + e] : 0;
+    }
+    __device__ __forceinline__ void write_out(T *Y, int64_t n, T alpha, T beta, int nv, int R) const
+    {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (e < per && o0 + e < R) {
+#pragma unroll
+                for (int v = 0; v < NVMAX; ++v)
+                    if (v < nv) {
+                        T *dst = Y + int64_t(v) * n + u[e];
+                        const T y = a[v][e];
+                        *dst = (beta == T(0)) ? alpha * y : alpha * y + beta * *dst;
+                    }
+            }
+    }
 };
+
+// Wide accumulator for passes of NV >= 8 vectors and tiles of at most 64 outputs: thread
+// (og, vg) = (tid % 16, tid / 16) owns outputs o0 .. o0+3 (o0 = 4 og) of vectors
+// v0 .. v0+VT-1 (v0 = VT vg, VT = NV / 8), a 4 x VT register block of the 64 x NV result.
+// Each column step j reads four tile entries and VT vector entries; with 16-byte aligned
+// rows four steps are read at once (16-byte loads along j for the vectors), so every loaded
+// value feeds 4 or VT fused multiply-adds. Each thread sums its columns in ascending order;
+// there is no cross-thread reduction, and the result is deterministic.
+template <typename T, int NV>
+struct AccW {
+    static constexpr int VT = NV / 8;
+    static constexpr int VEC = 4;
+    static_assert(NV % 8 == 0 && NV >= 8, "wide accumulator: NV is a multiple of 8");
+    T a[VT][4];
+    int o0, v0;
+    int64_t u[4];
+
+    __device__ __forceinline__ void setup(int /*R*/, int /*ld*/, int tid)
+    {
+        o0 = (tid & 15) * 4;
+        v0 = (tid >> 4) * VT;
+    }
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int v = 0; v < VT; ++v)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) a[v][e] = T(0);
+    }
+    __device__ static __forceinline__ void load4(T (&d)[4], const T *p)
+    {
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(d) = *reinterpret_cast<const float4 *>(p);
+        } else {
+            *reinterpret_cast<double2 *>(d) = *reinterpret_cast<const double2 *>(p);
+            *reinterpret_cast<double2 *>(d + 2) = *reinterpret_cast<const double2 *>(p + 2);
+        }
+    }
+    __device__ static __forceinline__ void store4(T *p, const T (&d)[4])
+    {
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(p) = *reinterpret_cast<const float4 *>(d);
+        } else {
+            *reinterpret_cast<double2 *>(p) = *reinterpret_cast<const double2 *>(d);
+            *reinterpret_cast<double2 *>(p + 2) = *reinterpret_cast<const double2 *>(d + 2);
+        }
+    }
+    // Columns j0 .. j0+3 with 16-byte aligned tile rows and vector segments.
+    __device__ __forceinline__ void step4(const T *__restrict__ tb, int ld, const T *__restrict__ xb, int xld)
+    {
+        T xv[VT][4];
+#pragma unroll
+        for (int v = 0; v < VT; ++v) load4(xv[v], xb + v * xld);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            T t[4];
+            load4(t, tb + jj * ld);
+#pragma unroll
+            for (int v = 0; v < VT; ++v)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) a[v][e] += t[e] * xv[v][jj];
+        }
+    }
+    // out[o][v] += sum_{j < C} tile[j*ld + o] * x[v*xld + j] for o < R, v < nv.
+    __device__ __forceinline__ void gemv(const T *__restrict__ tile, int ld, int R, int C, const T *__restrict__ x,
+                                         int xld, int nv)
+    {
+        if (o0 >= R || v0 >= nv) return;
+        const T *tb = tile + o0;
+        const T *xb = x + v0 * xld;
+        if (ld == 64 && xld == 64 && C == 64) {  // the common square tile: constant offsets
+#pragma unroll
+            for (int j = 0; j < 64; j += 4) step4(tb + j * 64, 64, xb + j, 64);
+            return;
+        }
+        if ((ld & 3) == 0 && (xld & 3) == 0 && o0 + 4 <= R) {
+            int j = 0;
+#pragma unroll 2
+            for (; j + 4 <= C; j += 4) step4(tb + j * ld, ld, xb + j, xld);
+            for (; j < C; ++j) {
+                T t[4];
+                load4(t, tb + j * ld);
+#pragma unroll
+                for (int v = 0; v < VT; ++v) {
+                    const T xs = xb[v * xld + j];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) a[v][e] += t[e] * xs;
+                }
+            }
+            return;
+        }
+        for (int j = 0; j < C; ++j) {  // unaligned rows or a ragged last output group
+            T t[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) t[e] = o0 + e < R ? tb[j * ld + e] : T(0);
+#pragma unroll
+            for (int v = 0; v < VT; ++v) {
+                const T xs = xb[v * xld + j];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) a[v][e] += t[e] * xs;
+            }
+        }
+    }
+    __device__ __forceinline__ bool reduce(int R, int nv, T * /*red*/) const { return o0 < R && v0 < nv; }
+    __device__ __forceinline__ void store(T *dst, int ld, int nv, int R) const
+    {
+        const bool vec = (ld & 3) == 0 && o0 + 4 <= R;
+#pragma unroll
+        for (int v = 0; v < VT; ++v) {
+            if (v0 + v >= nv) break;
+            T *d = dst + (v0 + v) * ld + o0;
+            if (vec) {
+                store4(d, a[v]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (o0 + e < R) d[e] = a[v][e];
+            }
+        }
+    }
+    __device__ __forceinline__ void add(const T *src, int ld, int nv, int R)
+    {
+        const bool vec = (ld & 3) == 0 && o0 + 4 <= R;
+#pragma unroll
+        for (int v = 0; v < VT; ++v) {
+            if (v0 + v >= nv) break;
+            const T *p = src + (v0 + v) * ld + o0;
+            T s[4];
+            if (vec) {
+                load4(s, p);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) s[e] = o0 + e < R ? p[e] : T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) a[v][e] += s[e];
+        }
+    }
+    __device__ __forceinline__ void fetch_rows(const int32_t *perm, int r0, int R)
+    {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) u[e] = o0 + e < R ? perm[r0 + o0 + e] : 0;
+    }
+    __device__ __forceinline__ void write_out(T *Y, int64_t n, T alpha, T beta, int nv, int R) const
+    {
+#pragma unroll
+        for (int v = 0; v < VT; ++v)
+            if (v0 + v < nv)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (o0 + e < R) {
+                        T *dst = Y + int64_t(v0 + v) * n + u[e];
+                        const T y = a[v][e];
+                        *dst = (beta == T(0)) ? alpha * y : alpha * y + beta * *dst;
+                    }
+    }
+};
+
+template <typename T, int NVMAX>
+using AccOf = typename std::conditional<(NVMAX >= kWideMin), AccW<T, NVMAX>, Acc<T, NVMAX>>::type;
 
 // ------------------------------------------------------------------ gather
 
@@ -413,7 +605,7 @@ __global__ void __launch_bounds__(kThreads)
     }
 
     const int tid = threadIdx.x;
-    Acc<T, NVMAX> acc;
+    AccOf<T, NVMAX> acc;
     acc.setup(k, kx, tid);
     const int wstride = kx * NVMAX;
     for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x) {
@@ -538,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     const int tid = threadIdx.x;
-    Acc<T, NVMAX> acc;
+    AccOf<T, NVMAX> acc;
     bool fresh = true;
     for (;;) {
         if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
@@ -624,7 +816,7 @@ __global__ void __launch_bounds__(kThreads)
 
     const int tid = threadIdx.x;
     const int wstride = kx * NVMAX;
-    Acc<T, NVMAX> acc;
+    AccOf<T, NVMAX> acc;
     for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x) {
         // subtree root: E_r yhat_parent + own
         acc.setup(k, kx, tid);
@@ -666,26 +858,12 @@ __global__ void __launch_bounds__(kThreads)
             const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
             acc.setup(R, mp, tid);
             acc.zero();
-            // output indices, fetched while the tile is in flight
-            int64_t u[Acc<T, NVMAX>::VEC];
-#pragma unroll
-            for (int e = 0; e < Acc<T, NVMAX>::VEC; ++e)
-                u[e] = (acc.g == 0 && e < acc.per && acc.o0 + e < R) ? op.perm[r0 + acc.o0 + e] : 0;
+            acc.fetch_rows(op.perm, r0, R);  // output rows, fetched while the tile is in flight
             if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
             acc.gemv(stage_tile(s, pp, ring.stage), mp, R, k, s.sub + ((1 << L) + j) * wstride, kx, nv);
             if (acc.reduce(R, nv, s.red)) {
                 acc.add(stage_x(s, pp, ring.stage), mp, nv, R);
-#pragma unroll
-                for (int e = 0; e < Acc<T, NVMAX>::VEC; ++e)
-                    if (e < acc.per && acc.o0 + e < R) {
-#pragma unroll
-                        for (int v = 0; v < NVMAX; ++v)
-                            if (v < nv) {
-                                T *dst = vec.Y + int64_t(v) * op.n + u[e];
-                                const T y = acc.a[v][e];
-                                *dst = (vec.beta == T(0)) ? vec.alpha * y : vec.alpha * y + vec.beta * *dst;
-                            }
-                    }
+                acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
             }
             release(&s.empty[ring.stage], lane);
             ring.next();

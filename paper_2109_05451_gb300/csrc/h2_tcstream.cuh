@@ -34,10 +34,9 @@ struct TcArgs {
     int64_t nchunks;
     const unsigned char *xb;         // input vector tiles of the coefficient tree, per node
     const unsigned char *xtb;        // input vector tiles of the permuted input, per leaf
-    float *yh, *yd;                  // FP32 output trees (chunked layouts, see ystride)
+    float *yh, *yd;                  // FP32 output trees: (node, v, i) at (node*nv + v)*ld + i
     int nv;                          // vectors
-    int kx, mp;                      // row strides of yh / yd rows
-    int64_t yh_chunk, yd_chunk;      // elements between 4-vector chunks of the output trees
+    int kx, mp;                      // ld of yh / yd
     int *ticket;
     int *err;
     int ns;                          // pipeline stages
@@ -266,12 +265,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
             if (lane == 0) h2p::mbar_arrive(&accfree[acc]);
             if (lane < 16 && row < info.rows) {
                 const bool dense = info.flags & kDense;
-                float *base = dense ? a.yd + int64_t(info.out_node) * a.mp * 4 : a.yh + int64_t(info.out_node) * a.kx * 4;
                 const int ld = dense ? a.mp : a.kx;
-                const int64_t cstride = dense ? a.yd_chunk : a.yh_chunk;
+                float *base = (dense ? a.yd : a.yh) + int64_t(info.out_node) * ld * a.nv + row;
 #pragma unroll
                 for (int e = 0; e < NP; ++e)
-                    if (e < a.nv) base[(e >> 2) * cstride + (e & 3) * ld + row] = __uint_as_float(v[e]);
+                    if (e < a.nv) base[e * ld] = __uint_as_float(v[e]);
             }
             if (acc == 1) phase ^= 1u;
             acc ^= 1;
@@ -284,10 +282,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
 
 // Vector tiles for the MMA B operand: for each node, rows = vectors (NP, zero beyond nv),
 // K = 64 coefficients (zero beyond k), split into bf16 hi and lo tiles, 128-byte swizzled.
-// src: FP32 tree in 4-vector chunks: element (node, v, i) at (v/4)*chunk + node*4*ld + (v%4)*ld + i.
+// src: FP32 tree with element (node, v, i) at (node*nv + v)*ld + i.
 // kvalid: coefficients per node (k), or, with leaf_lo given, the size of each leaf.
 template <int NP>
-__global__ void k_vec_tiles(const float *__restrict__ src, int64_t nodes, int ld, int64_t chunk, int kvalid, int nv,
+__global__ void k_vec_tiles(const float *__restrict__ src, int64_t nodes, int ld, int nv, int kvalid,
                             const int32_t *__restrict__ leaf_lo, unsigned char *__restrict__ dst)
 {
     const int64_t total = nodes * NP * 64;
@@ -296,7 +294,7 @@ __global__ void k_vec_tiles(const float *__restrict__ src, int64_t nodes, int ld
         const int r = int((e / 64) % NP), i = int(e % 64);
         const int valid = leaf_lo ? leaf_lo[node + 1] - leaf_lo[node] : kvalid;
         float x = 0.f;
-        if (r < nv && i < valid) x = src[(r >> 2) * chunk + node * 4 * ld + (r & 3) * ld + i];
+        if (r < nv && i < valid) x = src[(node * nv + r) * ld + i];
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
         const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
         unsigned char *t = dst + size_t(node) * 2 * NP * 128;

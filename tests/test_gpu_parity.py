@@ -102,6 +102,32 @@ def test_multi_rhs_columns_and_repeatability(built, prec):
     assert np.array_equal(gpu_matvec(op, X, prec), Y)  # bitwise repeatable (no atomics)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nv", [5, 8, 13, 32, 37])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_wide_passes_match_oracle(built, name, nv, prec):
+    """More than 4 vectors: one pass of up to 32 vectors on the wide kernels (37 = 32 + a
+    4-vector tail), every tile read once per pass."""
+    pts, ker, orc, op = built(name)
+    op.upload(prec)
+    X = si.gaussian_vectors(len(pts), nv, 11)
+    Y0 = si.gaussian_vectors(len(pts), nv, 12)
+    got = gpu_matvec(op, X, prec, 0.5, 2.0, Y0)
+    assert np.all(np.isfinite(got))
+    assert relerr(got, orc.matvec(X, 0.5, 2.0, Y0)) <= TOL[prec]
+
+
+def test_wide_fallback_for_large_leaves():
+    """Leaves of more than 64 points keep the 4-vector chunks for any vector count."""
+    pts = si.uniform_cloud(3000, 2, 9)
+    ker = ("exp", 0.2, 0, 0)
+    orc = oracle.OracleH2(pts, ker, 100, 4, 0.7)
+    op = h2.H2Operator(pts, ker, 100, 4, 0.7).upload("fp32")
+    X = si.gaussian_vectors(len(pts), 9, 13)
+    assert relerr(gpu_matvec(op, X, "fp32"), orc.matvec(X)) <= TOL["fp32"]
+    op.close()
+
+
 def test_workspace_entry_point(built):
     pts, ker, orc, op = built("grid64_exp")
     op.upload("fp64")
