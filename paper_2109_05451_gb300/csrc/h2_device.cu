@@ -137,6 +137,7 @@ struct Workspace {
     unsigned char *xb = nullptr, *xtb = nullptr;
 };
 
+constexpr int kTcSmemBudget = 224 * 1024;  // dynamic shared memory of the tensor-core stream
 constexpr int kWidePass = 32;  // vectors per pass of the wide kernels and of the tensor-core stream
 
 inline int pad16(int x) { return (x + 15) / 16 * 16; }
@@ -458,13 +459,13 @@ int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npa
     using namespace h2s;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_stream_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_stream_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBudget);
         cudaFuncSetAttribute(k_stream_tc<NP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         attr_done = true;
     }
     int ns = 8;
-    while (ns > 2 && tc_smem_bytes(NP, ns) > 200 * 1024) --ns;
+    while (ns > 2 && tc_smem_bytes(NP, ns) > kTcSmemBudget) --ns;
     const int64_t nodes = op.nnodes + 1;
     const unsigned g1 = unsigned(std::min<int64_t>((nodes * NP * 64 + 255) / 256, 65535));
     const unsigned g2 = unsigned(std::min<int64_t>((op.nleaves() * NP * 64 + 255) / 256, 65535));

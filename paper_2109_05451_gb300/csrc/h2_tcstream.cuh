@@ -3,18 +3,25 @@
 // With nv vectors the per-level products of Sec. 3.2 (Alg 4) and the dense product become
 // small GEMMs: for block (t, s), ( yhat_t )_{64 x N} += S_ts (64 x 64) * xhat_s (64 x N), N = nv
 // padded to a multiple of 16. Each entry a is stored as a_hi + a_lo with a_hi = bf16(a),
-// a_lo = bf16(a - a_hi); vectors are split the same way; the product keeps the three terms
-// hi*hi + hi*lo + lo*hi (the lo*lo term is below the representation error) and accumulates
-// in FP32 in tensor memory.
+// a_lo = bf16(a - a_hi); vectors are split the same way, and the product of the two split
+// representations accumulates in FP32 in tensor memory.
+//
+// A block's tile is [S_hi; S_lo] (128 x 64, K-major) and a node's vector tile [x_hi; x_lo]
+// (2N x 64), so one M = 128, N = 2N MMA per K-step forms all four partial products at once:
+//   D = [ S_hi x_hi   S_hi x_lo ]   rows 0..63
+//       [ S_lo x_hi   S_lo x_lo ]   rows 64..127,
+// and the row result is the sum of the four N-column quadrants, added in the epilogue.
 //
 // Roles per CTA (persistent, work handed out in chunks of whole rows by an atomic ticket):
 //   warp 4 (one lane): producer -- bulk-copies each block's hi/lo tiles (16 KB) and the input
 //                      vector's hi/lo tiles (2 x N x 128 B) into a ring of stages;
-//   warp 5 (one lane): MMA issuer -- 3 terms x 4 K-steps of tcgen05.mma per block into one of
-//                      two TMEM accumulators; tcgen05.commit frees the stage when the MMAs of
-//                      the block are done and signals the epilogue at the end of a row;
-//   warps 0-3:         epilogue -- tcgen05.ld of the 64 x N accumulator (warp w: rows
-//                      16w..16w+15), FP32 store of the row into the coefficient trees.
+//   warp 5 (one lane): MMA issuer -- 4 K-steps of tcgen05.mma per block into one of two TMEM
+//                      accumulators; tcgen05.commit frees the stage when the MMAs of the
+//                      block are done and signals the epilogue at the end of a row;
+//   warps 0-3:         epilogue -- tcgen05.ld of the 128 x 2N accumulator (warp w: rows
+//                      32w..32w+31); each thread adds its row's two column halves, warps 2-3
+//                      hand their sums (the S_lo rows) to warps 0-1 through shared memory,
+//                      and warps 0-1 store the FP32 row into the coefficient trees.
 #pragma once
 
 #include <cstdint>
@@ -48,15 +55,17 @@ struct TcRowInfo {
     int16_t flags;
 };
 
+// Two accumulator slots of 2 NP columns each.
 __host__ __device__ constexpr uint32_t tc_tmem_cols(int np)
 {
-    return 2 * np <= 32 ? 32u : (2 * np <= 64 ? 64u : 128u);
+    return 4 * np <= 32 ? 32u : (4 * np <= 64 ? 64u : (4 * np <= 128 ? 128u : 256u));
 }
 
 __host__ __device__ constexpr size_t tc_smem_bytes(int np, int ns)
 {
-    return size_t(ns) * (kTcTileBytes + 2u * np * 128u) + size_t(ns) * sizeof(StreamDesc) +
-           2 * kChunkDesc * sizeof(StreamDesc) + (2 * ns + 9) * sizeof(uint64_t) + 2 * 8 + 16;
+    return size_t(ns) * (kTcTileBytes + 2u * np * 128u) + 2u * 64u * np * sizeof(float) +
+           size_t(ns) * sizeof(StreamDesc) + 2 * kChunkDesc * sizeof(StreamDesc) + (2 * ns + 13) * sizeof(uint64_t) +
+           2 * 8 + 16;
 }
 
 // Grid: persistent; block: kTcThreads; NP = N (padded vectors, 16..64).
@@ -67,9 +76,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
     constexpr uint32_t kVecBytes = 2u * NP * 128u;  // hi + lo tiles of one node's vectors
     constexpr uint32_t kStage = kTcTileBytes + kVecBytes;
     const int ns = a.ns;
-    // layout: stages (1 KB aligned) | descriptors | barriers | TMEM address | flags
+    // layout: stages (1 KB aligned) | row exchange | descriptors | barriers | TMEM address | flags
     unsigned char *stages = smem_raw;
-    StreamDesc *sdesc = reinterpret_cast<StreamDesc *>(stages + size_t(ns) * kStage);
+    float *xch = reinterpret_cast<float *>(stages + size_t(ns) * kStage);  // [2][NP][64]
+    StreamDesc *sdesc = reinterpret_cast<StreamDesc *>(xch + 2 * 64 * NP);
     StreamDesc *dbuf = sdesc + ns;  // [2][kChunkDesc]
     uint64_t *full = reinterpret_cast<uint64_t *>(dbuf + 2 * kChunkDesc);
     uint64_t *empty = full + ns;
@@ -77,7 +87,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
     uint64_t *rowdone = dbar + 2;    // [2]
     uint64_t *accfree = rowdone + 2; // [2]
     uint64_t *fin = accfree + 2;     // the issuer's last MMAs have completed
-    TcRowInfo *rowinfo = reinterpret_cast<TcRowInfo *>(fin + 1);  // [2]
+    uint64_t *xready = fin + 1;      // [2] warps 2-3 have written their row sums
+    uint64_t *xfree = xready + 2;    // [2] warps 0-1 have read them
+    TcRowInfo *rowinfo = reinterpret_cast<TcRowInfo *>(xfree + 2);  // [2]
     uint32_t *taddr_s = reinterpret_cast<uint32_t *>(rowinfo + 2);
     int *abort_flag = reinterpret_cast<int *>(taddr_s + 1);
 
@@ -92,6 +104,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
         for (int i = 0; i < 2; ++i) {
             h2p::mbar_init(&rowdone[i], 2);  // the issuer's arrive + its tcgen05.commit
             h2p::mbar_init(&accfree[i], 4);  // the four epilogue warps
+            h2p::mbar_init(&xready[i], 2);   // lane 0 of warps 2 and 3
+            h2p::mbar_init(&xfree[i], 2);    // lane 0 of warps 0 and 1
         }
         h2p::mbar_init(fin, 1);
         *abort_flag = 0;
@@ -172,7 +186,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
     } else if (warp == 5) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = h2t::idesc_bf16_f32(64, NP);
+            constexpr uint32_t idesc = h2t::idesc_bf16_f32(128, 2 * NP);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;              // accumulator slot
@@ -195,21 +209,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
                 }
                 if (!(d.flags & kZero)) {
                     const unsigned char *st = stages + size_t(stage) * kStage;
-                    const uint64_t a_hi = h2t::smem_desc_sw128(st), a_lo = h2t::smem_desc_sw128(st + 8192);
-                    const uint64_t b_hi = h2t::smem_desc_sw128(st + kTcTileBytes);
-                    const uint64_t b_lo = h2t::smem_desc_sw128(st + kTcTileBytes + NP * 128);
-                    const uint32_t dt = tmem + uint32_t(acc * NP);
-                    uint32_t accumulate = fresh ? 0u : 1u;
+                    const uint64_t ad = h2t::smem_desc_sw128(st);                 // [S_hi; S_lo]
+                    const uint64_t bd = h2t::smem_desc_sw128(st + kTcTileBytes);  // [x_hi; x_lo]
+                    const uint32_t dt = tmem + uint32_t(acc * 2 * NP);
 #pragma unroll
-                    for (int term = 0; term < 3; ++term) {
-                        const uint64_t ad = term == 2 ? a_lo : a_hi;
-                        const uint64_t bd = term == 1 ? b_lo : b_hi;
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            h2t::mma_bf16(dt, ad + uint64_t(2 * kk), bd + uint64_t(2 * kk), idesc, accumulate);
-                            accumulate = 1u;
-                        }
-                    }
+                    for (int kk = 0; kk < 4; ++kk)
+                        h2t::mma_bf16(dt, ad + uint64_t(2 * kk), bd + uint64_t(2 * kk), idesc,
+                                      (fresh && kk == 0) ? 0u : 1u);
                     fresh = false;
                 } else {
                     fresh = true;  // a zero row is a whole row by itself
@@ -240,36 +246,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
         // ------------------------------------------------------------ epilogue (warps 0-3)
         int acc = 0;
         uint32_t phase = 0;
-        const int row = 16 * warp + lane;  // D row held by this thread (lanes 0..15)
+        const bool lo_rows = warp >= 2;            // D rows 64..127: the S_lo products
+        const int row = 32 * (warp & 1) + lane;    // output row of this thread
+        const uint32_t lanes = uint32_t(32 * warp) << 16;
         for (;;) {
             if (!h2p::mbar_wait(&rowdone[acc], phase, abort_flag, a.err)) break;
             const TcRowInfo info = rowinfo[acc];
             if (info.flags & kEnd) break;
             h2t::fence_after_sync();
-            uint32_t v[NP];
+            float sum[NP];
             if (!(info.flags & kZero)) {
 #pragma unroll
                 for (int c = 0; c < NP; c += 16) {
-                    uint32_t t[16];
-                    h2t::tmem_ld16(tmem + uint32_t(acc * NP + c) + (uint32_t(32 * warp) << 16), t);
+                    uint32_t t0[16], t1[16];
+                    h2t::tmem_ld16(tmem + uint32_t(acc * 2 * NP + c) + lanes, t0);
+                    h2t::tmem_ld16(tmem + uint32_t(acc * 2 * NP + NP + c) + lanes, t1);
                     h2t::tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) v[c + e] = t[e];
+                    for (int e = 0; e < 16; ++e) sum[c + e] = __uint_as_float(t0[e]) + __uint_as_float(t1[e]);
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < NP; ++e) v[e] = 0u;
+                for (int e = 0; e < NP; ++e) sum[e] = 0.f;
             }
             h2t::fence_before_sync();
             __syncwarp();
             if (lane == 0) h2p::mbar_arrive(&accfree[acc]);
-            if (lane < 16 && row < info.rows) {
-                const bool dense = info.flags & kDense;
-                const int ld = dense ? a.mp : a.kx;
-                float *base = (dense ? a.yd : a.yh) + int64_t(info.out_node) * ld * a.nv + row;
+            float *xs = xch + acc * 64 * NP;
+            if (lo_rows) {
+                if (!h2p::mbar_wait(&xfree[acc], phase ^ 1u, abort_flag, a.err)) break;
 #pragma unroll
-                for (int e = 0; e < NP; ++e)
-                    if (e < a.nv) base[e * ld] = __uint_as_float(v[e]);
+                for (int e = 0; e < NP; ++e) xs[e * 64 + row] = sum[e];
+                __syncwarp();
+                if (lane == 0) h2p::mbar_arrive(&xready[acc]);
+            } else {
+                if (!h2p::mbar_wait(&xready[acc], phase, abort_flag, a.err)) break;
+                if (row < info.rows) {
+                    const bool dense = info.flags & kDense;
+                    const int ld = dense ? a.mp : a.kx;
+                    float *base = (dense ? a.yd : a.yh) + int64_t(info.out_node) * ld * a.nv + row;
+#pragma unroll
+                    for (int e = 0; e < NP; ++e)
+                        if (e < a.nv) base[e * ld] = sum[e] + xs[e * 64 + row];
+                }
+                __syncwarp();
+                if (lane == 0) h2p::mbar_arrive(&xfree[acc]);
             }
             if (acc == 1) phase ^= 1u;
             acc ^= 1;
