@@ -425,8 +425,17 @@ int launch_wide(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double
     const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * k, size_t(dv.max_leaf_rows) * dv.max_leaf_rows) *
                                          es) + 15) / 16 * 16);
     const uint32_t x_str = uint32_t(std::max(mp, kx) * NVMAX * es);
-    const Pipe p_str = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 200 * 1024, 12);
+    // two CTAs per SM where three stages fit in half of the shared memory: eight consumer
+    // warps hide the latency of the register-blocked products; else one CTA per SM
+    Pipe p_str = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 110 * 1024, 12);
+    int per_sm = 2;
+    if (p_str.ns < 3) {
+        p_str = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 200 * 1024, 12);
+        per_sm = 1;
+    }
     const size_t sm_str = smem_bytes<T, NVMAX>(p_str, 0, kx, true);
+    const unsigned g_bot = unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(dv.num_sms) * per_sm, dv.n_chunks_bottom)));
+    const unsigned g_top = unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(dv.num_sms) * per_sm, dv.n_chunks_top)));
     set_kernel_attributes<T, NVMAX>();
 
     cudaEvent_t ev = dv.begin(st);
@@ -435,13 +444,13 @@ int launch_wide(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double
     ev = dv.begin(st);
     int ls = 0;
     if (dv.n_chunks_bottom > 0) {
-        k_stream<T, NVMAX><<<dv.grid_bottom, kThreads, sm_str, st>>>(o, v, p_str, dv.desc_bottom, dv.chunks_bottom,
-                                                                     dv.n_chunks_bottom, 0);
+        k_stream<T, NVMAX><<<g_bot, kThreads, sm_str, st>>>(o, v, p_str, dv.desc_bottom, dv.chunks_bottom,
+                                                            dv.n_chunks_bottom, 0);
         ++ls;
     }
     if (dv.n_chunks_top > 0) {
-        k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_str, st>>>(o, v, p_str, dv.desc_top, dv.chunks_top,
-                                                                  dv.n_chunks_top, 1);
+        k_stream<T, NVMAX><<<g_top, kThreads, sm_str, st>>>(o, v, p_str, dv.desc_top, dv.chunks_top,
+                                                         dv.n_chunks_top, 1);
         ++ls;
     }
     dv.end(1, ev, st, ls);
@@ -451,8 +460,9 @@ int launch_wide(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double
     return cuda_status(cudaGetLastError());
 }
 
-// Tensor-core stream of one pass (H2_BF16X2): split-BF16 tiles of the input vectors, then
-// the coupling and dense rows of every level; NP = vectors padded to a multiple of 16.
+// Tensor-core stream of one pass (H2_BF16X2): the coupling and dense rows of every level,
+// reading the split-BF16 vector tiles that the gather and the upsweep wrote; NP = vectors
+// padded to a multiple of 16.
 template <int NP>
 int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npass, cudaStream_t st)
 {
@@ -466,12 +476,6 @@ int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npa
     }
     int ns = 8;
     while (ns > 2 && tc_smem_bytes(NP, ns) > kTcSmemBudget) --ns;
-    const int64_t nodes = op.nnodes + 1;
-    const unsigned g1 = unsigned(std::min<int64_t>((nodes * NP * 64 + 255) / 256, 65535));
-    const unsigned g2 = unsigned(std::min<int64_t>((op.nleaves() * NP * 64 + 255) / 256, 65535));
-    k_vec_tiles<NP><<<g1, 256, 0, st>>>(static_cast<const float *>(w.xh), nodes, dv.kx, npass, op.k, nullptr, w.xb);
-    k_vec_tiles<NP><<<g2, 256, 0, st>>>(static_cast<const float *>(w.xt), op.nleaves(), dv.mp, npass, 0, dv.leaf_lo,
-                                        w.xtb);
     TcArgs a;
     a.vals = dv.vals;
     a.desc = dv.desc_bottom;
@@ -493,26 +497,30 @@ int launch_tc_stream(const h2_op &op, h2_device &dv, const Workspace &w, int npa
 }
 
 // Tensor-core product (H2_BF16X2), per pass of up to kWidePass vectors: FP32 upsweep on the
-// subtree kernels, the coupling and dense rows of every level on the tensor-core stream,
-// FP32 downsweep with the leaf expansion and the epilogue.
+// wide subtree kernels (which also write the split-BF16 vector tiles, NVMAX = the padded
+// pass width), the coupling and dense rows of every level on the tensor-core stream, FP32
+// downsweep with the leaf expansion and the epilogue.
 template <int NVMAX>
 int launch_tc_pass(const h2_op &op, h2_device &dv, const float *X, float *Y, int npass, double alpha, double beta,
                    const Workspace &w, cudaStream_t st)
 {
     using namespace h2s;
     using T = float;
+    static_assert(NVMAX % 16 == 0, "tensor-core passes are padded to 16 vectors");
     const Op<T> o = make_op<T>(op, dv);
-    const Vec<T> v{X, Y, npass, npass, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd),
-                   static_cast<T *>(w.xh), static_cast<T *>(w.yh), w.tickets, dv.err};
+    Vec<T> v{X, Y, npass, npass, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd),
+             static_cast<T *>(w.xh), static_cast<T *>(w.yh), w.tickets, dv.err};
+    v.xb = w.xb;
+    v.xtb = w.xtb;
+    v.np = NVMAX;
     const SweepPlan<T, NVMAX> sp = make_sweep_plan<T, NVMAX>(op, dv);
     set_kernel_attributes<T, NVMAX>();
     cudaEvent_t ev = dv.begin(st);
     const int lu = up_all(op, dv, o, v, sp, st);
     dv.end(0, ev, st, lu);
     ev = dv.begin(st);
-    const int rc = pad16(npass) <= 16 ? launch_tc_stream<16>(op, dv, w, npass, st)
-                                      : launch_tc_stream<32>(op, dv, w, npass, st);
-    dv.end(1, ev, st, 3);
+    const int rc = launch_tc_stream<NVMAX>(op, dv, w, npass, st);
+    dv.end(1, ev, st, 1);
     if (rc != H2_OK) return rc;
     ev = dv.begin(st);
     const int ld = down_all(op, dv, o, v, sp, st);
@@ -526,10 +534,8 @@ int launch_tc(const h2_op &op, h2_device &dv, const float *X, float *Y, int nv, 
     for (int v0 = 0; v0 < nv; v0 += kWidePass) {
         const int c = std::min(kWidePass, nv - v0);
         const size_t o = size_t(v0) * op.n;
-        const int rc = c <= kChunk ? launch_tc_pass<kChunk>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
-                     : c <= 8      ? launch_tc_pass<8>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
-                     : c <= 16     ? launch_tc_pass<16>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
-                                   : launch_tc_pass<32>(op, dv, X + o, Y + o, c, alpha, beta, w, st);
+        const int rc = c <= 16 ? launch_tc_pass<16>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                               : launch_tc_pass<32>(op, dv, X + o, Y + o, c, alpha, beta, w, st);
         if (rc != H2_OK) return rc;
     }
     return H2_OK;

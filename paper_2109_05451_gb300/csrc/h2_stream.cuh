@@ -27,6 +27,8 @@
 // segment starts on a 16-byte boundary.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cstdint>
 #include <type_traits>
 
@@ -72,7 +74,22 @@ struct Vec {
     T *xt, *yd, *xh, *yh;
     int *tickets;  // [0] bottom stream, [1] top stream (zeroed by k_gather)
     int *err;
+    // tensor-core path only: split-BF16 B-operand tiles of every node's xhat (written by the
+    // upsweep) and of every leaf's permuted input (written by the gather), np rows each
+    unsigned char *xb = nullptr, *xtb = nullptr;
+    int np = 0;
 };
+
+// Bytes of one node's split-BF16 vector tile: np rows (vectors) x 64 bf16, hi then lo.
+__host__ __device__ constexpr uint32_t vec_tile_bytes(int np) { return 2u * uint32_t(np) * 128u; }
+
+// Byte offset of element (row r, column k) in a K-major bf16 tile with 64 columns per
+// 128-byte row, 128-byte swizzle (the 16-byte chunk index XORed with the row index mod 8).
+__host__ __device__ inline uint32_t sw128(int r, int k)
+{
+    const uint32_t o = uint32_t(r) * 128u + uint32_t(k) * 2u;
+    return o ^ (((o >> 7) & 7u) << 4);
+}
 
 struct Pipe {
     int ns;               // stages
@@ -358,6 +375,8 @@ struct Acc {
             for (int e = 0; e < VEC; ++e)
                 if (v < nv && e < per && o0 + e < R) a[v][e] += src[v * ld + o0 + e];
     }
+    // The tensor-core path runs its sweeps on the wide accumulator; nothing to write here.
+    __device__ __forceinline__ void store_tile(unsigned char *, int, int, int) const {}
     // Leaf epilogue: user-order rows of the held outputs (fetched before the tile arrives),
     // then Y[v*n + row] = alpha y + beta Y for the threads holding final values.
     int64_t u[VEC];
@@ -524,6 +543,29 @@ struct AccW {
 #pragma unroll
         for (int e = 0; e < 4; ++e) u[e] = o0 + e < R ? perm[r0 + o0 + e] : 0;
     }
+    // Split-BF16 B-operand tile of the held block (rows = vectors v < np, columns = outputs):
+    // hi = bf16(a), lo = bf16(a - hi), zero for v >= nv or output >= R. Four consecutive
+    // outputs are 8 contiguous bytes of one swizzled 16-byte chunk.
+    __device__ __forceinline__ void store_tile(unsigned char *tile, int np, int nv, int R) const
+    {
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int v = 0; v < VT; ++v) {
+                const int r = v0 + v;
+                if (r >= np) break;
+                __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float x = (r < nv && o0 + e < R) ? a[v][e] : 0.f;
+                    hi[e] = __float2bfloat16_rn(x);
+                    lo[e] = __float2bfloat16_rn(x - __bfloat162float(hi[e]));
+                }
+                const uint32_t off = sw128(r, o0);
+                *reinterpret_cast<uint2 *>(tile + off) = *reinterpret_cast<const uint2 *>(hi);
+                *reinterpret_cast<uint2 *>(tile + np * 128 + off) = *reinterpret_cast<const uint2 *>(lo);
+            }
+        }
+    }
     __device__ __forceinline__ void write_out(T *Y, int64_t n, T alpha, T beta, int nv, int R) const
     {
 #pragma unroll
@@ -552,9 +594,27 @@ __global__ void k_gather(Op<T> op, Vec<T> vec)
     if (blockIdx.x == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
     for (int64_t leaf = blockIdx.x; leaf < op.nleaves; leaf += gridDim.x) {
         const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
-        for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
-            const int i = e % R, v = e / R;
-            vec.xt[(leaf * vec.vs + v) * op.mp + i] = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
+        if (vec.xtb == nullptr) {
+            for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+                const int i = e % R, v = e / R;
+                vec.xt[(leaf * vec.vs + v) * op.mp + i] = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
+            }
+        } else if constexpr (sizeof(T) == 4) {
+            // also the leaf's split-BF16 tile (np x 64, zero beyond the leaf and beyond nv)
+            unsigned char *tile = vec.xtb + leaf * vec_tile_bytes(vec.np);
+            for (int e = threadIdx.x; e < vec.np * 64; e += blockDim.x) {
+                const int i = e % 64, v = e / 64;
+                float x = 0.f;
+                if (i < R && v < vec.nv) {
+                    x = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
+                    vec.xt[(leaf * vec.vs + v) * op.mp + i] = x;
+                }
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+                const uint32_t off = sw128(v, i);
+                *reinterpret_cast<__nv_bfloat16 *>(tile + off) = hi;
+                *reinterpret_cast<__nv_bfloat16 *>(tile + vec.np * 128 + off) = lo;
+            }
         }
     }
 }
@@ -594,9 +654,11 @@ __global__ void __launch_bounds__(kThreads)
                 for (int lev = Lin; ok && lev > Lr; --lev) {
                     const int64_t cnt = int64_t(1) << (lev - Lr);
                     const int64_t c0 = (int64_t(1) << lev) + st * cnt;
+                    // an input level from an earlier launch travels with its transfer tiles
+                    const bool with_x = !leaf_input && lev == Lin;
                     for (int64_t c = c0; ok && c < c0 + cnt; ++c)
-                        ok = produce(s, pp, ring, op.E + c * k * kx, k * kx * es, nullptr, 0, nullptr, 0, nullptr,
-                                     vec.err);
+                        ok = produce(s, pp, ring, op.E + c * k * kx, k * kx * es, with_x ? vec.xh + c * kx * vs : nullptr,
+                                     with_x ? kx * nv * es : 0, nullptr, 0, nullptr, vec.err);
                 }
             }
             drain_on_abort(s, ring);
@@ -624,36 +686,33 @@ __global__ void __launch_bounds__(kThreads)
                     acc.store(s.sub + ((1 << L) + j) * wstride, kx, nv, k);
                     acc.store(vec.xh + (op.first_leaf + leaf) * kx * vs, kx, nv, k);
                 }
+                if (vec.xb) acc.store_tile(vec.xb + (op.first_leaf + leaf) * vec_tile_bytes(vec.np), vec.np, nv, k);
                 h2p::consumer_sync(kConsumers);
             }
-        } else {
-            // input level computed by an earlier launch
-            const int64_t c0 = (int64_t(1) << Lin) + (st << L);
-            for (int e = tid; e < (kx * nv) << L; e += kConsumers) {
-                const int j = e / (kx * nv), r = e % (kx * nv);
-                s.sub[((1 << L) + j) * wstride + r] = vec.xh[(c0 + j) * kx * vs + r];
-            }
-            h2p::consumer_sync(kConsumers);
         }
-        // transfers, level by level
+        // transfers, level by level (the input level of a launch without leaf input arrives in
+        // the stages, next to its transfer tiles)
         for (int lev = Lin; lev > Lr; --lev) {
             const int rel = lev - Lr;
             const int64_t cnt = int64_t(1) << rel;
+            const bool staged_x = !leaf_input && lev == Lin;
             for (int64_t pi = 0; pi < cnt / 2; ++pi) {
                 acc.zero();
                 for (int c = 0; c < 2; ++c) {
                     const int child_slot = (1 << rel) + int(2 * pi + c);
                     if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
-                    acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, s.sub + child_slot * wstride, kx, nv);
+                    const T *xc = staged_x ? stage_x(s, pp, ring.stage) : s.sub + child_slot * wstride;
+                    acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, xc, kx, nv);
                     release(&s.empty[ring.stage], lane);
                     ring.next();
                 }
+                const int64_t par = (int64_t(1) << (lev - 1)) + st * (cnt / 2) + pi;
                 if (acc.reduce(k, nv, s.red)) {
                     const int pslot = (1 << (rel - 1)) + int(pi);
-                    const int64_t par = (int64_t(1) << (lev - 1)) + st * (cnt / 2) + pi;
                     acc.store(s.sub + pslot * wstride, kx, nv, k);
                     acc.store(vec.xh + par * kx * vs, kx, nv, k);
                 }
+                if (vec.xb) acc.store_tile(vec.xb + par * vec_tile_bytes(vec.np), vec.np, nv, k);
                 h2p::consumer_sync(kConsumers);
             }
         }

@@ -301,28 +301,4 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
     if (warp == 0) h2t::tmem_dealloc(tmem, tc_tmem_cols(NP));
 }
 
-// Vector tiles for the MMA B operand: for each node, rows = vectors (NP, zero beyond nv),
-// K = 64 coefficients (zero beyond k), split into bf16 hi and lo tiles, 128-byte swizzled.
-// src: FP32 tree with element (node, v, i) at (node*nv + v)*ld + i.
-// kvalid: coefficients per node (k), or, with leaf_lo given, the size of each leaf.
-template <int NP>
-__global__ void k_vec_tiles(const float *__restrict__ src, int64_t nodes, int ld, int nv, int kvalid,
-                            const int32_t *__restrict__ leaf_lo, unsigned char *__restrict__ dst)
-{
-    const int64_t total = nodes * NP * 64;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t node = e / (NP * 64);
-        const int r = int((e / 64) % NP), i = int(e % 64);
-        const int valid = leaf_lo ? leaf_lo[node + 1] - leaf_lo[node] : kvalid;
-        float x = 0.f;
-        if (r < nv && i < valid) x = src[(node * nv + r) * ld + i];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-        unsigned char *t = dst + size_t(node) * 2 * NP * 128;
-        const uint32_t o = h2t::sw128_offset(r, i);
-        *reinterpret_cast<__nv_bfloat16 *>(t + o) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(t + NP * 128 + o) = lo;
-    }
-}
-
 }  // namespace h2s
