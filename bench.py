@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 import synthetic_inputs as si  # noqa: E402
 
 METRIC = "H2 matvec GB/s (nv=1, 2D Gaussian grid N=2^20, rank 64)"
+FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 CUDA-core peak at the maximum SM clock
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -154,6 +155,75 @@ def cpu_baseline(steps: int = 0):
             "gflops": 2 * ent / t / 1e9}
 
 
+def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind):
+    """The multi-vector workload: N = 2^21 uniform random points in [0,1]^3, exp(-r/0.2),
+    leaf 64, 4 x 4 x 4 Chebyshev grid (rank 64), eta 0.7, 32 vectors, in split-BF16 on the
+    tensor cores and in FP32. Its ~113 GB of stored blocks exceed L2 by far, so no flush is
+    needed between products. Bytes and flops are algorithmic: every stored entry once per
+    product (bases and transfers twice), X read and Y written; 2 flops per entry per vector."""
+    w = si.CLOUD3D_EXP
+    pts = w.make_points()
+    op = h2.H2Operator(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    info = op.info
+    n, nv = op.n, w.nv
+    mat_entries, vec_elems = entry_counts(info, nv)
+    bytes_step = 4 * (mat_entries + vec_elems)
+    flops = 2 * mat_entries * nv
+    Xh = np.ascontiguousarray(w.make_x(n).T).astype(np.float32)
+    out = {"workload": w.name, "n": n, "nv": nv, "rank": info.rank, "leaf": info.leaf_size, "eta": w.eta,
+           "kernel": "exp(-r/0.2)", "depth": info.depth, "coupling_blocks": info.n_coupling,
+           "dense_blocks": info.n_dense, "bytes_per_step": bytes_step, "flops_per_step": flops,
+           "l2": "inputs larger than L2 (113 GB of blocks per product), no flush"}
+    stream = torch.cuda.current_stream()
+    for prec in ("bf16x2", "fp32"):
+        t0 = time.perf_counter()
+        op.upload(prec)
+        upload_s = time.perf_counter() - t0
+        X = torch.from_numpy(Xh).cuda().t()
+        Y = op.new_vectors(nv, fill=0.0)
+        for _ in range(warmup):
+            op.matvec(X, Y)
+        h2.h2_get_timing(op.handle)
+        h2.h2_set_timing(op.handle, True)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            a.record(stream)
+            op.matvec(X, Y)
+            b.record(stream)
+        torch.cuda.synchronize()
+        h2.h2_set_timing(op.handle, False)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        phase_ms, phase_launches, prods = h2.h2_get_timing(op.handle)
+        phase_ms = phase_ms / max(prods, 1)
+        ms_step = float(np.mean(ms))
+        gbs = bytes_step / (ms_step * 1e-3) / 1e9
+        # the block stream (phase 1): every coupling and dense entry once, one read of each
+        # node's and leaf's input segment, one write of each output segment
+        seg = 4 * nv * ((info.n_nodes + 1) * info.rank + n)
+        blk_bytes = 4 * (info.coupling_entries + info.dense_entries) + 2 * seg
+        blk_gbs = blk_bytes / (float(phase_ms[1]) * 1e-3) / 1e9
+        if prec == "bf16x2":
+            roof = {"kernel": "k_stream_tc (split-BF16 tcgen05, 128x64x16 MMAs, FP32 accumulation in TMEM)",
+                    "bound": "hbm", "achieved": blk_gbs, "peak": peak_hbm, "unit": "GB/s",
+                    "frac": blk_gbs / peak_hbm, "peak_kind": peak_kind, "algorithmic_bytes": blk_bytes}
+        else:
+            # 16 flop per byte at 32 vectors: the FP32 stream is bound by the CUDA-core FMA
+            # rate, 152 SMs x 128 lanes x 2 flop x the maximum SM clock
+            blk_tflops = 2 * (info.coupling_entries + info.dense_entries) * nv / (float(phase_ms[1]) * 1e-3) / 1e12
+            roof = {"kernel": "k_stream (FP32, register-blocked wide accumulator)", "bound": "alu",
+                    "achieved": blk_tflops, "peak": FFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": blk_tflops / FFMA_PEAK_TFLOPS, "peak_kind": "derived (unit counts x clock)",
+                    "hbm_GB/s": blk_gbs}
+        out[prec] = {"ms_per_step": ms_step, "ms_median": float(np.median(ms)), "GB/s": gbs,
+                     "gflops": flops / (ms_step * 1e-3) / 1e9, "frac_of_hbm": gbs / peak_hbm,
+                     "steps": steps, "upload_s": upload_s,
+                     "phases_ms": dict(zip(h2.PHASES, [float(v) for v in phase_ms])), "roofline": roof}
+        del X, Y
+    op.close()
+    return out
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -178,6 +248,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-multi-rhs", action="store_true",
+                    help="skip the 32-vector measurement on the 2^21-point 3D cloud")
     ap.add_argument("--grid", type=int, default=1024,
                     help="grid side of the 2D Gaussian workload (1024 = the benchmarked N = 2^20; smaller "
                          "sides are for profiler captures)")
@@ -323,6 +395,12 @@ def main():
         "cpu_baseline": cpu,
         "build_s": build_s, "upload_s": res["upload_s"],
     }
+    if not args.no_multi_rhs:
+        op.close()
+        try:
+            line["multi_rhs"] = multi_rhs(h2, torch, max(5, args.steps // 20), 3, peak_hbm, peak_kind)
+        except Exception as exc:  # reported, never silently dropped
+            line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
     if res_fp64 is not None:
         ms64 = float(np.mean(res_fp64["step_ms"]))
         b64 = 8 * (mat_entries + vec_elems)
