@@ -155,13 +155,13 @@ def cpu_baseline(steps: int = 0):
             "gflops": 2 * ent / t / 1e9}
 
 
-def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind):
+def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None):
     """The multi-vector workload: N = 2^21 uniform random points in [0,1]^3, exp(-r/0.2),
     leaf 64, 4 x 4 x 4 Chebyshev grid (rank 64), eta 0.7, 32 vectors, in split-BF16 on the
     tensor cores and in FP32. Its ~113 GB of stored blocks exceed L2 by far, so no flush is
     needed between products. Bytes and flops are algorithmic: every stored entry once per
     product (bases and transfers twice), X read and Y written; 2 flops per entry per vector."""
-    w = si.CLOUD3D_EXP
+    w = si.CLOUD3D_EXP if not n_points or n_points == 2 ** 21 else si.cloud3d(n_points)
     pts = w.make_points()
     op = h2.H2Operator(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
     info = op.info
@@ -173,7 +173,7 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind):
     out = {"workload": w.name, "n": n, "nv": nv, "rank": info.rank, "leaf": info.leaf_size, "eta": w.eta,
            "kernel": "exp(-r/0.2)", "depth": info.depth, "coupling_blocks": info.n_coupling,
            "dense_blocks": info.n_dense, "bytes_per_step": bytes_step, "flops_per_step": flops,
-           "l2": "inputs larger than L2 (113 GB of blocks per product), no flush"}
+           "l2": f"inputs larger than L2 ({4 * mat_entries / 1e9:.1f} GB of blocks per product), no flush"}
     stream = torch.cuda.current_stream()
     for prec in ("bf16x2", "fp32"):
         t0 = time.perf_counter()
@@ -250,6 +250,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multi-rhs", action="store_true",
                     help="skip the 32-vector measurement on the 2^21-point 3D cloud")
+    ap.add_argument("--cloud-n", type=int, default=2 ** 21,
+                    help="points of the 3D cloud of the 32-vector measurement (2^21 = the benchmarked size; "
+                         "smaller sizes are for profiler captures)")
+    ap.add_argument("--multi-rhs-steps", type=int, default=0, help="timed 32-vector products (0: steps / 20, >= 5)")
     ap.add_argument("--grid", type=int, default=1024,
                     help="grid side of the 2D Gaussian workload (1024 = the benchmarked N = 2^20; smaller "
                          "sides are for profiler captures)")
@@ -398,7 +402,8 @@ def main():
     if not args.no_multi_rhs:
         op.close()
         try:
-            line["multi_rhs"] = multi_rhs(h2, torch, max(5, args.steps // 20), 3, peak_hbm, peak_kind)
+            mr_steps = args.multi_rhs_steps if args.multi_rhs_steps > 0 else max(5, args.steps // 20)
+            line["multi_rhs"] = multi_rhs(h2, torch, mr_steps, 3, peak_hbm, peak_kind, args.cloud_n)
         except Exception as exc:  # reported, never silently dropped
             line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
     if res_fp64 is not None:

@@ -135,6 +135,8 @@ struct Workspace {
     // tensor-core path (H2_BF16X2): split-BF16 vector tiles of the coefficient tree and of
     // the permuted input
     unsigned char *xb = nullptr, *xtb = nullptr;
+    // wide passes: row-major copy of X, later of the result rows (n x round4(pass vectors))
+    void *rows = nullptr;
 };
 
 constexpr int kTcSmemBudget = 224 * 1024;  // dynamic shared memory of the tensor-core stream
@@ -155,15 +157,17 @@ inline int pass_vectors(const h2_device &dv, int nv)
 
 // Workspace for one pass of vp vectors: permuted input and dense result ([leaf][v][mp]),
 // coefficient trees xhat and yhat ([node][v][kx]), the split-BF16 vector tiles of the
-// tensor-core path, and the scheduling tickets.
+// tensor-core path, the row-major staging buffer of wide passes, and the scheduling tickets.
 size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, void *base)
 {
     const int vp = pass_vectors(dv, nv), np = pad16(vp);
+    const bool wide = vp > kChunk || dv.tc;
     const size_t es = dv.esize;
     const size_t vec = align_up(size_t(op.nleaves()) * vp * dv.mp * es);
     const size_t tree = align_up(size_t(op.nnodes + 1) * vp * dv.kx * es);
     const size_t xb = dv.tc ? align_up(size_t(op.nnodes + 1) * 2 * np * 128) : 0;
     const size_t xtb = dv.tc ? align_up(size_t(op.nleaves()) * 2 * np * 128) : 0;
+    const size_t rows = wide ? align_up(size_t(op.n) * round4(vp) * es) : 0;
     if (w) {
         char *p = static_cast<char *>(base);
         w->xt = p;
@@ -172,9 +176,10 @@ size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, voi
         w->yh = p + 2 * vec + tree;
         w->xb = dv.tc ? reinterpret_cast<unsigned char *>(p + 2 * vec + 2 * tree) : nullptr;
         w->xtb = dv.tc ? w->xb + xb : nullptr;
-        w->tickets = reinterpret_cast<int *>(p + 2 * vec + 2 * tree + xb + xtb);
+        w->rows = wide ? p + 2 * vec + 2 * tree + xb + xtb : nullptr;
+        w->tickets = reinterpret_cast<int *>(p + 2 * vec + 2 * tree + xb + xtb + rows);
     }
-    return 2 * vec + 2 * tree + xb + xtb + kAlign;
+    return 2 * vec + 2 * tree + xb + xtb + rows + kAlign;
 }
 
 int cuda_status(cudaError_t e)
@@ -377,9 +382,14 @@ int up_all(const h2_op &op, const h2_device &dv, const h2s::Op<T> &o, const h2s:
            const SweepPlan<T, NVMAX> &sp, cudaStream_t st)
 {
     using namespace h2s;
+    int launches = 2;
+    if (v.xr) {
+        k_rows_in<T><<<dim3(unsigned((op.n + 31) / 32), unsigned((v.nv + 31) / 32)), dim3(32, 8), 0, st>>>(
+            v.X, op.n, v.nv, v.xr, v.ldr);
+        ++launches;
+    }
     k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
     k_up_sub<T, NVMAX><<<sp.grid_bsub, kThreads, sp.sm_bsub, st>>>(o, v, sp.bsub, op.q - sp.Lw, sp.Lw, sp.nsub, 1);
-    int launches = 2;
     for (int lin = op.q - sp.Lw; lin > 0;) {
         const int L = std::min(sp.Ltop, lin), lr = lin - L;
         const int64_t ns = int64_t(1) << lr;
@@ -406,6 +416,11 @@ int down_all(const h2_op &op, const h2_device &dv, const h2s::Op<T> &o, const h2
         lr += L + 1;
     }
     k_down_sub<T, NVMAX><<<sp.grid_bsub, kThreads, sp.sm_bsub, st>>>(o, v, sp.bsub, Lr0, sp.Lw, sp.nsub, 1);
+    if (v.yr) {
+        k_rows_out<T><<<dim3(unsigned((op.n + 31) / 32), unsigned((v.nv + 31) / 32)), dim3(32, 8), 0, st>>>(
+            v.yr, v.ldr, v.Y, op.n, v.nv, v.alpha, v.beta);
+        ++launches;
+    }
     return launches + 1;
 }
 
@@ -419,8 +434,10 @@ int launch_wide(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double
     const uint32_t es = sizeof(T);
     const int k = op.k, kx = dv.kx, mp = dv.mp;
     const Op<T> o = make_op<T>(op, dv);
-    const Vec<T> v{X, Y, nv, nv, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd),
-                   static_cast<T *>(w.xh), static_cast<T *>(w.yh), w.tickets, dv.err};
+    Vec<T> v{X, Y, nv, nv, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd),
+             static_cast<T *>(w.xh), static_cast<T *>(w.yh), w.tickets, dv.err};
+    v.xr = v.yr = static_cast<T *>(w.rows);
+    v.ldr = round4(nv);
     const SweepPlan<T, NVMAX> sp = make_sweep_plan<T, NVMAX>(op, dv);
     const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * k, size_t(dv.max_leaf_rows) * dv.max_leaf_rows) *
                                          es) + 15) / 16 * 16);
@@ -513,6 +530,8 @@ int launch_tc_pass(const h2_op &op, h2_device &dv, const float *X, float *Y, int
     v.xb = w.xb;
     v.xtb = w.xtb;
     v.np = NVMAX;
+    v.xr = v.yr = static_cast<T *>(w.rows);
+    v.ldr = round4(npass);
     const SweepPlan<T, NVMAX> sp = make_sweep_plan<T, NVMAX>(op, dv);
     set_kernel_attributes<T, NVMAX>();
     cudaEvent_t ev = dv.begin(st);

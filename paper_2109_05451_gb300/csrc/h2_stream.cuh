@@ -78,6 +78,10 @@ struct Vec {
     // upsweep) and of every leaf's permuted input (written by the gather), np rows each
     unsigned char *xb = nullptr, *xtb = nullptr;
     int np = 0;
+    // wide passes: row-major copies of X and of the result in user order ([row][v], ld ldr),
+    // so that the gather and the leaf epilogue move whole rows of nv values
+    T *xr = nullptr, *yr = nullptr;
+    int ldr = 0;
 };
 
 // Bytes of one node's split-BF16 vector tile: np rows (vectors) x 64 bf16, hi then lo.
@@ -375,8 +379,9 @@ struct Acc {
             for (int e = 0; e < VEC; ++e)
                 if (v < nv && e < per && o0 + e < R) a[v][e] += src[v * ld + o0 + e];
     }
-    // The tensor-core path runs its sweeps on the wide accumulator; nothing to write here.
+    // The tensor-core path and the row-major staging run on the wide accumulator only.
     __device__ __forceinline__ void store_tile(unsigned char *, int, int, int) const {}
+    __device__ __forceinline__ void write_rows(T *, int, int, int) const {}
     // Leaf epilogue: user-order rows of the held outputs (fetched before the tile arrives),
     // then Y[v*n + row] = alpha y + beta Y for the threads holding final values.
     int64_t u[VEC];
@@ -543,6 +548,25 @@ struct AccW {
 #pragma unroll
         for (int e = 0; e < 4; ++e) u[e] = o0 + e < R ? perm[r0 + o0 + e] : 0;
     }
+    // Leaf result rows in user order into the row-major buffer: yr[u*ldr + v] = y (the
+    // epilogue alpha y + beta Y follows in k_rows_out). VT consecutive vectors of a row are
+    // one 16-byte store when VT = 4.
+    __device__ __forceinline__ void write_rows(T *yr, int ldr, int nv, int R) const
+    {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (o0 + e >= R) continue;
+            T *d = yr + u[e] * ldr + v0;
+            if (VT == 4 && v0 + 4 <= nv && (ldr & 3) == 0) {
+                const T t[4] = {a[0][e], a[VT > 1 ? 1 : 0][e], a[VT > 2 ? 2 : 0][e], a[VT > 3 ? 3 : 0][e]};
+                store4(d, t);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VT; ++v)
+                    if (v0 + v < nv) d[v] = a[v][e];
+            }
+        }
+    }
     // Split-BF16 B-operand tile of the held block (rows = vectors v < np, columns = outputs):
     // hi = bf16(a), lo = bf16(a - hi), zero for v >= nv or output >= R. Four consecutive
     // outputs are 8 contiguous bytes of one swizzled 16-byte chunk.
@@ -594,7 +618,34 @@ __global__ void k_gather(Op<T> op, Vec<T> vec)
     if (blockIdx.x == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
     for (int64_t leaf = blockIdx.x; leaf < op.nleaves; leaf += gridDim.x) {
         const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
-        if (vec.xtb == nullptr) {
+        if (vec.xr != nullptr) {
+            // whole rows from the row-major copy (coalesced), staged and written per vector
+            __shared__ T rows[64 * 33];
+            for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+                const int i = e / vec.nv, v = e % vec.nv;
+                rows[i * 33 + v] = vec.xr[int64_t(op.perm[r0 + i]) * vec.ldr + v];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+                const int v = e / R, i = e % R;
+                vec.xt[(leaf * vec.vs + v) * op.mp + i] = rows[i * 33 + v];
+            }
+            if constexpr (sizeof(T) == 4) {
+                if (vec.xtb != nullptr) {
+                    unsigned char *tile = vec.xtb + leaf * vec_tile_bytes(vec.np);
+                    for (int e = threadIdx.x; e < vec.np * 64; e += blockDim.x) {
+                        const int i = e % 64, v = e / 64;
+                        const float x = (i < R && v < vec.nv) ? rows[i * 33 + v] : 0.f;
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+                        const uint32_t off = sw128(v, i);
+                        *reinterpret_cast<__nv_bfloat16 *>(tile + off) = hi;
+                        *reinterpret_cast<__nv_bfloat16 *>(tile + vec.np * 128 + off) = lo;
+                    }
+                }
+            }
+            __syncthreads();
+        } else if (vec.xtb == nullptr) {
             for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
                 const int i = e % R, v = e / R;
                 vec.xt[(leaf * vec.vs + v) * op.mp + i] = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
@@ -615,6 +666,56 @@ __global__ void k_gather(Op<T> op, Vec<T> vec)
                 *reinterpret_cast<__nv_bfloat16 *>(tile + off) = hi;
                 *reinterpret_cast<__nv_bfloat16 *>(tile + vec.np * 128 + off) = lo;
             }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ row-major staging
+
+// xr[u*ldr + v] = X[v*n + u] for u < n, v < nv: 32 x 32 tiles through shared memory, so
+// that both sides are read and written along their contiguous index. Block 32 x 8.
+template <typename T>
+__global__ void k_rows_in(const T *__restrict__ X, int64_t n, int nv, T *__restrict__ xr, int ldr)
+{
+    __shared__ T t[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t u0 = int64_t(blockIdx.x) * 32;
+    const int v0 = blockIdx.y * 32;
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t u = u0 + tx;
+        const int v = v0 + j;
+        if (u < n && v < nv) t[j][tx] = X[int64_t(v) * n + u];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t u = u0 + j;
+        const int v = v0 + tx;
+        if (u < n && v < nv) xr[u * ldr + v] = t[tx][j];
+    }
+}
+
+// Epilogue of a wide pass: Y[v*n + u] = alpha yr[u*ldr + v] + beta Y[v*n + u] (Y is not read
+// when beta = 0), through the same 32 x 32 shared-memory tiles.
+template <typename T>
+__global__ void k_rows_out(const T *__restrict__ yr, int ldr, T *__restrict__ Y, int64_t n, int nv, T alpha, T beta)
+{
+    __shared__ T t[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t u0 = int64_t(blockIdx.x) * 32;
+    const int v0 = blockIdx.y * 32;
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t u = u0 + j;
+        const int v = v0 + tx;
+        if (u < n && v < nv) t[j][tx] = yr[u * ldr + v];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t u = u0 + tx;
+        const int v = v0 + j;
+        if (u < n && v < nv) {
+            T *dst = Y + int64_t(v) * n + u;
+            const T y = t[tx][j];
+            *dst = (beta == T(0)) ? alpha * y : alpha * y + beta * *dst;
         }
     }
 }
@@ -922,7 +1023,10 @@ __global__ void __launch_bounds__(kThreads)
             acc.gemv(stage_tile(s, pp, ring.stage), mp, R, k, s.sub + ((1 << L) + j) * wstride, kx, nv);
             if (acc.reduce(R, nv, s.red)) {
                 acc.add(stage_x(s, pp, ring.stage), mp, nv, R);
-                acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
+                if (vec.yr)
+                    acc.write_rows(vec.yr, vec.ldr, nv, R);
+                else
+                    acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
             }
             release(&s.empty[ring.stage], lane);
             ring.next();
