@@ -212,6 +212,52 @@ int h2_get_timing(h2_handle h, double *phase_ms, int64_t *phase_launches, int64_
 /* Free the host operator, its device copy and its workspace. NULL is accepted. */
 int h2_destroy(h2_handle h);
 
+/* ---------------------------------------------------------------- CG serving loop
+ * No paper counterpart as an interface (the paper's application calls its Krylov solver,
+ * Sec. 6.4, inline): a request loop that runs CG solves of (A_H2 + sigma2 I) x = b on
+ * resident operators as requests arrive. Requests wait in FIFO order and are admitted as
+ * soon as a solve slot and enough slot memory are free (admission by device-memory
+ * footprint, h2_server_request_bytes); admitted solves advance concurrently, each on its
+ * own CUDA stream with its own workspace, so a solve admitted while others run overlaps
+ * them on the device (continuous batching). Each solve is unpreconditioned CG from x0 = 0
+ * with FP64 Krylov state and products in the operator's uploaded precision, with the
+ * arithmetic of h2_cg_solve in the same order: a served x equals h2_cg_solve's bitwise and
+ * does not depend on the other requests in flight. One scheduler thread per server; the
+ * calls below may come from any host thread. Operators used by a server must stay uploaded
+ * and alive until their requests complete, and must not have timing enabled. */
+typedef struct h2_server *h2_server_t;
+
+typedef struct {
+    int64_t request_id;
+    int status;          /* H2_OK converged, H2_ENOTCONV maxit reached or breakdown, < 0 error */
+    int iters;           /* CG iterations applied */
+    double true_relres;  /* |b - (A + sigma2 I) x| / |b| from one more product (0 when b = 0) */
+    double t_submit, t_admit, t_done;  /* seconds since h2_server_create, steady clock */
+} h2_request_result;
+
+/* slot_memory_bytes: device memory reserved once for the Krylov state and product workspace
+ * of admitted solves; max_slots >= 1: most solves in flight; max_points: largest n of any
+ * request (sizes each slot's pinned host staging). Binds to the current CUDA device and
+ * starts the scheduler thread. */
+int h2_server_create(size_t slot_memory_bytes, int max_slots, int64_t max_points, h2_server_t *out);
+/* Device bytes one request on this uploaded operator occupies inside a server (0 if h is
+ * NULL or not uploaded). */
+size_t h2_server_request_bytes(h2_handle h);
+/* Queue a solve with relative tolerance tol and at most maxit iterations. b and x: host
+ * arrays of n doubles owned by the caller; b is read when the request is admitted and x
+ * written when it completes, so both must stay valid until its result has been polled.
+ * *request_id identifies the result. Errors: H2_EINVAL (arguments, n > max_points),
+ * H2_ESTATE (operator not uploaded), H2_ENOMEM (the request can never fit the slot memory). */
+int h2_server_submit(h2_server_t s, h2_handle op, double sigma2, const double *b, double *x, double tol, int maxit,
+                     int64_t *request_id);
+/* Move up to max_results completed requests into results (host array) and set *n_results;
+ * never blocks. */
+int h2_server_poll(h2_server_t s, h2_request_result *results, int max_results, int *n_results);
+/* Block until no request is queued or in flight; H2_ETIMEOUT after timeout_s seconds. */
+int h2_server_wait(h2_server_t s, double timeout_s);
+/* Drop queued requests, let the ones in flight finish, stop the scheduler, free all. */
+int h2_server_destroy(h2_server_t s);
+
 /* Static description of a status code. */
 const char *h2_status_str(int status);
 

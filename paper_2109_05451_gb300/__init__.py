@@ -47,6 +47,11 @@ class h2_info(C.Structure):
     ]
 
 
+class h2_request_result(C.Structure):
+    _fields_ = [("request_id", C.c_int64), ("status", C.c_int), ("iters", C.c_int), ("true_relres", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
 # name -> (restype, argtypes); every symbol declared in include/h2.h
 _P, _I64, _I, _D, _SZ = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_size_t
 SIGNATURES = {
@@ -66,6 +71,12 @@ SIGNATURES = {
     "h2_get_timing": (_I, [_P, _P, _P, _P]),
     "h2_destroy": (_I, [_P]),
     "h2_status_str": (C.c_char_p, [_I]),
+    "h2_server_create": (_I, [_SZ, _I, _I64, C.POINTER(_P)]),
+    "h2_server_request_bytes": (_SZ, [_P]),
+    "h2_server_submit": (_I, [_P, _P, _D, _P, _P, _D, _I, C.POINTER(_I64)]),
+    "h2_server_poll": (_I, [_P, C.POINTER(h2_request_result), _I, C.POINTER(_I)]),
+    "h2_server_wait": (_I, [_P, _D]),
+    "h2_server_destroy": (_I, [_P]),
 }
 
 _lib = None
@@ -291,3 +302,59 @@ def _check_colmajor(t, n: int, nv: int, dtype):
         ok = tuple(t.shape) == (n, nv) and t.stride(0) == 1 and (nv == 1 or t.stride(1) == n)
     if not ok:
         raise ValueError("expected an (n, nv) column-major tensor with leading dimension n")
+
+
+class H2Server:
+    """CG serving loop (h2_server_*): solves of (A + sigma2 I) x = b on resident operators,
+    admitted in FIFO order as slots and slot memory free up, running concurrently on the GPU.
+    Holds each request's host arrays until its result is polled."""
+
+    def __init__(self, slot_memory_bytes: int, max_slots: int, max_points: int):
+        h = C.c_void_p()
+        _check(load().h2_server_create(int(slot_memory_bytes), int(max_slots), int(max_points), C.byref(h)),
+               "h2_server_create")
+        self.handle = h.value
+        self._live = {}  # request id -> (b, x)
+
+    @staticmethod
+    def request_bytes(op: "H2Operator") -> int:
+        return int(load().h2_server_request_bytes(op.handle))
+
+    def submit(self, op: "H2Operator", b: np.ndarray, tol: float, maxit: int, sigma2: float = 0.0) -> int:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        if b.shape != (op.n,):
+            raise ValueError("b must have n entries")
+        x = np.empty_like(b)
+        rid = C.c_int64(0)
+        _check(load().h2_server_submit(self.handle, op.handle, float(sigma2), _np_ptr(b), _np_ptr(x), float(tol),
+                                       int(maxit), C.byref(rid)), "h2_server_submit")
+        self._live[rid.value] = (b, x)
+        return rid.value
+
+    def poll(self, max_results: int = 256) -> list:
+        """Completed requests: dicts with id, status, iters, true_relres, times and x."""
+        buf = (h2_request_result * max_results)()
+        n = C.c_int(0)
+        _check(load().h2_server_poll(self.handle, buf, max_results, C.byref(n)), "h2_server_poll")
+        out = []
+        for r in buf[: n.value]:
+            b, x = self._live.pop(r.request_id)
+            out.append({"id": r.request_id, "status": r.status, "iters": r.iters, "true_relres": r.true_relres,
+                        "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done, "x": x})
+        return out
+
+    def wait(self, timeout_s: float = 600.0) -> int:
+        rc = load().h2_server_wait(self.handle, float(timeout_s))
+        _check(rc, "h2_server_wait", allow=(H2_OK, H2_ETIMEOUT))
+        return rc
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().h2_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,99 +12,12 @@
 #include <cmath>
 #include <cstring>
 
+#include "h2_cgk.cuh"
 #include "h2_internal.h"
 
 namespace {
 
-constexpr int kDotBlocks = 256;
-constexpr int kThreads = 256;
-
-int cuda_status(cudaError_t e)
-{
-    if (e == cudaSuccess) return H2_OK;
-    if (e == cudaErrorMemoryAllocation) return H2_ENOMEM;
-    return H2_ECUDA;
-}
-
-// partial[b] = sum over block b's contiguous range of a[i] * c[i], in a fixed order.
-__global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ c, int64_t n,
-                              double *__restrict__ partial)
-{
-    __shared__ double red[kThreads];
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
-    double s = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += a[i] * c[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w /= 2) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-}
-
-__global__ void k_dot_final(const double *__restrict__ partial, int nb, double *__restrict__ out)
-{
-    __shared__ double red[kThreads];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w /= 2) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = red[0];
-}
-
-__global__ void k_to_float(const double *__restrict__ a, float *__restrict__ f, int64_t n)
-{
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        f[i] = float(a[i]);
-}
-
-// Ap = A p + sigma2 p, from the product in float or double.
-template <typename T>
-__global__ void k_shift(const T *__restrict__ Ap_raw, const double *__restrict__ p, double sigma2,
-                        double *__restrict__ Ap, int64_t n)
-{
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        Ap[i] = double(Ap_raw[i]) + sigma2 * p[i];
-}
-
-// r = b - Ax
-__global__ void k_residual(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
-                           double *__restrict__ p, int64_t n)
-{
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const double v = b[i] - Ax[i];
-        r[i] = v;
-        if (p) p[i] = v;
-    }
-}
-
-// alpha = rr / pAp; x += alpha p; r -= alpha Ap
-__global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const double *__restrict__ Ap, const double *__restrict__ scal, int64_t n)
-{
-    const double alpha = scal[0] / scal[1];
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        x[i] += alpha * p[i];
-        r[i] -= alpha * Ap[i];
-    }
-}
-
-// beta = rr_new / rr; p = r + beta p; then rr = rr_new
-__global__ void k_update_p(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ scal,
-                           int64_t n)
-{
-    const double beta = scal[2] / scal[0];
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        p[i] = r[i] + beta * p[i];
-}
-
-__global__ void k_copy_scalar(double *__restrict__ scal, int dst, int src) { scal[dst] = scal[src]; }
+using namespace h2cg;
 
 struct CgState {
     int64_t n;
@@ -114,13 +27,7 @@ struct CgState {
     void *mem;
 };
 
-void dot(const CgState &c, const double *a, const double *b, double *out)
-{
-    k_dot_partial<<<kDotBlocks, kThreads, 0, c.st>>>(a, b, c.n, c.partial);
-    k_dot_final<<<1, kThreads, 0, c.st>>>(c.partial, kDotBlocks, out);
-}
-
-unsigned grid_for(int64_t n) { return unsigned(n / kThreads + 1 < 4096 ? n / kThreads + 1 : 4096); }
+void dot(const CgState &c, const double *a, const double *b, double *out) { h2cg::dot(a, b, c.n, c.partial, out, c.st); }
 
 // out = (A + sigma2 I) v
 int apply(h2_handle h, const CgState &c, const double *v, double *out, double sigma2, bool fp64)

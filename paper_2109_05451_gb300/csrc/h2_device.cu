@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -67,7 +68,8 @@ struct h2_device {
     // handle-owned workspace for h2_matvec
     void *ws = nullptr;
     size_t ws_bytes = 0;
-    // instrumentation (not synchronised between host threads)
+    // instrumentation: the launch and product counters are atomic; the event timing is for
+    // one host thread at a time (leave it off while products run from several threads)
     bool timing = false;
     struct PhaseRec {
         int phase;
@@ -76,8 +78,8 @@ struct h2_device {
     std::vector<cudaEvent_t> event_pool;
     std::vector<PhaseRec> pending;
     double phase_ms[H2_NPHASES] = {};
-    int64_t phase_launches[H2_NPHASES] = {};
-    int64_t products = 0;
+    std::atomic<int64_t> phase_launches[H2_NPHASES] = {};
+    std::atomic<int64_t> products{0};
 
     cudaEvent_t event()
     {
@@ -240,8 +242,10 @@ void set_kernel_attributes()
 
 template <typename T, int NVMAX>
 int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
-                 const Workspace &w, cudaStream_t st)
+                 const Workspace &w, cudaStream_t st, const h2_exec &ex)
 {
+    cudaStream_t side = static_cast<cudaStream_t>(ex.side);
+    cudaEvent_t ev_up = static_cast<cudaEvent_t>(ex.ev_up), ev_top = static_cast<cudaEvent_t>(ex.ev_top);
     using namespace h2s;
     const uint32_t es = sizeof(T);
     const int k = op.k, kx = dv.kx, mp = dv.mp;
@@ -279,8 +283,8 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     dv.end(0, ev, st, 2);
     const bool top = Lb >= 1;
     if (top) {
-        cudaEventRecord(dv.ev_up, st);
-        cudaStreamWaitEvent(dv.side, dv.ev_up, 0);
+        cudaEventRecord(ev_up, st);
+        cudaStreamWaitEvent(side, ev_up, 0);
     }
     // ---- stream A: coupling rows of the lower levels + dense rows
     ev = dv.begin(st);
@@ -290,7 +294,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     dv.end(1, ev, st, dv.n_chunks_bottom > 0 ? 1 : 0);
     // ---- stream B: the levels above the bottom subtrees
     if (top) {
-        cudaStream_t sb = dv.side;
+        cudaStream_t sb = side;
         cudaEvent_t eb = dv.begin(sb);
         int launches = 0;
         for (int lin = Lb; lin > 0;) {
@@ -315,8 +319,8 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
             lr += L + 1;
         }
         dv.end(2, eb, sb, launches);
-        cudaEventRecord(dv.ev_top, sb);
-        cudaStreamWaitEvent(st, dv.ev_top, 0);
+        cudaEventRecord(ev_top, sb);
+        cudaStreamWaitEvent(st, ev_top, 0);
     }
     // ---- stream A: bottom downsweep + leaf expansion + epilogue
     ev = dv.begin(st);
@@ -562,14 +566,14 @@ int launch_tc(const h2_op &op, h2_device &dv, const float *X, float *Y, int nv, 
 
 template <typename T>
 int launch_product(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
-                   const Workspace &w, cudaStream_t st)
+                   const Workspace &w, cudaStream_t st, const h2_exec &ex)
 {
     const int vp = pass_vectors(dv, nv);
     for (int v0 = 0; v0 < nv; v0 += vp) {
         const int c = std::min(vp, nv - v0);
         const size_t o = size_t(v0) * op.n;
-        const int rc = c == 1       ? launch_chunk<T, 1>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
-                     : c <= kChunk  ? launch_chunk<T, kChunk>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+        const int rc = c == 1       ? launch_chunk<T, 1>(op, dv, X + o, Y + o, c, alpha, beta, w, st, ex)
+                     : c <= kChunk  ? launch_chunk<T, kChunk>(op, dv, X + o, Y + o, c, alpha, beta, w, st, ex)
                      : c <= 8       ? launch_wide<T, 8>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
                      : c <= 16      ? launch_wide<T, 16>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
                                     : launch_wide<T, 32>(op, dv, X + o, Y + o, c, alpha, beta, w, st);
@@ -654,6 +658,61 @@ void h2_device_free(h2_op *op)
     delete op->dev;
     op->dev = nullptr;
     if (prev >= 0) cudaSetDevice(prev);
+}
+
+// ---------------------------------------------------------------- internal entry points (h2_internal.h)
+
+int h2_exec_create(h2_exec *ex)
+{
+    if (!ex) return H2_EINVAL;
+    *ex = h2_exec{};
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    cudaStream_t side = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int rc = cuda_status(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi_prio));
+    if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    ex->side = side;
+    ex->ev_up = a;
+    ex->ev_top = b;
+    if (rc != H2_OK) h2_exec_destroy(ex);
+    return rc;
+}
+
+void h2_exec_destroy(h2_exec *ex)
+{
+    if (!ex) return;
+    if (ex->ev_up) cudaEventDestroy(static_cast<cudaEvent_t>(ex->ev_up));
+    if (ex->ev_top) cudaEventDestroy(static_cast<cudaEvent_t>(ex->ev_top));
+    if (ex->side) cudaStreamDestroy(static_cast<cudaStream_t>(ex->side));
+    *ex = h2_exec{};
+}
+
+int h2_matvec_exec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *workspace,
+                   size_t ws_bytes, void *cuda_stream, const h2_exec *exp)
+{
+    if (!h || !X || !Y || nv < 1 || !workspace) return H2_EINVAL;
+    if (!h->dev) return H2_ESTATE;
+    h2_device &dv = *h->dev;
+    if (ws_bytes < ws_layout(*h, dv, nv, nullptr, nullptr)) return H2_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return H2_EINVAL;
+    h2_exec own;
+    own.side = dv.side;
+    own.ev_up = dv.ev_up;
+    own.ev_top = dv.ev_top;
+    const h2_exec &ex = exp ? *exp : own;
+    Workspace w;
+    ws_layout(*h, dv, nv, &w, workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    dv.products += 1;
+    if (dv.tc)
+        return launch_tc(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w, st);
+    if (dv.esize == 8)
+        return launch_product<double>(*h, dv, static_cast<const double *>(X), static_cast<double *>(Y), nv, alpha,
+                                      beta, w, st, ex);
+    return launch_product<float>(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w,
+                                 st, ex);
 }
 
 extern "C" {
@@ -892,9 +951,11 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     if (rc == H2_OK) {
         int lo_prio = 0, hi_prio = 0;
         cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
-        rc = cuda_status(cudaStreamCreateWithPriority(&dv->side, cudaStreamNonBlocking, hi_prio));
-        if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&dv->ev_up, cudaEventDisableTiming));
-        if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&dv->ev_top, cudaEventDisableTiming));
+        h2_exec ex;
+        rc = h2_exec_create(&ex);
+        dv->side = static_cast<cudaStream_t>(ex.side);
+        dv->ev_up = static_cast<cudaEvent_t>(ex.ev_up);
+        dv->ev_top = static_cast<cudaEvent_t>(ex.ev_top);
     }
     if (rc != H2_OK) h2_device_free(&op);
     return rc;
@@ -909,22 +970,7 @@ size_t h2_workspace_bytes(h2_handle h, int nv)
 int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *workspace,
                  size_t ws_bytes, void *cuda_stream)
 {
-    if (!h || !X || !Y || nv < 1 || !workspace) return H2_EINVAL;
-    if (!h->dev) return H2_ESTATE;
-    h2_device &dv = *h->dev;
-    if (ws_bytes < ws_layout(*h, dv, nv, nullptr, nullptr)) return H2_EINVAL;
-    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return H2_EINVAL;
-    Workspace w;
-    ws_layout(*h, dv, nv, &w, workspace);
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    dv.products += 1;
-    if (dv.tc)
-        return launch_tc(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w, st);
-    if (dv.esize == 8)
-        return launch_product<double>(*h, dv, static_cast<const double *>(X), static_cast<double *>(Y), nv, alpha,
-                                      beta, w, st);
-    return launch_product<float>(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w,
-                                 st);
+    return h2_matvec_exec(h, X, Y, nv, alpha, beta, workspace, ws_bytes, cuda_stream, nullptr);
 }
 
 int h2_matvec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *cuda_stream)
@@ -966,12 +1012,12 @@ int h2_get_timing(h2_handle h, double *phase_ms, int64_t *phase_launches, int64_
     dv.drain();
     for (int i = 0; i < H2_NPHASES; ++i) {
         if (phase_ms) phase_ms[i] = dv.phase_ms[i];
-        if (phase_launches) phase_launches[i] = dv.phase_launches[i];
+        const int64_t l = dv.phase_launches[i].exchange(0);
+        if (phase_launches) phase_launches[i] = l;
         dv.phase_ms[i] = 0;
-        dv.phase_launches[i] = 0;
     }
-    if (products) *products = dv.products;
-    dv.products = 0;
+    const int64_t pr = dv.products.exchange(0);
+    if (products) *products = pr;
     int flag = 0;
     if (cudaMemcpy(&flag, dv.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ECUDA;
     return flag ? H2_ETIMEOUT : H2_OK;

@@ -40,6 +40,23 @@ struct h2_op {
     h2_device *dev = nullptr;
 };
 
+// Fork/join context of one product: the high-priority side stream that runs the upper tree
+// levels next to the main stream, and the two events that order them (cudaStream_t /
+// cudaEvent_t, kept opaque here). Each handle owns one for h2_matvec / h2_matvec_ws; callers
+// that run products of one handle concurrently on several streams give each its own.
+struct h2_exec {
+    void *side = nullptr;
+    void *ev_up = nullptr;
+    void *ev_top = nullptr;
+};
+
+// h2_device.cu
+int h2_exec_create(h2_exec *ex);
+void h2_exec_destroy(h2_exec *ex);
+// h2_matvec_ws with an explicit fork/join context (nullptr: the handle's own).
+int h2_matvec_exec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *workspace,
+                   size_t ws_bytes, void *cuda_stream, const h2_exec *ex);
+
 // h2_host.cpp
 int h2_host_build(h2_op *op, const double *points, int64_t n, int dim, h2_kernel kernel,
                   int leaf_size, int cheb_order, double eta);

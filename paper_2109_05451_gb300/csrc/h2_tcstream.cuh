@@ -72,12 +72,12 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int np, int ns)
 template <int NP>
 __global__ void __launch_bounds__(kTcThreads, 1) k_stream_tc(TcArgs a)
 {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
     constexpr uint32_t kVecBytes = 2u * NP * 128u;  // hi + lo tiles of one node's vectors
     constexpr uint32_t kStage = kTcTileBytes + kVecBytes;
     const int ns = a.ns;
     // layout: stages (1 KB aligned) | row exchange | descriptors | barriers | TMEM address | flags
-    unsigned char *stages = smem_raw;
+    unsigned char *stages = tc_smem;
     float *xch = reinterpret_cast<float *>(stages + size_t(ns) * kStage);  // [2][NP][64]
     StreamDesc *sdesc = reinterpret_cast<StreamDesc *>(xch + 2 * 64 * NP);
     StreamDesc *dbuf = sdesc + ns;  // [2][kChunkDesc]

@@ -123,3 +123,23 @@ def test_info_counts_for_grid64():
         assert info.basis_entries == 4096 * 16 and info.uploaded_prec == -1
     finally:
         h2.h2_destroy(h)
+
+
+def test_server_calls_reject_bad_arguments_before_cuda():
+    lib = h2.load()
+    out = C.c_void_p()
+    assert lib.h2_server_create(0, 2, 1000, C.byref(out)) == h2.H2_EINVAL
+    assert lib.h2_server_create(1 << 20, 0, 1000, C.byref(out)) == h2.H2_EINVAL
+    assert lib.h2_server_create(1 << 20, 2, 0, C.byref(out)) == h2.H2_EINVAL
+    rid = C.c_int64(0)
+    b = np.zeros(4)
+    assert lib.h2_server_submit(None, None, 0.0, h2._np_ptr(b), h2._np_ptr(b), 1e-6, 10, C.byref(rid)) == h2.H2_EINVAL
+    n = C.c_int(0)
+    assert lib.h2_server_poll(None, None, 0, C.byref(n)) == h2.H2_EINVAL
+    assert lib.h2_server_wait(None, 1.0) == h2.H2_EINVAL
+    assert lib.h2_server_destroy(None) == h2.H2_EINVAL
+    h = h2.h2_build(si.grid_2d(16), ("exp", 0.1, 0, 0), 16, 4, 0.7)
+    try:
+        assert lib.h2_server_request_bytes(h) == 0  # not uploaded
+    finally:
+        h2.h2_destroy(h)

@@ -1,0 +1,156 @@
+"""GPU tests of the CG serving loop (h2_server_*): continuous batching of CG solves on
+resident operators.
+
+A served solve runs the arithmetic of h2_cg_solve in the same order, so its x, iteration
+count and true residual equal h2_cg_solve's (x0 = 0) bitwise, in every precision; a request
+gives the same result alone and in a mix of concurrent requests; admission never lets the
+requests in flight exceed the slot memory; caps and degenerate right-hand sides behave as
+h2_cg_solve's do. The converged residual is re-checked with the oracle's product.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2109_05451_gb300 as h2  # noqa: E402
+
+SIGMA2 = 0.1
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "bf16x2": 1e-4}
+SPECS = {
+    "grid64_fp64": (lambda: si.grid_2d(64), ("exp", 0.1, 0, 0), 64, 4, 0.9, "fp64"),
+    "grid50_fp32": (lambda: si.grid_2d(50), ("exp", 0.1, 0, 0), 32, 4, 0.9, "fp32"),
+    "cloud2d_fp32": (lambda: si.uniform_cloud(3000, 2, 3), ("exp", 0.1, 0, 0), 64, 6, 0.7, "fp32"),
+    "cloud3d_bf16x2": (lambda: si.uniform_cloud(4000, 3, 4), ("exp", 0.2, 0, 0), 64, 4, 0.7, "bf16x2"),
+}
+
+
+@pytest.fixture(scope="module")
+def ops():
+    out = {}
+    for name, (mk, ker, m, p, eta, prec) in SPECS.items():
+        pts = mk()
+        out[name] = (h2.H2Operator(pts, ker, m, p, eta).upload(prec), prec, pts)
+    yield out
+    for op, _, _ in out.values():
+        op.close()
+
+
+def rhs(n, seed):
+    return si.gaussian_vectors(n, 1, seed)[:, 0].copy()
+
+
+def reference_solve(op, b, tol, maxit):
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    rc, it, rr = h2.h2_cg_solve(op.handle, SIGMA2, bd, xd, tol, maxit)
+    torch.cuda.synchronize()
+    return rc, it, rr, xd.cpu().numpy()
+
+
+def serve_all(server, jobs, timeout=300.0):
+    """jobs: list of (op, b, tol, maxit); returns results in submission order."""
+    ids = [server.submit(op, b, tol, maxit, SIGMA2) for op, b, tol, maxit in jobs]
+    assert server.wait(timeout) == h2.H2_OK
+    got = {r["id"]: r for r in server.poll(len(ids) + 8)}
+    assert sorted(got) == sorted(ids)
+    return [got[i] for i in ids]
+
+
+@pytest.mark.parametrize("name", sorted(SPECS))
+def test_served_solve_equals_h2_cg_solve(ops, name):
+    op, prec, _ = ops[name]
+    b = rhs(op.n, 5)
+    server = h2.H2Server(4 * h2.H2Server.request_bytes(op), 2, op.n)
+    try:
+        (r,) = serve_all(server, [(op, b, TOL[prec], 500)])
+    finally:
+        server.close()
+    rc, it, rr, x = reference_solve(op, b, TOL[prec], 500)
+    assert r["status"] == rc == h2.H2_OK
+    assert r["iters"] == it > 0
+    assert r["true_relres"] == rr
+    assert np.array_equal(r["x"], x)
+
+
+def test_result_same_alone_and_in_a_mix(ops):
+    names = sorted(SPECS)
+    jobs = []
+    for j in range(16):
+        op, prec, _ = ops[names[j % len(names)]]
+        jobs.append((op, rhs(op.n, 100 + j), TOL[prec], 400))
+    probe = (ops["cloud2d_fp32"][0], rhs(ops["cloud2d_fp32"][0].n, 999), 1e-5, 400)
+    big = max(h2.H2Server.request_bytes(op) for op, _, _ in ops.values())
+    server = h2.H2Server(6 * big, 4, 5000)
+    try:
+        (alone,) = serve_all(server, [probe])
+        mixed = serve_all(server, jobs[:7] + [probe] + jobs[7:] + [probe])
+    finally:
+        server.close()
+    for r in (mixed[7], mixed[-1]):
+        assert r["status"] == alone["status"] and r["iters"] == alone["iters"]
+        assert np.array_equal(r["x"], alone["x"])
+    # the mix really overlapped on the device: some request was admitted while another ran
+    spans = sorted((r["t_admit"], r["t_done"]) for r in mixed)
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+    assert all(r["status"] == h2.H2_OK for r in mixed)
+
+
+def test_admission_respects_slot_memory(ops):
+    op_big = ops["cloud3d_bf16x2"][0]
+    op_small = ops["grid50_fp32"][0]
+    tiny = h2.H2Server(h2.H2Server.request_bytes(op_small), 1, 5000)
+    try:
+        with pytest.raises(h2.H2Error) as e:  # can never fit: refused at submission
+            tiny.submit(op_big, rhs(op_big.n, 1), 1e-4, 10)
+        assert e.value.status == h2.H2_ENOMEM
+    finally:
+        tiny.close()
+    cap = int(1.5 * h2.H2Server.request_bytes(op_big))
+    server = h2.H2Server(cap, 4, 5000)
+    try:
+        jobs = [(op_big if j % 2 == 0 else op_small, rhs((op_big if j % 2 == 0 else op_small).n, 200 + j), 1e-4, 60)
+                for j in range(8)]
+        res = serve_all(server, jobs)
+    finally:
+        server.close()
+    need = [h2.H2Server.request_bytes(op) for op, _, _, _ in jobs]
+    for i in range(len(res)):
+        live = [need[j] for j in range(len(res)) if res[j]["t_admit"] <= res[i]["t_admit"] < res[j]["t_done"]]
+        assert sum(live) <= cap
+    assert all(r["status"] in (h2.H2_OK, h2.H2_ENOTCONV) for r in res)
+
+
+def test_caps_and_degenerate_right_hand_sides(ops):
+    op, prec, _ = ops["cloud2d_fp32"]
+    b = rhs(op.n, 3)
+    server = h2.H2Server(4 * h2.H2Server.request_bytes(op), 2, op.n)
+    try:
+        capped, zero_b, no_it = serve_all(server, [(op, b, 1e-12, 3), (op, np.zeros(op.n), 1e-6, 50), (op, b, 1e-6, 0)])
+    finally:
+        server.close()
+    rc, it, rr, x = reference_solve(op, b, 1e-12, 3)
+    assert capped["status"] == rc == h2.H2_ENOTCONV and capped["iters"] == it == 3
+    assert np.array_equal(capped["x"], x) and capped["true_relres"] == rr
+    assert zero_b["status"] == h2.H2_OK and zero_b["iters"] == 0 and zero_b["true_relres"] == 0.0
+    assert not np.any(zero_b["x"])
+    assert no_it["status"] == h2.H2_ENOTCONV and no_it["iters"] == 0 and not np.any(no_it["x"])
+
+
+def test_converged_residual_checked_with_the_oracle(ops):
+    op, prec, pts = ops["grid64_fp64"]
+    mk, ker, m, p, eta, _ = SPECS["grid64_fp64"]
+    orc = oracle.OracleH2(pts, ker, m, p, eta)
+    b = rhs(op.n, 11)
+    server = h2.H2Server(4 * h2.H2Server.request_bytes(op), 1, op.n)
+    try:
+        (r,) = serve_all(server, [(op, b, 1e-10, 500)])
+    finally:
+        server.close()
+    assert r["status"] == h2.H2_OK
+    x = r["x"]
+    res = b - (orc.matvec(x[:, None])[:, 0] + SIGMA2 * x)
+    assert np.linalg.norm(res) / np.linalg.norm(b) <= 1e-9
