@@ -224,6 +224,71 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None):
     return out
 
 
+def serve_benchmark(h2, torch, requests_per_rate=32, maxit=100, rates=(0.5, 0.8, 1.0, 1.2), slots=8):
+    """CG serving loop (h2_server_*): solves of (K + 1e-2 I) x = b with tol 1e-6 on resident
+    operators of uniform random points in [0,1]^2 (N = 2^14, 2^16, 2^18, 2^20), kernel
+    (r^2 + 1e-4)^(-1.5), leaf 64, 8 x 8 Chebyshev grid (rank 64), eta 0.7, FP32 products and
+    FP64 Krylov state; b ~ N(0,1); sizes drawn uniformly; Poisson arrivals at the given
+    fractions of the one-at-a-time capacity. CG is capped at maxit iterations (this kernel's
+    conditioning puts tol 1e-6 far beyond any serving budget without a preconditioner: dense
+    FP64 CG needs ~6000 iterations at N = 2^14 and ~13x more per 4x in N), so the converged
+    fraction and the achieved true residuals are reported beside the latencies."""
+    sizes = [2 ** 14, 2 ** 16, 2 ** 18, 2 ** 20]
+    tol, sigma2 = 1e-6, 1e-2
+    ops = {n: h2.H2Operator(si.uniform_cloud(n, 2, 50 + i), ("imq", 1e-4, 1.5, 0), 64, 8, 0.7).upload("fp32")
+           for i, n in enumerate(sizes)}
+    big = max(h2.H2Server.request_bytes(o) for o in ops.values())
+    server = h2.H2Server(slots * big, slots, max(sizes))
+    try:
+        def rhs(n, seed):
+            return si.gaussian_vectors(n, 1, seed)[:, 0].copy()
+
+        # warm-up and one-at-a-time capacity (each size alone, sizes uniform)
+        alone = {}
+        for rep in range(2):
+            for n, op in ops.items():
+                server.submit(op, rhs(n, 7), tol, maxit, sigma2)
+                server.wait()
+                (r,) = server.poll()
+                alone[n] = r["t_done"] - r["t_submit"]
+        capacity = 1.0 / float(np.mean(list(alone.values())))
+        rng = np.random.default_rng(2026)
+        per_rate = []
+        for f in rates:
+            lam = f * capacity
+            gaps = rng.exponential(1.0 / lam, requests_per_rate)
+            pick = rng.integers(0, len(sizes), requests_per_rate)
+            bs = [rhs(sizes[k], 1000 + j) for j, k in enumerate(pick)]
+            t0 = time.perf_counter()
+            t = 0.0
+            for j in range(requests_per_rate):
+                t += gaps[j]
+                delay = t0 + t - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                server.submit(ops[sizes[pick[j]]], bs[j], tol, maxit, sigma2)
+            server.wait(600.0)
+            res = server.poll(requests_per_rate + 8)
+            lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+            wait_q = np.array([r["t_admit"] - r["t_submit"] for r in res])
+            span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+            per_rate.append({
+                "offered_fraction": f, "offered_solves_per_s": lam, "requests": len(res),
+                "solves_per_s": len(res) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_queue_ms": 1e3 * float(wait_q.mean()),
+                "mean_iters": float(np.mean([r["iters"] for r in res])),
+                "converged_fraction": float(np.mean([r["status"] == h2.H2_OK for r in res])),
+                "median_true_relres": float(np.median([r["true_relres"] for r in res]))})
+        return {"workload": "imq_cloud2d {2^14,2^16,2^18,2^20}, (r^2+1e-4)^-1.5, rank 64, sigma2 1e-2, tol 1e-6",
+                "maxit": maxit, "slots": slots, "precision": "fp32 products, fp64 Krylov state",
+                "alone_ms": {str(n): 1e3 * v for n, v in alone.items()},
+                "capacity_solves_per_s": capacity, "rates": per_rate}
+    finally:
+        server.close()
+        for op in ops.values():
+            op.close()
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -254,6 +319,9 @@ def main():
                     help="points of the 3D cloud of the 32-vector measurement (2^21 = the benchmarked size; "
                          "smaller sizes are for profiler captures)")
     ap.add_argument("--multi-rhs-steps", type=int, default=0, help="timed 32-vector products (0: steps / 20, >= 5)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the CG serving-loop measurement")
+    ap.add_argument("--serve-maxit", type=int, default=100, help="CG iteration cap of each served solve")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate")
     ap.add_argument("--grid", type=int, default=1024,
                     help="grid side of the 2D Gaussian workload (1024 = the benchmarked N = 2^20; smaller "
                          "sides are for profiler captures)")
@@ -406,6 +474,11 @@ def main():
             line["multi_rhs"] = multi_rhs(h2, torch, mr_steps, 3, peak_hbm, peak_kind, args.cloud_n)
         except Exception as exc:  # reported, never silently dropped
             line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if not args.no_serve:
+        try:
+            line["serve"] = serve_benchmark(h2, torch, args.serve_requests, args.serve_maxit)
+        except Exception as exc:  # reported, never silently dropped
+            line["serve"] = {"error": f"{type(exc).__name__}: {exc}"}
     if res_fp64 is not None:
         ms64 = float(np.mean(res_fp64["step_ms"]))
         b64 = 8 * (mat_entries + vec_elems)
