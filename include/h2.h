@@ -212,6 +212,34 @@ int h2_get_timing(h2_handle h, double *phase_ms, int64_t *phase_launches, int64_
 /* Free the host operator, its device copy and its workspace. NULL is accepted. */
 int h2_destroy(h2_handle h);
 
+/* ---------------------------------------------------------------- batched products
+ * Many products of uneven operators as one unit (no paper counterpart as an interface: the
+ * batched, level-by-level marshaling of Sec. 3 runs inside one operator there). For each
+ * member i: Y_i = alpha A_i X_i + beta Y_i with nv[i] vectors (device, column-major, ld = n_i,
+ * element type of the uploads). The members' coupling and dense block rows of every level
+ * form one work list that a persistent launch streams (one launch per width class of nv:
+ * 1, 2-4, 5-8, 9-16, 17-32); the members' upsweeps and downsweeps run on parallel branches
+ * before and after it. The whole product is captured once as a CUDA graph and replayed by
+ * h2_batch_run, always with the X, Y, alpha and beta given here (update the contents of X
+ * and Y between runs, not the pointers). All members share one precision, FP64 or FP32 (not
+ * H2_BF16X2), and take one pass each (nv <= 4, or nv <= 32 when k <= 64 and leaves hold <= 64
+ * points); members must stay uploaded and alive while the batch exists.
+ * flags: H2_BATCH_AUTOTUNE times candidate launch configurations of each merged stream (CTAs
+ * per SM, pipeline stages, scheduling chunk size) and appends the best to the autotuning
+ * cache (the file named by the environment variable H2_TUNE_CACHE, else h2_autotune.txt next
+ * to the library); without it a cached choice is used when present, else a default. */
+typedef struct h2_batch *h2_batch_t;
+#define H2_BATCH_AUTOTUNE 1
+int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void *const *Y, const int *nv, double alpha,
+                    double beta, int flags, h2_batch_t *out);
+/* Replay the batched product on the stream (asynchronous). */
+int h2_batch_run(h2_batch_t b, void *cuda_stream);
+/* After a synchronize: H2_ETIMEOUT if a bounded wait of any kernel of the batch ran out. */
+int h2_batch_check(h2_batch_t b);
+/* One-line description of the groups and their launch configurations (NUL-terminated). */
+int h2_batch_describe(h2_batch_t b, char *buf, size_t len);
+int h2_batch_destroy(h2_batch_t b);
+
 /* ---------------------------------------------------------------- CG serving loop
  * No paper counterpart as an interface (the paper's application calls its Krylov solver,
  * Sec. 6.4, inline): a request loop that runs CG solves of (A_H2 + sigma2 I) x = b on

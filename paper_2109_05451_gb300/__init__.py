@@ -71,6 +71,12 @@ SIGNATURES = {
     "h2_get_timing": (_I, [_P, _P, _P, _P]),
     "h2_destroy": (_I, [_P]),
     "h2_status_str": (C.c_char_p, [_I]),
+    "h2_batch_create": (_I, [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_I), _D, _D, _I,
+                             C.POINTER(_P)]),
+    "h2_batch_run": (_I, [_P, _P]),
+    "h2_batch_check": (_I, [_P]),
+    "h2_batch_describe": (_I, [_P, C.c_char_p, _SZ]),
+    "h2_batch_destroy": (_I, [_P]),
     "h2_server_create": (_I, [_SZ, _I, _I64, C.POINTER(_P)]),
     "h2_server_request_bytes": (_SZ, [_P]),
     "h2_server_submit": (_I, [_P, _P, _D, _P, _P, _D, _I, C.POINTER(_I64)]),
@@ -351,6 +357,57 @@ class H2Server:
     def close(self):
         if getattr(self, "handle", None):
             load().h2_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+H2_BATCH_AUTOTUNE = 1
+
+
+class H2Batch:
+    """Batched products of uneven operators (h2_batch_*): Y_i = alpha A_i X_i + beta Y_i for
+    every member, captured once as a CUDA graph and replayed by run(). Xs, Ys: CUDA tensors
+    (n_i, nv_i), column-major, of the members' element type; kept alive by the batch."""
+
+    def __init__(self, ops, Xs, Ys, alpha: float = 1.0, beta: float = 0.0, autotune: bool = False):
+        if not (len(ops) == len(Xs) == len(Ys)) or not ops:
+            raise ValueError("ops, Xs and Ys must have the same nonzero length")
+        nvs = []
+        for op, X, Y in zip(ops, Xs, Ys):
+            nv = 1 if X.dim() == 1 else X.shape[1]
+            _check_colmajor(X, op.n, nv, op.dtype)
+            _check_colmajor(Y, op.n, nv, op.dtype)
+            nvs.append(nv)
+        n = len(ops)
+        hs = (C.c_void_p * n)(*[op.handle for op in ops])
+        xs = (C.c_void_p * n)(*[X.data_ptr() for X in Xs])
+        ys = (C.c_void_p * n)(*[Y.data_ptr() for Y in Ys])
+        nv_arr = (C.c_int * n)(*nvs)
+        h = C.c_void_p()
+        _check(load().h2_batch_create(hs, n, xs, ys, nv_arr, float(alpha), float(beta),
+                                      H2_BATCH_AUTOTUNE if autotune else 0, C.byref(h)), "h2_batch_create")
+        self.handle = h.value
+        self._keep = (list(ops), list(Xs), list(Ys))
+
+    def run(self, stream=None):
+        _check(load().h2_batch_run(self.handle, _stream_ptr(stream)), "h2_batch_run")
+
+    def check(self):
+        _check(load().h2_batch_check(self.handle), "h2_batch_check")
+
+    def describe(self) -> str:
+        buf = C.create_string_buffer(4096)
+        _check(load().h2_batch_describe(self.handle, buf, 4096), "h2_batch_describe")
+        return buf.value.decode()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().h2_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -26,6 +26,16 @@
 #include "h2_kernels.cuh"
 #include "h2_stream.cuh"
 #include "h2_tcstream.cuh"
+#include "h2_batch.cuh"
+
+#include <dlfcn.h>
+
+#include <chrono>
+#include <cstdlib>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
 
 namespace {
 
@@ -61,6 +71,7 @@ struct h2_device {
     int64_t *chunks_bottom = nullptr, *chunks_top = nullptr;  // (first << 16) | count
     int grid_bottom = 0, grid_top = 0;
     int64_t n_chunks_bottom = 0, n_chunks_top = 0;
+    int64_t n_desc_bottom = 0, n_desc_top = 0;
     int *err = nullptr;  // device error flag (a bounded wait ran out)
     // execution resources
     cudaStream_t side = nullptr;
@@ -645,6 +656,378 @@ bool make_chunks(const std::vector<h2s::StreamDesc> &d, const std::vector<uint64
     return true;
 }
 
+// ---------------------------------------------------------------- batched products
+
+// Width class of a pass of nv vectors (the accumulator the kernels instantiate).
+int width_class(int nv) { return nv == 1 ? 1 : nv <= kChunk ? kChunk : nv <= 8 ? 8 : nv <= 16 ? 16 : 32; }
+
+// Launch configuration of one merged stream: CTAs per SM, pipeline stages, chunk target.
+struct StreamCfg {
+    int per_sm = 1;
+    int ns = 0;
+    uint64_t chunk_target = 512 * 1024;
+};
+
+// Autotuner cache: one line per key, "key per_sm ns chunk_target ms", in the file named by
+// H2_TUNE_CACHE or else beside libh2.so.
+std::string tune_cache_path()
+{
+    if (const char *e = std::getenv("H2_TUNE_CACHE")) return e;
+    Dl_info info;
+    if (dladdr(reinterpret_cast<void *>(&tune_cache_path), &info) && info.dli_fname) {
+        std::string f = info.dli_fname;
+        const size_t slash = f.rfind('/');
+        return (slash == std::string::npos ? std::string(".") : f.substr(0, slash)) + "/h2_autotune.txt";
+    }
+    return "h2_autotune.txt";
+}
+
+std::mutex &tune_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+
+bool tune_lookup(const std::string &key, StreamCfg *cfg)
+{
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    std::ifstream in(tune_cache_path());
+    std::string line;
+    bool found = false;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        std::string k;
+        StreamCfg c;
+        double ms = 0;
+        if (ls >> k >> c.per_sm >> c.ns >> c.chunk_target >> ms && k == key) {
+            *cfg = c;  // the last entry for a key wins
+            found = true;
+        }
+    }
+    return found;
+}
+
+void tune_store(const std::string &key, const StreamCfg &c, double ms)
+{
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    std::ofstream out(tune_cache_path(), std::ios::app);
+    if (out) out << key << ' ' << c.per_sm << ' ' << c.ns << ' ' << c.chunk_target << ' ' << ms << '\n';
+}
+
+}  // namespace
+
+// A batch: every member's workspace, the merged descriptor list of each width class and
+// the captured graph of the whole batched product.
+struct h2_batch {
+    struct Member {
+        h2_handle op;
+        const void *X;
+        void *Y;
+        int nv;
+        Workspace w;
+    };
+    struct Group {
+        int width = 0;
+        std::vector<int> members;            // indices into members
+        std::vector<h2s::StreamDesc> desc;   // merged, host
+        std::vector<uint64_t> bytes;         // streamed bytes per descriptor
+        h2s::StreamDesc *d_desc = nullptr;
+        int64_t *d_chunks = nullptr;
+        size_t chunk_cap = 0;                // capacity of d_chunks (records)
+        int64_t nchunks = 0;
+        void *d_ops = nullptr;               // BatchOp<T>[members]
+        uint32_t tile_bytes = 0, x_bytes = 0;
+        StreamCfg cfg;
+        bool tuned = false;
+    };
+    int device = 0, num_sms = 0;
+    size_t esize = 4;
+    double alpha = 1, beta = 0;
+    std::vector<Member> members;
+    std::vector<Group> groups;
+    void *ws_mem = nullptr;
+    int *d_flags = nullptr;                  // [0..15] tickets per group, [16] error flag
+    std::vector<cudaStream_t> branches;
+    std::vector<cudaEvent_t> ev_branch;
+    cudaEvent_t ev_fork = nullptr, ev_mid = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+template <typename T, int NV>
+void batch_member_up(h2_batch::Member &m, double alpha, double beta, cudaStream_t st, bool up)
+{
+    using namespace h2s;
+    const h2_op &op = *m.op;
+    h2_device &dv = *op.dev;
+    const Op<T> o = make_op<T>(op, dv);
+    Vec<T> v{static_cast<const T *>(m.X), static_cast<T *>(m.Y), m.nv, m.nv, T(alpha), T(beta), static_cast<T *>(m.w.xt),
+             static_cast<T *>(m.w.yd), static_cast<T *>(m.w.xh), static_cast<T *>(m.w.yh), m.w.tickets, dv.err};
+    if (NV >= kWideMin) {
+        v.xr = v.yr = static_cast<T *>(m.w.rows);
+        v.ldr = round4(m.nv);
+    }
+    if (up)
+        up_all(op, dv, o, v, make_sweep_plan<T, NV>(op, dv), st);
+    else
+        down_all(op, dv, o, v, make_sweep_plan<T, NV>(op, dv), st);
+}
+
+// One member's upsweep (gather included) or downsweep (alpha y + beta Y included).
+template <typename T>
+void batch_member_sweep(const h2_batch &b, h2_batch::Member &m, cudaStream_t st, bool up)
+{
+    switch (width_class(m.nv)) {
+    case 1: set_kernel_attributes<T, 1>(); return batch_member_up<T, 1>(m, b.alpha, b.beta, st, up);
+    case kChunk: set_kernel_attributes<T, kChunk>(); return batch_member_up<T, kChunk>(m, b.alpha, b.beta, st, up);
+    case 8: set_kernel_attributes<T, 8>(); return batch_member_up<T, 8>(m, b.alpha, b.beta, st, up);
+    case 16: set_kernel_attributes<T, 16>(); return batch_member_up<T, 16>(m, b.alpha, b.beta, st, up);
+    default: set_kernel_attributes<T, 32>(); return batch_member_up<T, 32>(m, b.alpha, b.beta, st, up);
+    }
+}
+
+template <typename T, int NV>
+int batch_group_stream(h2_batch &b, h2_batch::Group &g, int gi, cudaStream_t st)
+{
+    using namespace h2s;
+    if (g.nchunks == 0) return H2_OK;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_stream_batch<T, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_stream_batch<T, NV>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr = true;
+    }
+    const Pipe p{g.cfg.ns, g.tile_bytes, g.x_bytes};
+    const size_t smem = smem_bytes<T, NV>(p, 0, 0, true);
+    const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(b.num_sms) * g.cfg.per_sm, g.nchunks)));
+    k_stream_batch<T, NV><<<grid, kThreads, smem, st>>>(static_cast<const BatchOp<T> *>(g.d_ops), p, g.d_desc,
+                                                        g.d_chunks, g.nchunks, b.d_flags + gi, b.d_flags + 16);
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+int batch_group_stream_any(h2_batch &b, h2_batch::Group &g, int gi, cudaStream_t st)
+{
+    switch (g.width) {
+    case 1: return batch_group_stream<T, 1>(b, g, gi, st);
+    case kChunk: return batch_group_stream<T, kChunk>(b, g, gi, st);
+    case 8: return batch_group_stream<T, 8>(b, g, gi, st);
+    case 16: return batch_group_stream<T, 16>(b, g, gi, st);
+    default: return batch_group_stream<T, 32>(b, g, gi, st);
+    }
+}
+
+template <typename T>
+size_t batch_group_smem(const h2_batch::Group &g, int ns)
+{
+    const h2s::Pipe p{ns, g.tile_bytes, g.x_bytes};
+    switch (g.width) {
+    case 1: return h2s::smem_bytes<T, 1>(p, 0, 0, true);
+    case kChunk: return h2s::smem_bytes<T, kChunk>(p, 0, 0, true);
+    case 8: return h2s::smem_bytes<T, 8>(p, 0, 0, true);
+    case 16: return h2s::smem_bytes<T, 16>(p, 0, 0, true);
+    default: return h2s::smem_bytes<T, 32>(p, 0, 0, true);
+    }
+}
+
+// Stages for per_sm CTAs per SM (budget 200 KB / 110 KB / 72 KB), at most 12; 0 if < 2 fit.
+template <typename T>
+int batch_stages(const h2_batch::Group &g, int per_sm)
+{
+    const size_t budget = per_sm == 1 ? 200 * 1024 : per_sm == 2 ? 110 * 1024 : 72 * 1024;
+    for (int ns = 12; ns >= 2; --ns)
+        if (batch_group_smem<T>(g, ns) <= budget) return ns;
+    return 0;
+}
+
+int batch_set_chunks(h2_batch::Group &g, uint64_t target)
+{
+    std::vector<int64_t> ch;
+    if (!make_chunks(g.desc, g.bytes, target, ch)) return H2_EINVAL;
+    if (ch.size() > g.chunk_cap) return H2_EINVAL;
+    g.nchunks = int64_t(ch.size());
+    if (!ch.empty()) {
+        const int rc = cuda_status(cudaMemcpy(g.d_chunks, ch.data(), ch.size() * 8, cudaMemcpyHostToDevice));
+        if (rc != H2_OK) return rc;
+    }
+    g.cfg.chunk_target = target;
+    return H2_OK;
+}
+
+// The whole batched product on the capture stream: upsweeps on branch streams, the merged
+// streams after all of them, downsweeps on the branches, joined back. Without the
+// downsweeps (with_down false) nothing of the members' X and Y is written.
+template <typename T>
+int batch_enqueue(h2_batch &b, cudaStream_t st, bool with_down = true)
+{
+    int rc = cuda_status(cudaEventRecord(b.ev_fork, st));
+    const size_t nb = b.branches.size();
+    for (size_t i = 0; rc == H2_OK && i < b.members.size(); ++i) {
+        cudaStream_t br = b.branches[i % nb];
+        if (i < nb) cudaStreamWaitEvent(br, b.ev_fork, 0);
+        batch_member_sweep<T>(b, b.members[i], br, true);
+    }
+    if (rc == H2_OK) rc = cuda_status(cudaGetLastError());
+    for (size_t j = 0; rc == H2_OK && j < std::min(nb, b.members.size()); ++j) {
+        cudaEventRecord(b.ev_branch[j], b.branches[j]);
+        cudaStreamWaitEvent(st, b.ev_branch[j], 0);
+    }
+    if (rc == H2_OK) rc = cuda_status(cudaMemsetAsync(b.d_flags, 0, 16 * sizeof(int), st));
+    for (size_t gi = 0; rc == H2_OK && gi < b.groups.size(); ++gi)
+        rc = batch_group_stream_any<T>(b, b.groups[gi], int(gi), st);
+    if (rc == H2_OK) rc = cuda_status(cudaEventRecord(b.ev_mid, st));
+    for (size_t i = 0; rc == H2_OK && with_down && i < b.members.size(); ++i) {
+        cudaStream_t br = b.branches[i % nb];
+        if (i < nb) cudaStreamWaitEvent(br, b.ev_mid, 0);
+        batch_member_sweep<T>(b, b.members[i], br, false);
+    }
+    for (size_t j = 0; rc == H2_OK && with_down && j < std::min(nb, b.members.size()); ++j) {
+        cudaEventRecord(b.ev_branch[j], b.branches[j]);
+        cudaStreamWaitEvent(st, b.ev_branch[j], 0);
+    }
+    if (rc == H2_OK) rc = cuda_status(cudaGetLastError());
+    return rc;
+}
+
+// Time one merged stream configuration (median of three launches after one warm-up).
+template <typename T>
+double batch_time_group(h2_batch &b, size_t gi, cudaStream_t st)
+{
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<float> ms;
+    for (int r = 0; r < 4; ++r) {
+        cudaMemsetAsync(b.d_flags + gi, 0, sizeof(int), st);
+        cudaEventRecord(e0, st);
+        batch_group_stream_any<T>(b, b.groups[gi], int(gi), st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0) ms.push_back(t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::sort(ms.begin(), ms.end());
+    return cudaGetLastError() == cudaSuccess ? ms[ms.size() / 2] : 1e30;
+}
+
+template <typename T>
+std::string batch_tune_key(const h2_batch &b, const h2_batch::Group &g)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, b.device);
+    std::string name = prop.name;
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    uint64_t total = 0;
+    for (uint64_t x : g.bytes) total += x;
+    int lg = 0;
+    while ((uint64_t(1) << (lg + 1)) <= total) ++lg;  // log2 of the streamed bytes
+    std::ostringstream k;
+    k << "stream_batch/" << (sizeof(T) == 8 ? "fp64" : "fp32") << "/w" << g.width << "/tile" << g.tile_bytes
+      << "/x" << g.x_bytes << "/log2B" << lg << "/" << name;
+    return k.str();
+}
+
+// Pick each group's (CTAs per SM, stages, chunk target): from the cache, else by timing
+// the candidates (when allowed), else the default (two CTAs per SM where three stages fit).
+template <typename T>
+int batch_configure(h2_batch &b, bool autotune, cudaStream_t st)
+{
+    for (size_t gi = 0; gi < b.groups.size(); ++gi) {
+        h2_batch::Group &g = b.groups[gi];
+        const std::string key = batch_tune_key<T>(b, g);
+        StreamCfg c;
+        if (tune_lookup(key, &c) && c.ns >= 2 && batch_group_smem<T>(g, c.ns) <= 200 * 1024 &&
+            batch_set_chunks(g, c.chunk_target) == H2_OK) {
+            g.cfg = c;
+            g.tuned = true;
+            continue;
+        }
+        g.cfg.per_sm = batch_stages<T>(g, 2) >= 3 ? 2 : 1;
+        g.cfg.ns = batch_stages<T>(g, g.cfg.per_sm);
+        int rc = batch_set_chunks(g, 512 * 1024);
+        if (rc != H2_OK) return rc;
+        if (!autotune || g.nchunks == 0) continue;
+        StreamCfg best = g.cfg;
+        double best_ms = 1e30;
+        for (int per_sm : {1, 2, 3})
+            for (uint64_t target : {uint64_t(128) << 10, uint64_t(512) << 10, uint64_t(2) << 20}) {
+                const int ns = batch_stages<T>(g, per_sm);
+                if (ns < 2) continue;
+                g.cfg.per_sm = per_sm;
+                g.cfg.ns = ns;
+                if (batch_set_chunks(g, target) != H2_OK) continue;
+                const double ms = batch_time_group<T>(b, gi, st);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = g.cfg;
+                }
+            }
+        g.cfg = best;
+        rc = batch_set_chunks(g, best.chunk_target);
+        if (rc != H2_OK) return rc;
+        g.tuned = true;
+        tune_store(key, best, best_ms);
+    }
+    return H2_OK;
+}
+
+template <typename T>
+int batch_build_group_tables(h2_batch &b)
+{
+    using namespace h2s;
+    for (h2_batch::Group &g : b.groups) {
+        std::vector<BatchOp<T>> tab;
+        for (int mi : g.members) {
+            h2_batch::Member &m = b.members[size_t(mi)];
+            const h2_device &dv = *m.op->dev;
+            BatchOp<T> o;
+            o.vals = dv.vals;
+            o.xh = static_cast<const T *>(m.w.xh);
+            o.xt = static_cast<const T *>(m.w.xt);
+            o.yh = static_cast<T *>(m.w.yh);
+            o.yd = static_cast<T *>(m.w.yd);
+            o.kx = dv.kx;
+            o.mp = dv.mp;
+            o.vs = m.nv;
+            o.nv = m.nv;
+            tab.push_back(o);
+        }
+        int rc = cuda_status(cudaMalloc(&g.d_ops, std::max<size_t>(1, tab.size()) * sizeof(BatchOp<T>)));
+        if (rc == H2_OK && !tab.empty())
+            rc = cuda_status(cudaMemcpy(g.d_ops, tab.data(), tab.size() * sizeof(BatchOp<T>), cudaMemcpyHostToDevice));
+        if (rc != H2_OK) return rc;
+    }
+    return H2_OK;
+}
+
+void batch_free(h2_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto &g : b->groups) {
+        if (g.d_desc) cudaFree(g.d_desc);
+        if (g.d_chunks) cudaFree(g.d_chunks);
+        if (g.d_ops) cudaFree(g.d_ops);
+    }
+    for (cudaStream_t s : b->branches) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->ev_branch) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_mid) cudaEventDestroy(b->ev_mid);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->ws_mem) cudaFree(b->ws_mem);
+    if (b->d_flags) cudaFree(b->d_flags);
+    delete b;
+}
+
 }  // namespace
 
 void h2_device_free(h2_op *op)
@@ -830,6 +1213,8 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     }
     dv->n_chunks_bottom = int64_t(pb.size());
     dv->n_chunks_top = int64_t(pt.size());
+    dv->n_desc_bottom = int64_t(db.size());
+    dv->n_desc_top = int64_t(dt.size());
     dv->grid_bottom = int(std::max<int64_t>(1, std::min<int64_t>(dv->num_sms, dv->n_chunks_bottom)));
     dv->grid_top = int(std::max<int64_t>(1, std::min<int64_t>(dv->num_sms, dv->n_chunks_top)));
 
@@ -1137,4 +1522,179 @@ const char *h2_status_str(int status)
     }
 }
 
-}  // extern "C"
+// ---------------------------------------------------------------- batched products
+
+int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void *const *Y, const int *nv, double alpha,
+                    double beta, int flags, h2_batch_t *out)
+{
+    if (!out) return H2_EINVAL;
+    *out = nullptr;
+    if (!ops || count < 1 || !X || !Y || !nv) return H2_EINVAL;
+    size_t esize = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!ops[i] || !X[i] || !Y[i] || nv[i] < 1) return H2_EINVAL;
+        const h2_device *dv = ops[i]->dev;
+        if (!dv) return H2_ESTATE;
+        if (dv->tc) return H2_EINVAL;  // FP64 or FP32 members only
+        if (esize && dv->esize != esize) return H2_EINVAL;
+        esize = dv->esize;
+        if (!(nv[i] <= kChunk || (wide_ok(*dv) && nv[i] <= kWidePass))) return H2_EINVAL;  // one pass each
+    }
+    h2_batch *b = new (std::nothrow) h2_batch;
+    if (!b) return H2_ENOMEM;
+    b->esize = esize;
+    b->alpha = alpha;
+    b->beta = beta;
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    int rc = H2_OK;
+    // workspaces, one allocation
+    std::vector<size_t> wsz(static_cast<size_t>(count));
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        wsz[size_t(i)] = align_up(ws_layout(*ops[i], *ops[i]->dev, nv[i], nullptr, nullptr));
+        total += wsz[size_t(i)];
+    }
+    rc = cuda_status(cudaMalloc(&b->ws_mem, total));
+    size_t off = 0;
+    for (int i = 0; rc == H2_OK && i < count; ++i) {
+        h2_batch::Member m;
+        m.op = ops[i];
+        m.X = X[i];
+        m.Y = Y[i];
+        m.nv = nv[i];
+        ws_layout(*ops[i], *ops[i]->dev, nv[i], &m.w, static_cast<char *>(b->ws_mem) + off);
+        off += wsz[size_t(i)];
+        b->members.push_back(m);
+    }
+    // groups by accumulator width: merged descriptors tagged with the member's table index
+    for (int i = 0; rc == H2_OK && i < count; ++i) {
+        const int wc = width_class(nv[i]);
+        size_t gi = 0;
+        while (gi < b->groups.size() && b->groups[gi].width != wc) ++gi;
+        if (gi == b->groups.size()) {
+            b->groups.emplace_back();
+            b->groups.back().width = wc;
+        }
+        h2_batch::Group &g = b->groups[gi];
+        const int slot = int(g.members.size());
+        g.members.push_back(i);
+        const h2_op &op = *ops[i];
+        const h2_device &dv = *op.dev;
+        std::vector<h2s::StreamDesc> d(size_t(dv.n_desc_bottom + dv.n_desc_top));
+        if (dv.n_desc_bottom)
+            rc = cuda_status(cudaMemcpy(d.data(), dv.desc_bottom, size_t(dv.n_desc_bottom) * sizeof(h2s::StreamDesc),
+                                        cudaMemcpyDeviceToHost));
+        if (rc == H2_OK && dv.n_desc_top)
+            rc = cuda_status(cudaMemcpy(d.data() + dv.n_desc_bottom, dv.desc_top,
+                                        size_t(dv.n_desc_top) * sizeof(h2s::StreamDesc), cudaMemcpyDeviceToHost));
+        for (h2s::StreamDesc &e : d) {
+            e.pad1 = slot;
+            const uint64_t tb = (e.flags & h2s::kZero) ? uint64_t(op.k) * esize : uint64_t(e.rows) * e.cols * esize;
+            g.desc.push_back(e);
+            g.bytes.push_back(tb);
+            g.tile_bytes = std::max<uint32_t>(g.tile_bytes, uint32_t((tb + 15) / 16 * 16));
+        }
+        g.x_bytes = std::max<uint32_t>(g.x_bytes, uint32_t(std::max(dv.mp, dv.kx) * wc * esize));
+    }
+    for (h2_batch::Group &g : b->groups) {
+        if (rc != H2_OK) break;
+        g.chunk_cap = std::max<size_t>(1, g.desc.size());
+        rc = cuda_status(cudaMalloc(&g.d_desc, std::max<size_t>(1, g.desc.size()) * sizeof(h2s::StreamDesc)));
+        if (rc == H2_OK && !g.desc.empty())
+            rc = cuda_status(cudaMemcpy(g.d_desc, g.desc.data(), g.desc.size() * sizeof(h2s::StreamDesc),
+                                        cudaMemcpyHostToDevice));
+        if (rc == H2_OK) rc = cuda_status(cudaMalloc(&g.d_chunks, g.chunk_cap * 8));
+    }
+    if (rc == H2_OK) rc = esize == 8 ? batch_build_group_tables<double>(*b) : batch_build_group_tables<float>(*b);
+    if (rc == H2_OK) rc = cuda_status(cudaMalloc(&b->d_flags, 17 * sizeof(int)));
+    if (rc == H2_OK) rc = cuda_status(cudaMemset(b->d_flags, 0, 17 * sizeof(int)));
+    if (rc == H2_OK) rc = cuda_status(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    const int nb = std::min(count, 16);
+    for (int j = 0; rc == H2_OK && j < nb; ++j) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        rc = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        if (rc == H2_OK) b->branches.push_back(s);
+        if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        if (rc == H2_OK) b->ev_branch.push_back(e);
+    }
+    if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&b->ev_mid, cudaEventDisableTiming));
+    // default configuration, one eager upsweep and merged stream (kernel attributes, valid
+    // trees for tuning; X is read, Y is not written), then the tuned configuration and the
+    // captured graph
+    auto configure = [&](bool tune) {
+        return esize == 8 ? batch_configure<double>(*b, tune, b->cap) : batch_configure<float>(*b, tune, b->cap);
+    };
+    auto enqueue = [&](cudaStream_t st, bool with_down) {
+        return esize == 8 ? batch_enqueue<double>(*b, st, with_down) : batch_enqueue<float>(*b, st, with_down);
+    };
+    if (rc == H2_OK) rc = configure(false);
+    if (rc == H2_OK) rc = enqueue(b->cap, false);  // leaves every Y untouched
+    if (rc == H2_OK) rc = cuda_status(cudaStreamSynchronize(b->cap));
+    if (rc == H2_OK && (flags & H2_BATCH_AUTOTUNE)) {
+        for (auto &g : b->groups) g.tuned = false;
+        rc = configure(true);
+        if (rc == H2_OK) rc = cuda_status(cudaStreamSynchronize(b->cap));
+    }
+    if (rc == H2_OK) rc = cuda_status(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    if (rc == H2_OK) {
+        int rc2 = enqueue(b->cap, true);
+        const int rc3 = cuda_status(cudaStreamEndCapture(b->cap, &b->graph));
+        rc = rc2 != H2_OK ? rc2 : rc3;
+    }
+    if (rc == H2_OK) rc = cuda_status(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    if (rc != H2_OK) {
+        cudaGetLastError();
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return H2_OK;
+}
+
+int h2_batch_run(h2_batch_t b, void *cuda_stream)
+{
+    if (!b || !b->exec) return H2_EINVAL;
+    return cuda_status(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)));
+}
+
+int h2_batch_check(h2_batch_t b)
+{
+    if (!b) return H2_EINVAL;
+    int flag = 0;
+    if (cudaMemcpy(&flag, b->d_flags + 16, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ECUDA;
+    for (const auto &m : b->members) {
+        int f = 0;
+        if (cudaMemcpy(&f, m.op->dev->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ECUDA;
+        flag |= f;
+    }
+    return flag ? H2_ETIMEOUT : H2_OK;
+}
+
+int h2_batch_describe(h2_batch_t b, char *buf, size_t len)
+{
+    if (!b || !buf || len == 0) return H2_EINVAL;
+    std::ostringstream o;
+    o << "members " << b->members.size() << " branches " << b->branches.size();
+    for (const auto &g : b->groups)
+        o << "; width " << g.width << ": members " << g.members.size() << " blocks " << g.desc.size() << " chunks "
+          << g.nchunks << " ctas/sm " << g.cfg.per_sm << " stages " << g.cfg.ns << " chunk " << g.cfg.chunk_target
+          << (g.tuned ? " (tuned)" : " (default)");
+    const std::string str = o.str();
+    const size_t n = std::min(len - 1, str.size());
+    std::memcpy(buf, str.data(), n);
+    buf[n] = 0;
+    return H2_OK;
+}
+
+int h2_batch_destroy(h2_batch_t b)
+{
+    if (!b) return H2_EINVAL;
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    batch_free(b);
+    return H2_OK;
+}
+
+}  // extern "C\"

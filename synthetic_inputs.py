@@ -115,3 +115,46 @@ def cloud3d(n: int, nv: int = 32) -> Workload:
 
 
 WORKLOADS = {w.name: w for w in (GRID64_EXP, GRID1024_GAUSS, CLOUD3D_EXP)}
+
+
+@dataclasses.dataclass(frozen=True)
+class BatchMember:
+    """One operator of the batched workload: its points, kernel, construction parameters
+    and the number of vectors of its product."""
+    name: str
+    points: np.ndarray
+    kernel: tuple
+    leaf_size: int
+    cheb_order: int
+    eta: float
+    nv: int
+    x_seed: int
+
+    def make_x(self) -> np.ndarray:
+        return gaussian_vectors(len(self.points), self.nv, self.x_seed)
+
+
+def uneven_batch(count: int = 64, n_min: int = 2 ** 12, n_max: int = 2 ** 18, seed: int = 4,
+                 nv_max: int = 16) -> list:
+    """Operators of uneven size for a batched product, drawn from default_rng(seed) in order:
+    N log-uniform in [n_min, n_max]; even members are 2D grids with side round(sqrt(N))
+    (N := side^2) and a Chebyshev order in {4, ..., 8} per dimension, odd members uniform 3D
+    clouds with an order in {3, 4}; kernel exp(-r/l) with l uniform in [0.05, 0.3]; leaf 64,
+    eta 0.7; nv uniform in {1, ..., nv_max}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))))
+        ell = float(rng.uniform(0.05, 0.3))
+        nv = int(rng.integers(1, nv_max + 1))
+        if i % 2 == 0:
+            side = max(2, int(round(np.sqrt(n))))
+            p = int(rng.integers(4, 9))
+            pts = grid_2d(side)
+            name = f"grid{side}"
+        else:
+            p = int(rng.integers(3, 5))
+            pts = uniform_cloud(n, 3, int(rng.integers(0, 2 ** 31)))
+            name = f"cloud3d_{n}"
+        out.append(BatchMember(f"{i:02d}_{name}", pts, ("exp", ell, 0.0, 0), 64, p, 0.7, nv, 10_000 + i))
+    return out
