@@ -289,6 +289,62 @@ def serve_benchmark(h2, torch, requests_per_rate=32, maxit=100, rates=(0.5, 0.8,
             op.close()
 
 
+def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18):
+    """Batched products of 64 uneven operators (synthetic_inputs.uneven_batch: N log-uniform
+    in [2^12, 2^18], even members 2D grids with orders 4-8, odd members 3D clouds with orders
+    3-4, exp(-r/l) with l in [0.05, 0.3], leaf 64, eta 0.7, nv in 1..16), FP32, as one
+    graph-replayed batch (h2_batch_run, autotuned) against the same products issued one after
+    another (h2_matvec). The batch streams more than L2 holds, so no flush is needed."""
+    members = si.uneven_batch(count=count, n_max=n_max)
+    ops, Xs, Ys = [], [], []
+    total_bytes = 0
+    total_flops = 0
+    for m in members:
+        op = h2.H2Operator(m.points, m.kernel, m.leaf_size, m.cheb_order, m.eta).upload("fp32")
+        mat, vec = entry_counts(op.info, m.nv)
+        total_bytes += 4 * (mat + vec)
+        total_flops += 2 * mat * m.nv
+        ops.append(op)
+        Xs.append(torch.from_numpy(np.ascontiguousarray(m.make_x().T)).float().cuda().t())
+        Ys.append(op.new_vectors(m.nv, fill=0.0))
+    stream = torch.cuda.current_stream()
+    try:
+        t0 = time.perf_counter()
+        batch = h2.H2Batch(ops, Xs, Ys, autotune=True)
+        create_s = time.perf_counter() - t0
+        desc = batch.describe()
+
+        def timed(fn):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in evs:
+                a.record(stream)
+                fn()
+                b.record(stream)
+            torch.cuda.synchronize()
+            return [a.elapsed_time(b) for a, b in evs]
+
+        ms_batch = timed(batch.run)
+        batch.check()
+        ms_seq = timed(lambda: [op.matvec(X, Y) for op, X, Y in zip(ops, Xs, Ys)])
+        batch.close()
+        mb, msq = float(np.median(ms_batch)), float(np.median(ms_seq))
+        return {"workload": f"uneven_batch: {count} operators, N log-uniform [2^12, {n_max}], 2D grids / 3D "
+                            "clouds, exp(-r/l), rank 16-64, nv 1-16, FP32",
+                "points": int(sum(len(m.points) for m in members)), "vectors": int(sum(m.nv for m in members)),
+                "bytes_per_step": total_bytes, "flops_per_step": total_flops,
+                "batched_ms": mb, "batched_GB/s": total_bytes / (mb * 1e-3) / 1e9,
+                "batched_gflops": total_flops / (mb * 1e-3) / 1e9,
+                "sequential_ms": msq, "sequential_GB/s": total_bytes / (msq * 1e-3) / 1e9,
+                "speedup_vs_sequential": msq / mb, "create_s": create_s, "configuration": desc,
+                "l2": "inputs larger than L2, no flush"}
+    finally:
+        for op in ops:
+            op.close()
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -320,6 +376,10 @@ def main():
                          "smaller sizes are for profiler captures)")
     ap.add_argument("--multi-rhs-steps", type=int, default=0, help="timed 32-vector products (0: steps / 20, >= 5)")
     ap.add_argument("--no-serve", action="store_true", help="skip the CG serving-loop measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-operator measurement")
+    ap.add_argument("--batch-count", type=int, default=64, help="operators of the batched measurement")
+    ap.add_argument("--batch-nmax", type=int, default=2 ** 18,
+                    help="largest N of the batched measurement (smaller values are for profiler captures)")
     ap.add_argument("--serve-maxit", type=int, default=100, help="CG iteration cap of each served solve")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate")
     ap.add_argument("--grid", type=int, default=1024,
@@ -474,6 +534,11 @@ def main():
             line["multi_rhs"] = multi_rhs(h2, torch, mr_steps, 3, peak_hbm, peak_kind, args.cloud_n)
         except Exception as exc:  # reported, never silently dropped
             line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if not args.no_batch:
+        try:
+            line["batch"] = batch_benchmark(h2, torch, count=args.batch_count, n_max=args.batch_nmax)
+        except Exception as exc:  # reported, never silently dropped
+            line["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_serve:
         try:
             line["serve"] = serve_benchmark(h2, torch, args.serve_requests, args.serve_maxit)

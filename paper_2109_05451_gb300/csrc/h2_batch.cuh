@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {
                         const BatchOp<T> &o = ops[batch_op(d)];
                         const bool dense = d.flags & kDense;
-                        const uint32_t tb = (uint32_t(d.rows) * d.cols * es + 15u) & ~15u;
+                        const uint32_t tb = (uint32_t(d.ld) * d.cols * es + 15u) & ~15u;
                         const T *x = dense ? o.xt + int64_t(d.x_node) * o.mp * o.vs : o.xh + int64_t(d.x_node) * o.kx * o.vs;
                         const uint32_t xb = uint32_t(dense ? o.mp : o.kx) * o.nv * es;
                         ok = produce(s, pp, ring, o.vals + d.src, tb, x, xb, nullptr, 0, &d, err);
@@ -101,12 +101,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool dense = d.flags & kDense;
         const int xld = dense ? o.mp : o.kx;
         if (fresh) {
-            acc.setup(d.rows, d.rows, tid);
+            acc.setup(d.rows, d.ld, tid);
             acc.zero();
             fresh = false;
         }
         if (!(d.flags & kZero))
-            acc.gemv(stage_tile(s, pp, ring.stage), d.rows, d.rows, d.cols, stage_x(s, pp, ring.stage), xld, o.nv);
+            acc.gemv(stage_tile(s, pp, ring.stage), d.ld, d.rows, d.cols, stage_x(s, pp, ring.stage), xld, o.nv);
         release(&s.empty[ring.stage], lane);
         ring.next();
         if (d.flags & kLast) {

@@ -278,8 +278,8 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     const Pipe p_tsub = make_pipe<T, NVMAX>(tile_sub, x_sub, 2 << Ltop, kx, false, 64 * 1024, 4);
     const size_t sm_bsub = smem_bytes<T, NVMAX>(p_bsub, 2 << Lbot, kx, false);
     const size_t sm_tsub = smem_bytes<T, NVMAX>(p_tsub, 2 << Ltop, kx, false);
-    const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * k, size_t(dv.max_leaf_rows) * dv.max_leaf_rows) *
-                                         es) + 15) / 16 * 16);
+    const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * kx, size_t(mp) * dv.max_leaf_rows) * es) + 15) /
+                                       16 * 16);
     const uint32_t x_str = uint32_t(std::max(mp, kx) * NVMAX * es);
     const Pipe p_bot = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
     const Pipe p_top = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
@@ -454,8 +454,8 @@ int launch_wide(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double
     v.xr = v.yr = static_cast<T *>(w.rows);
     v.ldr = round4(nv);
     const SweepPlan<T, NVMAX> sp = make_sweep_plan<T, NVMAX>(op, dv);
-    const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * k, size_t(dv.max_leaf_rows) * dv.max_leaf_rows) *
-                                         es) + 15) / 16 * 16);
+    const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * kx, size_t(mp) * dv.max_leaf_rows) * es) + 15) /
+                                       16 * 16);
     const uint32_t x_str = uint32_t(std::max(mp, kx) * NVMAX * es);
     // two CTAs per SM where three stages fit in half of the shared memory: eight consumer
     // warps hide the latency of the register-blocked products; else one CTA per SM
@@ -602,7 +602,7 @@ int generate_blocks(const h2_op &op, h2_device &dv, const int32_t *d_cpl_row, co
     const int64_t ncpl = int64_t(op.cpl_col.size()), ndns = int64_t(op.dns_col.size());
     if (ncpl > 0)
         h2k::gen_coupling<T><<<unsigned(std::min<int64_t>(ncpl, 1 << 20)), 256, 0, st>>>(
-            reinterpret_cast<T *>(dv.vals), d_cpl_row, d_cpl_col, ncpl, d_cheb, op.dim, op.p, op.k, dv.kkp, f);
+            reinterpret_cast<T *>(dv.vals), d_cpl_row, d_cpl_col, ncpl, d_cheb, op.dim, op.p, op.k, dv.kx, f);
     if (ndns > 0)
         h2k::gen_dense<T><<<unsigned(std::min<int64_t>(ndns, 1 << 20)), 256, 0, st>>>(
             reinterpret_cast<T *>(dv.vals + d_region), d_dns_off, d_dns_row, d_dns_col, ndns, dv.leaf_lo,
@@ -657,6 +657,8 @@ bool make_chunks(const std::vector<h2s::StreamDesc> &d, const std::vector<uint64
 }
 
 // ---------------------------------------------------------------- batched products
+
+constexpr int kBatchGroups = 64;  // most merged streams of one batch (width x tile-size classes)
 
 // Width class of a pass of nv vectors (the accumulator the kernels instantiate).
 int width_class(int nv) { return nv == 1 ? 1 : nv <= kChunk ? kChunk : nv <= 8 ? 8 : nv <= 16 ? 16 : 32; }
@@ -728,6 +730,7 @@ struct h2_batch {
     };
     struct Group {
         int width = 0;
+        uint64_t tile_class = 0;             // power of two >= every tile of the group
         std::vector<int> members;            // indices into members
         std::vector<h2s::StreamDesc> desc;   // merged, host
         std::vector<uint64_t> bytes;         // streamed bytes per descriptor
@@ -746,7 +749,7 @@ struct h2_batch {
     std::vector<Member> members;
     std::vector<Group> groups;
     void *ws_mem = nullptr;
-    int *d_flags = nullptr;                  // [0..15] tickets per group, [16] error flag
+    int *d_flags = nullptr;                  // [0, kBatchGroups) tickets per group, [kBatchGroups] error flag
     std::vector<cudaStream_t> branches;
     std::vector<cudaEvent_t> ev_branch;
     cudaEvent_t ev_fork = nullptr, ev_mid = nullptr;
@@ -805,7 +808,7 @@ int batch_group_stream(h2_batch &b, h2_batch::Group &g, int gi, cudaStream_t st)
     const size_t smem = smem_bytes<T, NV>(p, 0, 0, true);
     const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(b.num_sms) * g.cfg.per_sm, g.nchunks)));
     k_stream_batch<T, NV><<<grid, kThreads, smem, st>>>(static_cast<const BatchOp<T> *>(g.d_ops), p, g.d_desc,
-                                                        g.d_chunks, g.nchunks, b.d_flags + gi, b.d_flags + 16);
+                                                        g.d_chunks, g.nchunks, b.d_flags + gi, b.d_flags + kBatchGroups);
     return cuda_status(cudaGetLastError());
 }
 
@@ -834,12 +837,13 @@ size_t batch_group_smem(const h2_batch::Group &g, int ns)
     }
 }
 
-// Stages for per_sm CTAs per SM (budget 200 KB / 110 KB / 72 KB), at most 12; 0 if < 2 fit.
+// Stages for per_sm CTAs per SM (budget 200 KB / 110 KB / 72 KB), at most 24 (small tiles
+// get deep rings); 0 if fewer than 2 fit.
 template <typename T>
 int batch_stages(const h2_batch::Group &g, int per_sm)
 {
     const size_t budget = per_sm == 1 ? 200 * 1024 : per_sm == 2 ? 110 * 1024 : 72 * 1024;
-    for (int ns = 12; ns >= 2; --ns)
+    for (int ns = 24; ns >= 2; --ns)
         if (batch_group_smem<T>(g, ns) <= budget) return ns;
     return 0;
 }
@@ -876,9 +880,20 @@ int batch_enqueue(h2_batch &b, cudaStream_t st, bool with_down = true)
         cudaEventRecord(b.ev_branch[j], b.branches[j]);
         cudaStreamWaitEvent(st, b.ev_branch[j], 0);
     }
-    if (rc == H2_OK) rc = cuda_status(cudaMemsetAsync(b.d_flags, 0, 16 * sizeof(int), st));
-    for (size_t gi = 0; rc == H2_OK && gi < b.groups.size(); ++gi)
-        rc = batch_group_stream_any<T>(b, b.groups[gi], int(gi), st);
+    if (rc == H2_OK) rc = cuda_status(cudaMemsetAsync(b.d_flags, 0, kBatchGroups * sizeof(int), st));
+    // the merged streams write disjoint rows: they run concurrently on the branches, so one
+    // group's tail overlaps the others' work
+    if (rc == H2_OK) rc = cuda_status(cudaEventRecord(b.ev_mid, st));
+    const size_t ng = std::min(nb, b.groups.size());
+    for (size_t gi = 0; rc == H2_OK && gi < b.groups.size(); ++gi) {
+        cudaStream_t br = b.branches[gi % nb];
+        if (gi < ng) cudaStreamWaitEvent(br, b.ev_mid, 0);
+        rc = batch_group_stream_any<T>(b, b.groups[gi], int(gi), br);
+    }
+    for (size_t j = 0; rc == H2_OK && j < ng; ++j) {
+        cudaEventRecord(b.ev_branch[j], b.branches[j]);
+        cudaStreamWaitEvent(st, b.ev_branch[j], 0);
+    }
     if (rc == H2_OK) rc = cuda_status(cudaEventRecord(b.ev_mid, st));
     for (size_t i = 0; rc == H2_OK && with_down && i < b.members.size(); ++i) {
         cudaStream_t br = b.branches[i % nb];
@@ -1136,7 +1151,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     }
     dv->kx = round4(k);
     dv->mp = round4(dv->max_leaf_rows);
-    dv->kkp = (int64_t(k) * k + 3) / 4 * 4;
+    dv->kkp = int64_t(k) * round4(k);  // entries per stored coupling tile (ld kx)
     dv->L = std::min(op.q, 4);
     dv->Lb = op.q - dv->L;
     dv->root_row = op.cpl_rowptr[2] > op.cpl_rowptr[1];
@@ -1152,7 +1167,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
         for (int64_t b = op.dns_rowptr[t]; b < op.dns_rowptr[t + 1]; ++b) {
             dns_row[b] = int32_t(t);
             const int64_t s = op.dns_col[b];
-            const int64_t cnt = int64_t(leaf_lo[t + 1] - leaf_lo[t]) * (leaf_lo[s + 1] - leaf_lo[s]);
+            const int64_t cnt = int64_t(round4(leaf_lo[t + 1] - leaf_lo[t])) * (leaf_lo[s + 1] - leaf_lo[s]);
             dns_off[b + 1] = dns_off[b] + (cnt + 31) / 32 * 32;  // 128-byte aligned blocks
         }
     const size_t tcb = h2s::kTcTileBytes;  // split-BF16 tile of one block
@@ -1175,6 +1190,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
             h2s::StreamDesc d{};
             d.out_node = int32_t(t);
             d.rows = int16_t(k);
+            d.ld = int16_t(round4(k));
             d.flags = h2s::kZero | h2s::kLast;
             (is_top ? dt : db).push_back(d);
             (is_top ? bt : bb).push_back(uint64_t(k) * es);
@@ -1186,9 +1202,10 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
             d.out_node = int32_t(t);
             d.rows = int16_t(k);
             d.cols = int16_t(k);
+            d.ld = int16_t(round4(k));
             d.flags = b + 1 == b1 ? h2s::kLast : 0;
             (is_top ? dt : db).push_back(d);
-            (is_top ? bt : bb).push_back(dv->tc ? tcb : uint64_t(k) * k * es);
+            (is_top ? bt : bb).push_back(dv->tc ? tcb : uint64_t(d.ld) * k * es);
         }
     }
     for (int64_t t = 0; t < nleaves; ++t) {
@@ -1201,9 +1218,10 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
             d.out_node = int32_t(t);
             d.rows = int16_t(leaf_lo[t + 1] - leaf_lo[t]);
             d.cols = int16_t(leaf_lo[s + 1] - leaf_lo[s]);
+            d.ld = int16_t(round4(d.rows));
             d.flags = h2s::kDense | (b + 1 == b1 ? h2s::kLast : 0);
             db.push_back(d);
-            bb.push_back(dv->tc ? tcb : uint64_t(d.rows) * d.cols * es);
+            bb.push_back(dv->tc ? tcb : uint64_t(d.ld) * d.cols * es);
         }
     }
     std::vector<int64_t> pb, pt;
@@ -1567,18 +1585,16 @@ int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void 
         off += wsz[size_t(i)];
         b->members.push_back(m);
     }
-    // groups by accumulator width: merged descriptors tagged with the member's table index
+    // groups by accumulator width and tile-size class (the next power of two of a row's
+    // largest tile, so that small tiles get deep pipelines of small stages); descriptors are
+    // tagged with the member's index in their group's table, and rows stay whole
+    auto tile_class = [](uint64_t bytes) {
+        uint64_t c = 1024;
+        while (c < bytes) c <<= 1;
+        return c;
+    };
     for (int i = 0; rc == H2_OK && i < count; ++i) {
         const int wc = width_class(nv[i]);
-        size_t gi = 0;
-        while (gi < b->groups.size() && b->groups[gi].width != wc) ++gi;
-        if (gi == b->groups.size()) {
-            b->groups.emplace_back();
-            b->groups.back().width = wc;
-        }
-        h2_batch::Group &g = b->groups[gi];
-        const int slot = int(g.members.size());
-        g.members.push_back(i);
         const h2_op &op = *ops[i];
         const h2_device &dv = *op.dev;
         std::vector<h2s::StreamDesc> d(size_t(dv.n_desc_bottom + dv.n_desc_top));
@@ -1588,14 +1604,44 @@ int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void 
         if (rc == H2_OK && dv.n_desc_top)
             rc = cuda_status(cudaMemcpy(d.data() + dv.n_desc_bottom, dv.desc_top,
                                         size_t(dv.n_desc_top) * sizeof(h2s::StreamDesc), cudaMemcpyDeviceToHost));
-        for (h2s::StreamDesc &e : d) {
-            e.pad1 = slot;
-            const uint64_t tb = (e.flags & h2s::kZero) ? uint64_t(op.k) * esize : uint64_t(e.rows) * e.cols * esize;
-            g.desc.push_back(e);
-            g.bytes.push_back(tb);
-            g.tile_bytes = std::max<uint32_t>(g.tile_bytes, uint32_t((tb + 15) / 16 * 16));
+        std::vector<std::pair<size_t, int>> slot_of;  // group index -> this member's slot there
+        size_t r0 = 0;
+        for (size_t e = 0; rc == H2_OK && e < d.size(); ++e) {
+            if (!(d[e].flags & h2s::kLast)) continue;
+            // the row d[r0 .. e]
+            uint64_t row_max = 0;
+            std::vector<uint64_t> tb(e + 1 - r0);
+            for (size_t j = r0; j <= e; ++j) {
+                tb[j - r0] = (d[j].flags & h2s::kZero) ? uint64_t(op.k) * esize : uint64_t(d[j].ld) * d[j].cols * esize;
+                row_max = std::max(row_max, tb[j - r0]);
+            }
+            const uint64_t cls = tile_class(row_max);
+            size_t gi = 0;
+            while (gi < b->groups.size() && !(b->groups[gi].width == wc && b->groups[gi].tile_class == cls)) ++gi;
+            if (gi == b->groups.size()) {
+                b->groups.emplace_back();
+                b->groups.back().width = wc;
+                b->groups.back().tile_class = cls;
+            }
+            h2_batch::Group &g = b->groups[gi];
+            int slot = -1;
+            for (auto &sv : slot_of)
+                if (sv.first == gi) slot = sv.second;
+            if (slot < 0) {
+                slot = int(g.members.size());
+                g.members.push_back(i);
+                slot_of.push_back({gi, slot});
+                g.x_bytes = std::max<uint32_t>(g.x_bytes, uint32_t(std::max(dv.mp, dv.kx) * wc * esize));
+            }
+            for (size_t j = r0; j <= e; ++j) {
+                h2s::StreamDesc x = d[j];
+                x.pad1 = slot;
+                g.desc.push_back(x);
+                g.bytes.push_back(tb[j - r0]);
+                g.tile_bytes = std::max<uint32_t>(g.tile_bytes, uint32_t((tb[j - r0] + 15) / 16 * 16));
+            }
+            r0 = e + 1;
         }
-        g.x_bytes = std::max<uint32_t>(g.x_bytes, uint32_t(std::max(dv.mp, dv.kx) * wc * esize));
     }
     for (h2_batch::Group &g : b->groups) {
         if (rc != H2_OK) break;
@@ -1607,8 +1653,9 @@ int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void 
         if (rc == H2_OK) rc = cuda_status(cudaMalloc(&g.d_chunks, g.chunk_cap * 8));
     }
     if (rc == H2_OK) rc = esize == 8 ? batch_build_group_tables<double>(*b) : batch_build_group_tables<float>(*b);
-    if (rc == H2_OK) rc = cuda_status(cudaMalloc(&b->d_flags, 17 * sizeof(int)));
-    if (rc == H2_OK) rc = cuda_status(cudaMemset(b->d_flags, 0, 17 * sizeof(int)));
+    if (rc == H2_OK && b->groups.size() > size_t(kBatchGroups)) rc = H2_EINVAL;
+    if (rc == H2_OK) rc = cuda_status(cudaMalloc(&b->d_flags, (kBatchGroups + 1) * sizeof(int)));
+    if (rc == H2_OK) rc = cuda_status(cudaMemset(b->d_flags, 0, (kBatchGroups + 1) * sizeof(int)));
     if (rc == H2_OK) rc = cuda_status(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     const int nb = std::min(count, 16);
     for (int j = 0; rc == H2_OK && j < nb; ++j) {
@@ -1664,7 +1711,7 @@ int h2_batch_check(h2_batch_t b)
 {
     if (!b) return H2_EINVAL;
     int flag = 0;
-    if (cudaMemcpy(&flag, b->d_flags + 16, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ECUDA;
+    if (cudaMemcpy(&flag, b->d_flags + kBatchGroups, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ECUDA;
     for (const auto &m : b->members) {
         int f = 0;
         if (cudaMemcpy(&f, m.op->dev->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ECUDA;
@@ -1681,7 +1728,7 @@ int h2_batch_describe(h2_batch_t b, char *buf, size_t len)
     for (const auto &g : b->groups)
         o << "; width " << g.width << ": members " << g.members.size() << " blocks " << g.desc.size() << " chunks "
           << g.nchunks << " ctas/sm " << g.cfg.per_sm << " stages " << g.cfg.ns << " chunk " << g.cfg.chunk_target
-          << (g.tuned ? " (tuned)" : " (default)");
+          << (g.tuned ? " (tuned)" : " (default)") << " tiles<=" << g.tile_class;
     const std::string str = o.str();
     const size_t n = std::min(len - 1, str.size());
     std::memcpy(buf, str.data(), n);

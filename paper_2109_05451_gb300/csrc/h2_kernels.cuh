@@ -51,28 +51,34 @@ __device__ __forceinline__ double kernel_eval(const KernelFn &f, const double *x
 // (grid-stride over blocks).
 template <typename T>
 __global__ void gen_coupling(T *__restrict__ S, const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-                             int64_t nblocks, const double *__restrict__ cheb, int dim, int p, int k, int64_t kkp,
+                             int64_t nblocks, const double *__restrict__ cheb, int dim, int p, int k, int kx,
                              KernelFn f)
 {
-    const int64_t kk = int64_t(k) * k;
+    // S_ts stored transposed, [mu][nu] with ld kx (nu fastest, zero for k <= nu < kx)
+    const int64_t bs = int64_t(k) * kx;
     for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
         const int64_t t = row[b], s = col[b];
-        for (int64_t e = threadIdx.x; e < kk; e += blockDim.x) {
-            const int nu = int(e % k), mu = int(e / k);
-            double xt[3], xs[3];
-            int rn = nu, rm = mu;
-            for (int d = 0; d < dim; ++d) {
-                xt[d] = cheb[(t * dim + d) * p + rn % p];
-                xs[d] = cheb[(s * dim + d) * p + rm % p];
-                rn /= p;
-                rm /= p;
+        for (int64_t e = threadIdx.x; e < bs; e += blockDim.x) {
+            const int nu = int(e % kx), mu = int(e / kx);
+            double v = 0.0;
+            if (nu < k) {
+                double xt[3], xs[3];
+                int rn = nu, rm = mu;
+                for (int d = 0; d < dim; ++d) {
+                    xt[d] = cheb[(t * dim + d) * p + rn % p];
+                    xs[d] = cheb[(s * dim + d) * p + rm % p];
+                    rn /= p;
+                    rm /= p;
+                }
+                v = kernel_eval(f, xt, xs, dim);
             }
-            S[b * kkp + e] = T(kernel_eval(f, xt, xs, dim));
+            S[b * bs + e] = T(v);
         }
     }
 }
 
-// Dense blocks D_ts[i][j] = kappa(x_i, x_j), stored transposed (i fastest).
+// Dense blocks D_ts[i][j] = kappa(x_i, x_j), stored transposed: [j][i] with ld = rows rounded
+// up to 4 (i fastest, zero for rows <= i < ld).
 template <typename T>
 __global__ void gen_dense(T *__restrict__ D, const int64_t *__restrict__ off, const int32_t *__restrict__ row,
                           const int32_t *__restrict__ col, int64_t nblocks, const int32_t *__restrict__ leaf_lo,
@@ -82,10 +88,12 @@ __global__ void gen_dense(T *__restrict__ D, const int64_t *__restrict__ off, co
         const int t = row[b], s = col[b];
         const int r0 = leaf_lo[t], rt = leaf_lo[t + 1] - r0;
         const int c0 = leaf_lo[s], cs = leaf_lo[s + 1] - c0;
-        const int64_t cnt = int64_t(rt) * cs;
+        const int ld = (rt + 3) / 4 * 4;
+        const int64_t cnt = int64_t(ld) * cs;
         for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-            const int i = int(e % rt), j = int(e / rt);
-            D[off[b] + e] = T(kernel_eval(f, pts_tree + int64_t(r0 + i) * dim, pts_tree + int64_t(c0 + j) * dim, dim));
+            const int i = int(e % ld), j = int(e / ld);
+            D[off[b] + e] = i < rt ? T(kernel_eval(f, pts_tree + int64_t(r0 + i) * dim, pts_tree + int64_t(c0 + j) * dim, dim))
+                                   : T(0);
         }
     }
 }

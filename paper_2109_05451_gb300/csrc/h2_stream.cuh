@@ -47,7 +47,7 @@ struct alignas(16) StreamDesc {
     int32_t out_node; // heap index (coupling) or leaf index (dense) of the output segment
     int16_t rows, cols;
     int16_t flags;    // kDense | kLast | kZero | kEnd
-    int16_t pad0;
+    int16_t ld;       // leading dimension of the stored tile: rows rounded up to 4, zero-padded
     int32_t pad1;
 };
 constexpr int16_t kDense = 1;  // dense block (else coupling block)
@@ -480,7 +480,9 @@ struct AccW {
             for (int j = 0; j < 64; j += 4) step4(tb + j * 64, 64, xb + j, 64);
             return;
         }
-        if ((ld & 3) == 0 && (xld & 3) == 0 && o0 + 4 <= R) {
+        // every tile is zero-padded up to its leading dimension, so a group of four outputs
+        // that straddles R reads zeros beyond it (and the stores mask them)
+        if ((ld & 3) == 0 && (xld & 3) == 0 && o0 + 4 <= ld) {
             int j = 0;
 #pragma unroll 2
             for (; j + 4 <= C; j += 4) step4(tb + j * ld, ld, xb + j, xld);
@@ -869,7 +871,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = produce(s, pp, ring, nullptr, 0, nullptr, 0, nullptr, 0, &d, vec.err);
                     } else {
                         const bool dense = d.flags & kDense;
-                        const uint32_t tb = (uint32_t(d.rows) * d.cols * es + 15u) & ~15u;
+                        const uint32_t tb = (uint32_t(d.ld) * d.cols * es + 15u) & ~15u;
                         const T *x = dense ? vec.xt + int64_t(d.x_node) * mp * vs : vec.xh + int64_t(d.x_node) * kx * vs;
                         const uint32_t xb = (dense ? mp : kx) * nv * es;
                         ok = produce(s, pp, ring, op.vals + d.src, tb, x, xb, nullptr, 0, &d, vec.err);
@@ -899,12 +901,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool dense = d.flags & kDense;
         const int xld = dense ? mp : kx;
         if (fresh) {
-            acc.setup(d.rows, d.rows, tid);
+            acc.setup(d.rows, d.ld, tid);
             acc.zero();
             fresh = false;
         }
         if (!(d.flags & kZero))
-            acc.gemv(stage_tile(s, pp, ring.stage), d.rows, d.rows, d.cols, stage_x(s, pp, ring.stage), xld, nv);
+            acc.gemv(stage_tile(s, pp, ring.stage), d.ld, d.rows, d.cols, stage_x(s, pp, ring.stage), xld, nv);
         release(&s.empty[ring.stage], lane);
         ring.next();
         if (d.flags & kLast) {
