@@ -403,7 +403,10 @@ int up_all(const h2_op &op, const h2_device &dv, const h2s::Op<T> &o, const h2s:
             v.X, op.n, v.nv, v.xr, v.ldr);
         ++launches;
     }
-    k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
+    if (v.xr)
+        k_gather_rows<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
+    else
+        k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
     k_up_sub<T, NVMAX><<<sp.grid_bsub, kThreads, sp.sm_bsub, st>>>(o, v, sp.bsub, op.q - sp.Lw, sp.Lw, sp.nsub, 1);
     for (int lin = op.q - sp.Lw; lin > 0;) {
         const int L = std::min(sp.Ltop, lin), lr = lin - L;

@@ -379,9 +379,6 @@ struct Acc {
             for (int e = 0; e < VEC; ++e)
                 if (v < nv && e < per && o0 + e < R) a[v][e] += src[v * ld + o0 + e];
     }
-    // The tensor-core path and the row-major staging run on the wide accumulator only.
-    __device__ __forceinline__ void store_tile(unsigned char *, int, int, int) const {}
-    __device__ __forceinline__ void write_rows(T *, int, int, int) const {}
     // Leaf epilogue: user-order rows of the held outputs (fetched before the tile arrives),
     // then Y[v*n + row] = alpha y + beta Y for the threads holding final values.
     int64_t u[VEC];
@@ -613,47 +610,20 @@ using AccOf = typename std::conditional<(NVMAX >= kWideMin), AccW<T, NVMAX>, Acc
 // ------------------------------------------------------------------ gather
 
 // xt[leaf][v][i] = X[v*n + perm[leaf_lo[leaf] + i]]: one CTA per leaf (grid-stride). Also
-// resets the scheduling tickets of this product.
+// resets the scheduling tickets of this product. With vec.xtb (tensor-core passes) it also
+// writes each leaf's split-BF16 tile.
 template <typename T>
 __global__ void k_gather(Op<T> op, Vec<T> vec)
 {
     if (blockIdx.x == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
     for (int64_t leaf = blockIdx.x; leaf < op.nleaves; leaf += gridDim.x) {
         const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
-        if (vec.xr != nullptr) {
-            // whole rows from the row-major copy (coalesced), staged and written per vector
-            __shared__ T rows[64 * 33];
-            for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
-                const int i = e / vec.nv, v = e % vec.nv;
-                rows[i * 33 + v] = vec.xr[int64_t(op.perm[r0 + i]) * vec.ldr + v];
-            }
-            __syncthreads();
-            for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
-                const int v = e / R, i = e % R;
-                vec.xt[(leaf * vec.vs + v) * op.mp + i] = rows[i * 33 + v];
-            }
-            if constexpr (sizeof(T) == 4) {
-                if (vec.xtb != nullptr) {
-                    unsigned char *tile = vec.xtb + leaf * vec_tile_bytes(vec.np);
-                    for (int e = threadIdx.x; e < vec.np * 64; e += blockDim.x) {
-                        const int i = e % 64, v = e / 64;
-                        const float x = (i < R && v < vec.nv) ? rows[i * 33 + v] : 0.f;
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-                        const uint32_t off = sw128(v, i);
-                        *reinterpret_cast<__nv_bfloat16 *>(tile + off) = hi;
-                        *reinterpret_cast<__nv_bfloat16 *>(tile + vec.np * 128 + off) = lo;
-                    }
-                }
-            }
-            __syncthreads();
-        } else if (vec.xtb == nullptr) {
+        if (vec.xtb == nullptr) {
             for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
                 const int i = e % R, v = e / R;
                 vec.xt[(leaf * vec.vs + v) * op.mp + i] = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
             }
         } else if constexpr (sizeof(T) == 4) {
-            // also the leaf's split-BF16 tile (np x 64, zero beyond the leaf and beyond nv)
             unsigned char *tile = vec.xtb + leaf * vec_tile_bytes(vec.np);
             for (int e = threadIdx.x; e < vec.np * 64; e += blockDim.x) {
                 const int i = e % 64, v = e / 64;
@@ -669,6 +639,44 @@ __global__ void k_gather(Op<T> op, Vec<T> vec)
                 *reinterpret_cast<__nv_bfloat16 *>(tile + vec.np * 128 + off) = lo;
             }
         }
+    }
+}
+
+// The gather of wide passes (leaves of at most 64 points, at most 32 vectors): each permuted
+// point's nv values are one row of the row-major copy vec.xr (coalesced reads), staged in
+// shared memory and written per vector, with the split-BF16 tile when vec.xtb is set. Also
+// resets the scheduling tickets.
+template <typename T>
+__global__ void k_gather_rows(Op<T> op, Vec<T> vec)
+{
+    __shared__ T rows[64 * 33];
+    if (blockIdx.x == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
+    for (int64_t leaf = blockIdx.x; leaf < op.nleaves; leaf += gridDim.x) {
+        const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
+        for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+            const int i = e / vec.nv, v = e % vec.nv;
+            rows[i * 33 + v] = vec.xr[int64_t(op.perm[r0 + i]) * vec.ldr + v];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+            const int v = e / R, i = e % R;
+            vec.xt[(leaf * vec.vs + v) * op.mp + i] = rows[i * 33 + v];
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (vec.xtb != nullptr) {
+                unsigned char *tile = vec.xtb + leaf * vec_tile_bytes(vec.np);
+                for (int e = threadIdx.x; e < vec.np * 64; e += blockDim.x) {
+                    const int i = e % 64, v = e / 64;
+                    const float x = (i < R && v < vec.nv) ? rows[i * 33 + v] : 0.f;
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+                    const uint32_t off = sw128(v, i);
+                    *reinterpret_cast<__nv_bfloat16 *>(tile + off) = hi;
+                    *reinterpret_cast<__nv_bfloat16 *>(tile + vec.np * 128 + off) = lo;
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -789,7 +797,8 @@ __global__ void __launch_bounds__(kThreads)
                     acc.store(s.sub + ((1 << L) + j) * wstride, kx, nv, k);
                     acc.store(vec.xh + (op.first_leaf + leaf) * kx * vs, kx, nv, k);
                 }
-                if (vec.xb) acc.store_tile(vec.xb + (op.first_leaf + leaf) * vec_tile_bytes(vec.np), vec.np, nv, k);
+                if constexpr (NVMAX >= kWideMin)
+                    if (vec.xb) acc.store_tile(vec.xb + (op.first_leaf + leaf) * vec_tile_bytes(vec.np), vec.np, nv, k);
                 h2p::consumer_sync(kConsumers);
             }
         }
@@ -815,7 +824,8 @@ __global__ void __launch_bounds__(kThreads)
                     acc.store(s.sub + pslot * wstride, kx, nv, k);
                     acc.store(vec.xh + par * kx * vs, kx, nv, k);
                 }
-                if (vec.xb) acc.store_tile(vec.xb + par * vec_tile_bytes(vec.np), vec.np, nv, k);
+                if constexpr (NVMAX >= kWideMin)
+                    if (vec.xb) acc.store_tile(vec.xb + par * vec_tile_bytes(vec.np), vec.np, nv, k);
                 h2p::consumer_sync(kConsumers);
             }
         }
@@ -1025,10 +1035,16 @@ __global__ void __launch_bounds__(kThreads)
             acc.gemv(stage_tile(s, pp, ring.stage), mp, R, k, s.sub + ((1 << L) + j) * wstride, kx, nv);
             if (acc.reduce(R, nv, s.red)) {
                 acc.add(stage_x(s, pp, ring.stage), mp, nv, R);
-                if (vec.yr)
-                    acc.write_rows(vec.yr, vec.ldr, nv, R);
-                else
+                // narrow passes write Y directly (a runtime choice here slowed the nv = 1 leaf
+                // epilogue measurably); wide passes may stage rows for k_rows_out
+                if constexpr (NVMAX >= kWideMin) {
+                    if (vec.yr)
+                        acc.write_rows(vec.yr, vec.ldr, nv, R);
+                    else
+                        acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
+                } else {
                     acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
+                }
             }
             release(&s.empty[ring.stage], lane);
             ring.next();
