@@ -155,7 +155,7 @@ def cpu_baseline(steps: int = 0):
             "gflops": 2 * ent / t / 1e9}
 
 
-def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None):
+def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with_fp64=True):
     """The multi-vector workload: N = 2^21 uniform random points in [0,1]^3, exp(-r/0.2),
     leaf 64, 4 x 4 x 4 Chebyshev grid (rank 64), eta 0.7, 32 vectors, in split-BF16 on the
     tensor cores and in FP32. Its ~113 GB of stored blocks exceed L2 by far, so no flush is
@@ -175,12 +175,18 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None):
            "dense_blocks": info.n_dense, "bytes_per_step": bytes_step, "flops_per_step": flops,
            "l2": f"inputs larger than L2 ({4 * mat_entries / 1e9:.1f} GB of blocks per product), no flush"}
     stream = torch.cuda.current_stream()
-    for prec in ("bf16x2", "fp32"):
+    results = {}
+    precs = ("bf16x2", "fp32", "fp64") if with_fp64 else ("bf16x2", "fp32")
+    for prec in precs:
         t0 = time.perf_counter()
         op.upload(prec)
         upload_s = time.perf_counter() - t0
         X = torch.from_numpy(Xh).cuda().t()
+        if prec == "fp64":
+            X = X.double()
         Y = op.new_vectors(nv, fill=0.0)
+        if prec == "fp64":  # DFMA-bound (about 2 s per product): one warm-up, two timed
+            steps, warmup = 2, 1
         for _ in range(warmup):
             op.matvec(X, Y)
         h2.h2_get_timing(op.handle)
@@ -215,11 +221,21 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None):
                     "achieved": blk_tflops, "peak": FFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": blk_tflops / FFMA_PEAK_TFLOPS, "peak_kind": "derived (unit counts x clock)",
                     "hbm_GB/s": blk_gbs}
+        if prec == "fp64":
+            roof = {"kernel": "k_stream (FP64, register-blocked wide accumulator)", "bound": "alu",
+                    "note": "DFMA-bound: 16 flop per FP64 byte at 32 vectors; FP64 rate is a small fraction of FP32"}
+            gbs = 8 * (mat_entries + vec_elems) / (ms_step * 1e-3) / 1e9
         out[prec] = {"ms_per_step": ms_step, "ms_median": float(np.median(ms)), "GB/s": gbs,
                      "gflops": flops / (ms_step * 1e-3) / 1e9, "frac_of_hbm": gbs / peak_hbm,
                      "steps": steps, "upload_s": upload_s,
                      "phases_ms": dict(zip(h2.PHASES, [float(v) for v in phase_ms])), "roofline": roof}
+        results[prec] = Y.t().contiguous().cpu().double().numpy()
         del X, Y
+    if "fp64" in results:
+        ref = results["fp64"]
+        nref = float(np.linalg.norm(ref))
+        for prec in ("bf16x2", "fp32"):
+            out[prec]["relerr_vs_fp64"] = float(np.linalg.norm(results[prec] - ref)) / nref
     op.close()
     return out
 
@@ -375,6 +391,8 @@ def main():
                     help="points of the 3D cloud of the 32-vector measurement (2^21 = the benchmarked size; "
                          "smaller sizes are for profiler captures)")
     ap.add_argument("--multi-rhs-steps", type=int, default=0, help="timed 32-vector products (0: steps / 20, >= 5)")
+    ap.add_argument("--no-multi-rhs-fp64", action="store_true",
+                    help="skip the FP64 product of the 32-vector workload (218 GB of blocks at 2^21 points)")
     ap.add_argument("--no-serve", action="store_true", help="skip the CG serving-loop measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-operator measurement")
     ap.add_argument("--batch-count", type=int, default=64, help="operators of the batched measurement")
@@ -531,7 +549,8 @@ def main():
         op.close()
         try:
             mr_steps = args.multi_rhs_steps if args.multi_rhs_steps > 0 else max(5, args.steps // 20)
-            line["multi_rhs"] = multi_rhs(h2, torch, mr_steps, 3, peak_hbm, peak_kind, args.cloud_n)
+            line["multi_rhs"] = multi_rhs(h2, torch, mr_steps, 3, peak_hbm, peak_kind, args.cloud_n,
+                                          not args.no_multi_rhs_fp64)
         except Exception as exc:  # reported, never silently dropped
             line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batch:
