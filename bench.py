@@ -107,6 +107,21 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over the ranks (x itself without a process group)."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(world: int, bytes_per_rank_step: float, ms_per_step: float) -> float:
+    """Whole-job throughput of independent replicas: every rank moves bytes_per_rank_step
+    per step, and the job's step takes the slowest rank's time."""
+    return world * bytes_per_rank_step / (ms_per_step * 1e-3) / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -475,13 +490,10 @@ def main():
         res = time_products("fp32", args.steps, max(3, args.warmup))
     clocks = clk.summary()
     ms_local = float(np.sum(res["step_ms"]))
-    ms_t = torch.tensor([ms_local], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_total = float(ms_t.item())
+    ms_total = max_over_ranks(ms_local, dist, "cuda")
     ms_step = ms_total / args.steps
     bytes_step = 4 * (mat_entries + vec_elems)
-    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    value = job_gbs(world, bytes_step, ms_step)
 
     # roofline of the dominant kernel: the streaming product of coupling rows (levels below
     # the top) and dense rows (phase 1); its algorithmic bytes are the blocks it streams plus
@@ -510,10 +522,7 @@ def main():
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    e2e_t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * bytes_step / (float(e2e_t.item()) * 1e-3) / 1e9
+    e2e_value = job_gbs(world, bytes_step, max_over_ranks(e2e_ms, dist, "cuda"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
