@@ -320,6 +320,50 @@ def serve_benchmark(h2, torch, requests_per_rate=32, maxit=100, rates=(0.5, 0.8,
             op.close()
 
 
+def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, Y_stored):
+    """The same product with the coupling and dense entries evaluated in FP32 inside the
+    stream (H2_FP32_MF: no blocks stored; bases and transfers as in FP32). Its bound is the
+    arithmetic of the evaluations: one special-function operation per Gaussian entry, at
+    most 152 SMs x 16 per clock x 2.07 GHz; the measured rate is evaluations per second over
+    the block stream's time. The L2 is flushed before every timed product, as for the stored
+    path."""
+    info = op.info
+    evals = info.coupling_entries + info.dense_entries
+    ref = Y_stored.double().cpu().numpy()
+    op.upload("fp32mf")
+    X = torch.from_numpy(x_host).to(device="cuda", dtype=torch.float32)
+    Y = torch.empty_like(X)
+    for _ in range(warmup):
+        op.matvec(X, Y)
+    h2.h2_get_timing(op.handle)
+    h2.h2_set_timing(op.handle, True)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        op.matvec(X, Y)
+        b.record(stream)
+    torch.cuda.synchronize()
+    h2.h2_set_timing(op.handle, False)
+    phase_ms, _, prods = h2.h2_get_timing(op.handle)
+    phase_ms = phase_ms / max(prods, 1)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    got = Y.double().cpu().numpy()
+    sfu_peak = 152 * 16 * 2.07e9
+    stream_rate = evals / (float(phase_ms[1]) * 1e-3)
+    out = {"ms_per_step": ms, "speedup_vs_stored": stored_ms / ms, "evaluations_per_step": evals,
+           "evaluations_per_s": evals / (ms * 1e-3), "device_bytes": h2.h2_get_info(op.handle).device_bytes,
+           "phases_ms": dict(zip(h2.PHASES, [float(v) for v in phase_ms])),
+           "relerr_vs_stored_fp32": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+           "roofline": {"kernel": "k_stream_mf (FP32 evaluation of coupling and dense entries)", "bound": "alu",
+                        "achieved": stream_rate, "peak": sfu_peak, "unit": "evaluations/s",
+                        "frac": stream_rate / sfu_peak,
+                        "peak_kind": "derived: 152 SMs x 16 special-function results per clock x 2.07 GHz"}}
+    op.upload("fp32")
+    return out
+
+
 def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18):
     """Batched products of 64 uneven operators (synthetic_inputs.uneven_batch: N log-uniform
     in [2^12, 2^18], even members 2D grids with orders 4-8, odd members 3D clouds with orders
@@ -409,6 +453,7 @@ def main():
     ap.add_argument("--no-multi-rhs-fp64", action="store_true",
                     help="skip the FP64 product of the 32-vector workload (218 GB of blocks at 2^21 points)")
     ap.add_argument("--no-serve", action="store_true", help="skip the CG serving-loop measurement")
+    ap.add_argument("--no-matrix-free", action="store_true", help="skip the matrix-free product measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-operator measurement")
     ap.add_argument("--batch-count", type=int, default=64, help="operators of the batched measurement")
     ap.add_argument("--batch-nmax", type=int, default=2 ** 18,
@@ -554,6 +599,12 @@ def main():
         "cpu_baseline": cpu,
         "build_s": build_s, "upload_s": res["upload_s"],
     }
+    if not args.no_matrix_free:
+        try:
+            line["matrix_free"] = matrix_free(h2, torch, op, x_host, flush, stream, max(20, args.steps // 4),
+                                              max(3, args.warmup), ms_step, res["Y"])
+        except Exception as exc:  # reported, never silently dropped
+            line["matrix_free"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_multi_rhs:
         op.close()
         try:

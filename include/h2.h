@@ -31,7 +31,7 @@
  *     void*, NULL = the legacy default stream). Launch errors are returned at once; a
  *     fault during execution surfaces at a later call or synchronisation as H2_ECUDA.
  *   - Multivectors are n x nv, column-major, leading dimension n, in the caller's point
- *     order. Element type: double for H2_FP64, float for H2_FP32 and H2_BF16X2.
+ *     order. Element type: double for H2_FP64, float for H2_FP32, H2_BF16X2 and H2_FP32_MF.
  *   - Inputs are copied at h2_build; device X, Y, b, x stay owned by the caller; the
  *     handle owns its host operator and its device copy until h2_destroy.
  *   - One handle may be used by one stream at a time through h2_matvec (its internal
@@ -76,7 +76,9 @@ typedef struct {
 typedef enum {
     H2_FP64 = 0,  /* entries and arithmetic in double */
     H2_FP32 = 1,  /* entries and arithmetic in float */
-    H2_BF16X2 = 2 /* entries as bf16 hi + bf16 lo pairs, FP32 accumulation */
+    H2_BF16X2 = 2, /* entries as bf16 hi + bf16 lo pairs, FP32 accumulation */
+    H2_FP32_MF = 3 /* matrix-free FP32: bases and transfers stored, coupling and dense entries
+                      evaluated in float inside every product (no blocks stored) */
 } h2_prec;
 
 #define H2_MAX_LEVELS 32

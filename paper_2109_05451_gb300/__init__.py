@@ -19,11 +19,11 @@ import numpy as np
 from . import build as _build
 
 H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ETIMEOUT, H2_ESTATE, H2_ENOTCONV = 0, -1, -2, -3, -4, -5, 1
-H2_FP64, H2_FP32, H2_BF16X2 = 0, 1, 2
+H2_FP64, H2_FP32, H2_BF16X2, H2_FP32_MF = 0, 1, 2, 3
 H2_K_EXP, H2_K_GAUSS, H2_K_IMQ, H2_K_POLY = 0, 1, 2, 3
 H2_MAX_LEVELS = 32
 KERNELS = {"exp": H2_K_EXP, "gauss": H2_K_GAUSS, "imq": H2_K_IMQ, "poly": H2_K_POLY}
-PRECISIONS = {"fp64": H2_FP64, "fp32": H2_FP32, "bf16x2": H2_BF16X2}
+PRECISIONS = {"fp64": H2_FP64, "fp32": H2_FP32, "bf16x2": H2_BF16X2, "fp32mf": H2_FP32_MF}
 
 
 class H2Error(RuntimeError):

@@ -27,6 +27,7 @@
 #include "h2_stream.cuh"
 #include "h2_tcstream.cuh"
 #include "h2_batch.cuh"
+#include "h2_mf.cuh"
 
 #include <dlfcn.h>
 
@@ -73,6 +74,9 @@ struct h2_device {
     int64_t n_chunks_bottom = 0, n_chunks_top = 0;
     int64_t n_desc_bottom = 0, n_desc_top = 0;
     int *err = nullptr;  // device error flag (a bounded wait ran out)
+    // matrix-free FP32 (H2_FP32_MF): coordinates instead of blocks
+    bool mf = false;
+    h2s::MfArgs mfa{};
     // execution resources
     cudaStream_t side = nullptr;
     cudaEvent_t ev_up = nullptr, ev_top = nullptr;
@@ -164,6 +168,7 @@ inline bool wide_ok(const h2_device &dv) { return dv.kx <= 64 && dv.mp <= 64; }
 // vectors, on the wide kernels; otherwise kChunk.
 inline int pass_vectors(const h2_device &dv, int nv)
 {
+    if (dv.mf) return std::min(nv, kChunk);
     if (dv.tc || (nv > kChunk && wide_ok(dv))) return std::min(nv, kWidePass);
     return std::min(nv, kChunk);
 }
@@ -251,6 +256,51 @@ void set_kernel_attributes()
     done = true;
 }
 
+// Matrix-free stream launch for the operator's kernel kind and dimension (FP32 only).
+template <int KIND, int DIM, int NVMAX>
+void launch_mf_kind(const h2s::Op<float> &o, const h2s::Vec<float> &v, const h2s::MfArgs &ma, const h2s::Pipe &p,
+                    size_t smem, unsigned grid, const h2s::StreamDesc *desc, const int64_t *chunks, int64_t nchunks,
+                    int ticket, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(h2s::k_stream_mf<KIND, DIM, NVMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        cudaFuncSetAttribute(h2s::k_stream_mf<KIND, DIM, NVMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr = true;
+    }
+    h2s::k_stream_mf<KIND, DIM, NVMAX><<<grid, h2s::kThreads, smem, st>>>(o, v, ma, p, desc, chunks, nchunks, ticket);
+}
+
+template <int DIM, int NVMAX>
+void launch_mf_dim(int kind, const h2s::Op<float> &o, const h2s::Vec<float> &v, const h2s::MfArgs &ma,
+                   const h2s::Pipe &p, size_t smem, unsigned grid, const h2s::StreamDesc *desc, const int64_t *chunks,
+                   int64_t nchunks, int ticket, cudaStream_t st)
+{
+    switch (kind) {
+    case H2_K_EXP:
+        return launch_mf_kind<H2_K_EXP, DIM, NVMAX>(o, v, ma, p, smem, grid, desc, chunks, nchunks, ticket, st);
+    case H2_K_GAUSS:
+        return launch_mf_kind<H2_K_GAUSS, DIM, NVMAX>(o, v, ma, p, smem, grid, desc, chunks, nchunks, ticket, st);
+    case H2_K_IMQ:
+        return launch_mf_kind<H2_K_IMQ, DIM, NVMAX>(o, v, ma, p, smem, grid, desc, chunks, nchunks, ticket, st);
+    default:
+        return launch_mf_kind<H2_K_POLY, DIM, NVMAX>(o, v, ma, p, smem, grid, desc, chunks, nchunks, ticket, st);
+    }
+}
+
+template <int NVMAX>
+void launch_mf(const h2_op &op, const h2s::Op<float> &o, const h2s::Vec<float> &v, const h2s::MfArgs &ma,
+               const h2s::Pipe &p, size_t smem, unsigned grid, const h2s::StreamDesc *desc, const int64_t *chunks,
+               int64_t nchunks, int ticket, cudaStream_t st)
+{
+    if (op.dim == 3)
+        launch_mf_dim<3, NVMAX>(op.ker.kind, o, v, ma, p, smem, grid, desc, chunks, nchunks, ticket, st);
+    else
+        launch_mf_dim<2, NVMAX>(op.ker.kind, o, v, ma, p, smem, grid, desc, chunks, nchunks, ticket, st);
+}
+
 template <typename T, int NVMAX>
 int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
                  const Workspace &w, cudaStream_t st, const h2_exec &ex)
@@ -281,9 +331,18 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * kx, size_t(mp) * dv.max_leaf_rows) * es) + 15) /
                                        16 * 16);
     const uint32_t x_str = uint32_t(std::max(mp, kx) * NVMAX * es);
-    const Pipe p_bot = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
-    const Pipe p_top = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
+    // matrix-free: no tiles; per stage the input segment and two coordinate lists; the
+    // evaluation is bound by instruction issue and latency, so four small CTAs per SM
+    // (16 consumer warps) share each SM, leaving room for the side stream's kernels
+    const bool mf = dv.mf && sizeof(T) == 4;
+    const uint32_t x_mf = mf_seg_bytes(kx, mp, NVMAX) + 2 * mf_coord_bytes(k, mp);
+    const Pipe p_bot = mf ? make_pipe<T, NVMAX>(0, x_mf, 0, kx, true, 36 * 1024, 12)
+                          : make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
+    const Pipe p_top = mf ? make_pipe<T, NVMAX>(0, x_mf, 0, kx, true, 32 * 1024, 4)
+                          : make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
     const size_t sm_bot = smem_bytes<T, NVMAX>(p_bot, 0, kx, true), sm_top = smem_bytes<T, NVMAX>(p_top, 0, kx, true);
+    const unsigned grid_bot = mf ? unsigned(std::max<int64_t>(1, std::min<int64_t>(4 * int64_t(dv.num_sms), dv.n_chunks_bottom)))
+                                 : unsigned(dv.grid_bottom);
     set_kernel_attributes<T, NVMAX>();
     const int grid_bsub = int(std::min<int64_t>(nsub, int64_t(dv.num_sms) * 2));
 
@@ -299,9 +358,20 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     }
     // ---- stream A: coupling rows of the lower levels + dense rows
     ev = dv.begin(st);
-    if (dv.n_chunks_bottom > 0)
-        k_stream<T, NVMAX><<<dv.grid_bottom, kThreads, sm_bot, st>>>(o, v, p_bot, dv.desc_bottom, dv.chunks_bottom,
-                                                                     dv.n_chunks_bottom, 0);
+    if (dv.n_chunks_bottom > 0) {
+        if constexpr (sizeof(T) == 4 && NVMAX <= kChunk) {
+            if (mf) {
+                launch_mf<NVMAX>(op, o, v, dv.mfa, p_bot, sm_bot, grid_bot, dv.desc_bottom, dv.chunks_bottom,
+                                 dv.n_chunks_bottom, 0, st);
+            } else {
+                k_stream<T, NVMAX><<<grid_bot, kThreads, sm_bot, st>>>(o, v, p_bot, dv.desc_bottom, dv.chunks_bottom,
+                                                                       dv.n_chunks_bottom, 0);
+            }
+        } else {
+            k_stream<T, NVMAX><<<grid_bot, kThreads, sm_bot, st>>>(o, v, p_bot, dv.desc_bottom, dv.chunks_bottom,
+                                                                   dv.n_chunks_bottom, 0);
+        }
+    }
     dv.end(1, ev, st, dv.n_chunks_bottom > 0 ? 1 : 0);
     // ---- stream B: the levels above the bottom subtrees
     if (top) {
@@ -317,8 +387,17 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
             lin = lr;
         }
         if (dv.n_chunks_top > 0) {
-            k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
-                                                                      dv.n_chunks_top, 1);
+            bool done = false;
+            if constexpr (sizeof(T) == 4 && NVMAX <= kChunk) {
+                if (mf) {
+                    launch_mf<NVMAX>(op, o, v, dv.mfa, p_top, sm_top, unsigned(dv.grid_top), dv.desc_top,
+                                     dv.chunks_top, dv.n_chunks_top, 1, sb);
+                    done = true;
+                }
+            }
+            if (!done)
+                k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
+                                                                          dv.n_chunks_top, 1);
             ++launches;
         }
         for (int lr = 0; lr <= Lb - 1;) {
@@ -610,6 +689,18 @@ int generate_blocks(const h2_op &op, h2_device &dv, const int32_t *d_cpl_row, co
         h2k::gen_dense<T><<<unsigned(std::min<int64_t>(ndns, 1 << 20)), 256, 0, st>>>(
             reinterpret_cast<T *>(dv.vals + d_region), d_dns_off, d_dns_row, d_dns_col, ndns, dv.leaf_lo,
             d_pts_tree, op.dim, f);
+    return cuda_status(cudaGetLastError());
+}
+
+// Coordinates of the matrix-free precision: every cluster's Chebyshev points and every
+// leaf's points as float4.
+int generate_mf_points(const h2_op &op, h2_device &dv, const double *d_cheb, const double *d_pts, cudaStream_t st)
+{
+    const int64_t nodes = op.nnodes + 1;
+    h2s::k_mf_node_points<<<unsigned(std::min<int64_t>((nodes * op.k + 255) / 256, 65535)), 256, 0, st>>>(
+        d_cheb, nodes, op.dim, op.p, op.k, const_cast<float4 *>(dv.mfa.node_pts));
+    h2s::k_mf_leaf_points<<<unsigned(std::min<int64_t>((op.nleaves() * dv.mp + 255) / 256, 65535)), 256, 0, st>>>(
+        d_pts, dv.leaf_lo, op.nleaves(), op.dim, dv.mp, const_cast<float4 *>(dv.mfa.leaf_pts));
     return cuda_status(cudaGetLastError());
 }
 
@@ -1121,7 +1212,7 @@ extern "C" {
 int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
 {
     if (!h) return H2_EINVAL;
-    if (prec != H2_FP64 && prec != H2_FP32 && prec != H2_BF16X2) return H2_EINVAL;
+    if (prec != H2_FP64 && prec != H2_FP32 && prec != H2_BF16X2 && prec != H2_FP32_MF) return H2_EINVAL;
     h2_op &op = *h;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     h2_device_free(&op);
@@ -1133,6 +1224,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     dv->prec = prec;
     dv->esize = prec == H2_FP64 ? 8 : 4;  // bases and transfers: FP32 for H2_BF16X2
     dv->tc = prec == H2_BF16X2;
+    dv->mf = prec == H2_FP32_MF;
     const size_t es = dv->esize;
     const int k = op.k;
     const int64_t nleaves = op.nleaves(), first_leaf = op.first_leaf(), ncpl = int64_t(op.cpl_col.size()),
@@ -1174,8 +1266,9 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
             dns_off[b + 1] = dns_off[b] + (cnt + 31) / 32 * 32;  // 128-byte aligned blocks
         }
     const size_t tcb = h2s::kTcTileBytes;  // split-BF16 tile of one block
-    const size_t s_bytes = dv->tc ? size_t(ncpl) * tcb : align_up(size_t(ncpl) * dv->kkp * es);
-    const size_t d_bytes = dv->tc ? size_t(ndns) * tcb : align_up(size_t(dns_off[ndns]) * es);
+    // stored entries (none for the matrix-free precision, which keeps coordinates instead)
+    const size_t s_bytes = dv->mf ? 0 : dv->tc ? size_t(ncpl) * tcb : align_up(size_t(ncpl) * dv->kkp * es);
+    const size_t d_bytes = dv->mf ? 0 : dv->tc ? size_t(ndns) * tcb : align_up(size_t(dns_off[ndns]) * es);
 
     // ---- stream descriptors: coupling rows of levels >= Lb and all dense rows (bottom),
     //      coupling rows of levels < Lb (top)
@@ -1250,6 +1343,8 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     const size_t o_U = take(size_t(nleaves) * mp * kx * es), o_Ut = take(size_t(nleaves) * kx * mp * es);
     const size_t o_E = take(size_t(op.nnodes + 1) * k * kx * es), o_Et = take(size_t(op.nnodes + 1) * k * kx * es);
     const size_t o_vals = take(s_bytes + d_bytes);
+    const size_t o_npts = dv->mf ? take(size_t(op.nnodes + 1) * k * sizeof(float4)) : 0;
+    const size_t o_lpts = dv->mf ? take(size_t(nleaves) * mp * sizeof(float4)) : 0;
     const size_t o_db = take(db.size() * sizeof(h2s::StreamDesc)), o_dt = take(dt.size() * sizeof(h2s::StreamDesc));
     const size_t o_pb = take(pb.size() * 8), o_pt = take(pt.size() * 8), o_err = take(16);
     const size_t persistent = off;
@@ -1285,6 +1380,15 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     dv->chunks_bottom = reinterpret_cast<int64_t *>(arena + o_pb);
     dv->chunks_top = reinterpret_cast<int64_t *>(arena + o_pt);
     dv->err = reinterpret_cast<int *>(arena + o_err);
+    if (dv->mf) {
+        dv->mfa.node_pts = reinterpret_cast<const float4 *>(arena + o_npts);
+        dv->mfa.leaf_pts = reinterpret_cast<const float4 *>(arena + o_lpts);
+        dv->mfa.k = k;
+        dv->mfa.a = float(op.ker.a);
+        dv->mfa.neg_inv_a = op.ker.a != 0.0 ? float(-1.0 / op.ker.a) : 0.f;
+        dv->mfa.neg_b = float(-op.ker.b);
+        dv->mfa.deg = op.ker.deg;
+    }
     char *tp = tmp;
     double *d_cheb = reinterpret_cast<double *>(tp);
     tp += t_cheb;
@@ -1349,7 +1453,8 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     cp(d_doff, dns_off.data(), (ndns + 1) * 8);
     if (rc == H2_OK) rc = cuda_status(cudaMemsetAsync(dv->err, 0, 16, st));
     if (rc == H2_OK)
-        rc = dv->tc ? generate_tc_blocks(op, *dv, d_crow, d_drow, d_dcol, d_ccol, d_cheb, d_pts, s_bytes, st)
+        rc = dv->mf ? generate_mf_points(op, *dv, d_cheb, d_pts, st)
+             : dv->tc ? generate_tc_blocks(op, *dv, d_crow, d_drow, d_dcol, d_ccol, d_cheb, d_pts, s_bytes, st)
              : es == 8 ? generate_blocks<double>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st)
                        : generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st);
     if (rc == H2_OK) rc = cuda_status(cudaStreamSynchronize(st));
@@ -1556,7 +1661,7 @@ int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void 
         if (!ops[i] || !X[i] || !Y[i] || nv[i] < 1) return H2_EINVAL;
         const h2_device *dv = ops[i]->dev;
         if (!dv) return H2_ESTATE;
-        if (dv->tc) return H2_EINVAL;  // FP64 or FP32 members only
+        if (dv->tc || dv->mf) return H2_EINVAL;  // stored FP64 or FP32 members only
         if (esize && dv->esize != esize) return H2_EINVAL;
         esize = dv->esize;
         if (!(nv[i] <= kChunk || (wide_ok(*dv) && nv[i] <= kWidePass))) return H2_EINVAL;  // one pass each

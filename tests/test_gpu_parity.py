@@ -16,8 +16,8 @@ pytestmark = pytest.mark.gpu
 
 import paper_2109_05451_gb300 as h2  # noqa: E402
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
-DT = {"fp64": torch.float64, "fp32": torch.float32}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32mf": 1e-5}
+DT = {"fp64": torch.float64, "fp32": torch.float32, "fp32mf": torch.float32}
 
 
 def relerr(a, b):
@@ -128,6 +128,21 @@ def test_wide_fallback_for_large_leaves():
     op.close()
 
 
+@pytest.mark.parametrize("nv", [1, 3, 6])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_matrix_free_matches_oracle(built, name, nv):
+    """Coupling and dense entries evaluated in FP32 inside the product (no blocks stored):
+    the same structure, so the oracle's product is the reference (1e-5)."""
+    pts, ker, orc, op = built(name)
+    op.upload("fp32mf")
+    assert h2.h2_get_info(op.handle).uploaded_prec == h2.H2_FP32_MF
+    X = si.gaussian_vectors(len(pts), nv, 21)
+    Y0 = si.gaussian_vectors(len(pts), nv, 22)
+    got = gpu_matvec(op, X, "fp32mf", 1.25, -0.5, Y0)
+    assert np.all(np.isfinite(got))
+    assert relerr(got, orc.matvec(X, 1.25, -0.5, Y0)) <= TOL["fp32mf"]
+
+
 def test_workspace_entry_point(built):
     pts, ker, orc, op = built("grid64_exp")
     op.upload("fp64")
@@ -159,7 +174,7 @@ def grid1024():
     return w, op, X, rows, ref, orc
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp32mf"])
 def test_full_size_grid1024_sampled_leaves(grid1024, prec):
     """N = 2^20 Gaussian grid, rank 64, eta 0.7, nv = 1 -- the benchmarked workload."""
     w, op, X, rows, ref, orc = grid1024
