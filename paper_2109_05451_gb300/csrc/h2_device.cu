@@ -79,7 +79,7 @@ struct h2_device {
     h2s::MfArgs mfa{};
     // execution resources
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_up = nullptr, ev_top = nullptr;
+    cudaEvent_t ev_up = nullptr, ev_top = nullptr, ev_topup = nullptr;
     // handle-owned workspace for h2_matvec
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -140,6 +140,7 @@ struct h2_device {
         for (auto e : event_pool) cudaEventDestroy(e);
         if (ev_up) cudaEventDestroy(ev_up);
         if (ev_top) cudaEventDestroy(ev_top);
+        if (ev_topup) cudaEventDestroy(ev_topup);
         if (side) cudaStreamDestroy(side);
     }
 };
@@ -338,8 +339,8 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     const uint32_t x_mf = mf_seg_bytes(kx, mp, NVMAX) + 2 * mf_coord_bytes(k, mp);
     const Pipe p_bot = mf ? make_pipe<T, NVMAX>(0, x_mf, 0, kx, true, 36 * 1024, 12)
                           : make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
-    const Pipe p_top = mf ? make_pipe<T, NVMAX>(0, x_mf, 0, kx, true, 32 * 1024, 4)
-                          : make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
+    // (the upper levels' coupling blocks are stored for the matrix-free precision too)
+    const Pipe p_top = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
     const size_t sm_bot = smem_bytes<T, NVMAX>(p_bot, 0, kx, true), sm_top = smem_bytes<T, NVMAX>(p_top, 0, kx, true);
     const unsigned grid_bot = mf ? unsigned(std::max<int64_t>(1, std::min<int64_t>(4 * int64_t(dv.num_sms), dv.n_chunks_bottom)))
                                  : unsigned(dv.grid_bottom);
@@ -352,9 +353,32 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
     dv.end(0, ev, st, 2);
     const bool top = Lb >= 1;
+    cudaEvent_t ev_topup = static_cast<cudaEvent_t>(ex.ev_topup);
     if (top) {
         cudaEventRecord(ev_up, st);
         cudaStreamWaitEvent(side, ev_up, 0);
+    }
+    cudaEvent_t eb = nullptr;
+    int top_launches = 0;
+    // ---- stream B, part 1: upsweep of the levels above the bottom subtrees
+    auto top_up = [&]() {
+        eb = dv.begin(side);
+        for (int lin = Lb; lin > 0;) {
+            const int L = std::min(Ltop, lin), lr = lin - L;
+            const int64_t ns = int64_t(1) << lr;
+            k_up_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, side>>>(
+                o, v, p_tsub, lr, L, ns, 0);
+            ++top_launches;
+            lin = lr;
+        }
+    };
+    // The matrix-free stream keeps the SMs' issue slots busy, which slows latency-bound
+    // kernels next to it several times: it starts only after the upper upsweep, which then
+    // runs alone; the upper rows and downsweep overlap it.
+    if (top && mf) {
+        top_up();
+        cudaEventRecord(ev_topup, side);
+        cudaStreamWaitEvent(st, ev_topup, 0);
     }
     // ---- stream A: coupling rows of the lower levels + dense rows
     ev = dv.begin(st);
@@ -373,42 +397,24 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
         }
     }
     dv.end(1, ev, st, dv.n_chunks_bottom > 0 ? 1 : 0);
-    // ---- stream B: the levels above the bottom subtrees
+    // ---- stream B, part 2: coupling rows of the upper levels, their downsweep
     if (top) {
         cudaStream_t sb = side;
-        cudaEvent_t eb = dv.begin(sb);
-        int launches = 0;
-        for (int lin = Lb; lin > 0;) {
-            const int L = std::min(Ltop, lin), lr = lin - L;
-            const int64_t ns = int64_t(1) << lr;
-            k_up_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, sb>>>(
-                o, v, p_tsub, lr, L, ns, 0);
-            ++launches;
-            lin = lr;
-        }
+        if (!mf) top_up();
         if (dv.n_chunks_top > 0) {
-            bool done = false;
-            if constexpr (sizeof(T) == 4 && NVMAX <= kChunk) {
-                if (mf) {
-                    launch_mf<NVMAX>(op, o, v, dv.mfa, p_top, sm_top, unsigned(dv.grid_top), dv.desc_top,
-                                     dv.chunks_top, dv.n_chunks_top, 1, sb);
-                    done = true;
-                }
-            }
-            if (!done)
-                k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
-                                                                          dv.n_chunks_top, 1);
-            ++launches;
+            k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
+                                                                      dv.n_chunks_top, 1);
+            ++top_launches;
         }
         for (int lr = 0; lr <= Lb - 1;) {
             const int L = std::min(Ltop, Lb - 1 - lr);
             const int64_t ns = int64_t(1) << lr;
             k_down_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, sb>>>(
                 o, v, p_tsub, lr, L, ns, 0);
-            ++launches;
+            ++top_launches;
             lr += L + 1;
         }
-        dv.end(2, eb, sb, launches);
+        dv.end(2, eb, sb, top_launches);
         cudaEventRecord(ev_top, sb);
         cudaStreamWaitEvent(st, ev_top, 0);
     }
@@ -678,10 +684,10 @@ int launch_product(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, dou
 template <typename T>
 int generate_blocks(const h2_op &op, h2_device &dv, const int32_t *d_cpl_row, const int32_t *d_dns_row,
                     const int32_t *d_dns_col, const int64_t *d_dns_off, const int32_t *d_cpl_col,
-                    const double *d_cheb, const double *d_pts_tree, size_t d_region, cudaStream_t st)
+                    const double *d_cheb, const double *d_pts_tree, size_t d_region, cudaStream_t st,
+                    int64_t ncpl, int64_t ndns)
 {
     h2k::KernelFn f{int(op.ker.kind), op.ker.a, op.ker.b, op.ker.deg};
-    const int64_t ncpl = int64_t(op.cpl_col.size()), ndns = int64_t(op.dns_col.size());
     if (ncpl > 0)
         h2k::gen_coupling<T><<<unsigned(std::min<int64_t>(ncpl, 1 << 20)), 256, 0, st>>>(
             reinterpret_cast<T *>(dv.vals), d_cpl_row, d_cpl_col, ncpl, d_cheb, op.dim, op.p, op.k, dv.kx, f);
@@ -1161,13 +1167,15 @@ int h2_exec_create(h2_exec *ex)
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     cudaStream_t side = nullptr;
-    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
     int rc = cuda_status(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi_prio));
     if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
     if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    if (rc == H2_OK) rc = cuda_status(cudaEventCreateWithFlags(&c, cudaEventDisableTiming));
     ex->side = side;
     ex->ev_up = a;
     ex->ev_top = b;
+    ex->ev_topup = c;
     if (rc != H2_OK) h2_exec_destroy(ex);
     return rc;
 }
@@ -1177,6 +1185,7 @@ void h2_exec_destroy(h2_exec *ex)
     if (!ex) return;
     if (ex->ev_up) cudaEventDestroy(static_cast<cudaEvent_t>(ex->ev_up));
     if (ex->ev_top) cudaEventDestroy(static_cast<cudaEvent_t>(ex->ev_top));
+    if (ex->ev_topup) cudaEventDestroy(static_cast<cudaEvent_t>(ex->ev_topup));
     if (ex->side) cudaStreamDestroy(static_cast<cudaStream_t>(ex->side));
     *ex = h2_exec{};
 }
@@ -1193,6 +1202,7 @@ int h2_matvec_exec(h2_handle h, const void *X, void *Y, int nv, double alpha, do
     own.side = dv.side;
     own.ev_up = dv.ev_up;
     own.ev_top = dv.ev_top;
+    own.ev_topup = dv.ev_topup;
     const h2_exec &ex = exp ? *exp : own;
     Workspace w;
     ws_layout(*h, dv, nv, &w, workspace);
@@ -1266,8 +1276,12 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
             dns_off[b + 1] = dns_off[b] + (cnt + 31) / 32 * 32;  // 128-byte aligned blocks
         }
     const size_t tcb = h2s::kTcTileBytes;  // split-BF16 tile of one block
-    // stored entries (none for the matrix-free precision, which keeps coordinates instead)
-    const size_t s_bytes = dv->mf ? 0 : dv->tc ? size_t(ncpl) * tcb : align_up(size_t(ncpl) * dv->kkp * es);
+    // stored entries; the matrix-free precision keeps coordinates instead, and stores only the
+    // coupling blocks of the levels above the bottom subtrees (a prefix of the level-ordered
+    // CSR), which its side stream streams like the stored path
+    const int64_t ncpl_top = op.cpl_rowptr[std::min<int64_t>(int64_t(1) << dv->Lb, op.nnodes + 1)];
+    const size_t s_bytes = dv->mf ? align_up(size_t(ncpl_top) * dv->kkp * es)
+                           : dv->tc ? size_t(ncpl) * tcb : align_up(size_t(ncpl) * dv->kkp * es);
     const size_t d_bytes = dv->mf ? 0 : dv->tc ? size_t(ndns) * tcb : align_up(size_t(dns_off[ndns]) * es);
 
     // ---- stream descriptors: coupling rows of levels >= Lb and all dense rows (bottom),
@@ -1384,6 +1398,9 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
         dv->mfa.node_pts = reinterpret_cast<const float4 *>(arena + o_npts);
         dv->mfa.leaf_pts = reinterpret_cast<const float4 *>(arena + o_lpts);
         dv->mfa.k = k;
+        dv->mfa.p = op.p;
+        dv->mfa.dim = op.dim;
+        dv->mfa.lp = (op.p & (op.p - 1)) == 0 ? __builtin_ctz(unsigned(op.p)) : -1;
         dv->mfa.a = float(op.ker.a);
         dv->mfa.neg_inv_a = op.ker.a != 0.0 ? float(-1.0 / op.ker.a) : 0.f;
         dv->mfa.neg_b = float(-op.ker.b);
@@ -1455,8 +1472,13 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     if (rc == H2_OK)
         rc = dv->mf ? generate_mf_points(op, *dv, d_cheb, d_pts, st)
              : dv->tc ? generate_tc_blocks(op, *dv, d_crow, d_drow, d_dcol, d_ccol, d_cheb, d_pts, s_bytes, st)
-             : es == 8 ? generate_blocks<double>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st)
-                       : generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st);
+             : es == 8 ? generate_blocks<double>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st,
+                                                 ncpl, ndns)
+                       : generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st,
+                                                ncpl, ndns);
+    if (rc == H2_OK && dv->mf && ncpl_top > 0)
+        rc = generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st,
+                                    ncpl_top, 0);
     if (rc == H2_OK) rc = cuda_status(cudaStreamSynchronize(st));
     cudaFree(tmp);
     if (rc == H2_OK) {
@@ -1467,6 +1489,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
         dv->side = static_cast<cudaStream_t>(ex.side);
         dv->ev_up = static_cast<cudaEvent_t>(ex.ev_up);
         dv->ev_top = static_cast<cudaEvent_t>(ex.ev_top);
+        dv->ev_topup = static_cast<cudaEvent_t>(ex.ev_topup);
     }
     if (rc != H2_OK) h2_device_free(&op);
     return rc;

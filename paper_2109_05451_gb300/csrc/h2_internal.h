@@ -48,6 +48,7 @@ struct h2_exec {
     void *side = nullptr;
     void *ev_up = nullptr;
     void *ev_top = nullptr;
+    void *ev_topup = nullptr;  // the side stream's upsweep is done (matrix-free schedule)
 };
 
 // h2_device.cu

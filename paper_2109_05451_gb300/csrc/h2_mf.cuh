@@ -22,6 +22,8 @@ struct MfArgs {
     const float4 *node_pts;  // [node][k]: Chebyshev points of every cluster (x, y, z, 0)
     const float4 *leaf_pts;  // [leaf][mp]: the points of every leaf in tree order
     int k;
+    int p, lp;               // points per dimension of the Chebyshev grids, log2(p) (or -1)
+    int dim;                 // coordinates per point
     float a, neg_inv_a, neg_b;  // kernel parameters: a, -1/a, -b
     int deg;
 };
@@ -55,6 +57,24 @@ __device__ __forceinline__ float mf_kernel(const float (&x)[3], const float4 &y,
         }
     }
 }
+
+// One-dimensional factor of a separable kernel: kappa(x, y) = prod_d f(x_d, y_d) for the
+// Gaussian (f = exp(-(x_d - y_d)^2 / a)) and the product kernel (f = (1 + x_d y_d)^deg).
+template <int KIND>
+__device__ __forceinline__ float mf_factor(float x, float y, const MfArgs &a)
+{
+    if constexpr (KIND == H2_K_GAUSS) {
+        const float d = x - y;
+        return __expf(d * d * a.neg_inv_a);
+    } else {
+        const float g = 1.f + x * y;
+        float v = 1.f;
+        for (int e = 0; e < a.deg; ++e) v *= g;
+        return v;
+    }
+}
+
+__device__ __forceinline__ float coord(const float4 &p, int d) { return d == 0 ? p.x : (d == 1 ? p.y : p.z); }
 
 // Shared-memory bytes of one stage's vector region: input segment, column coordinates, row
 // coordinates.
@@ -156,6 +176,18 @@ __global__ void __launch_bounds__(kThreads, 4)
     const int tid = threadIdx.x;
     Acc<float, NVMAX> acc;
     float tc[4][3];  // row coordinates of this thread's four outputs
+    // Separable kernels on Chebyshev tensor grids: a coupling block is the Kronecker product
+    // S = F_{dim-1} x ... x F_0 of p x p factor tables, F_d[a][b] = f(xi^t_{d,a}, xi^s_{d,b}),
+    // so a block needs dim p^2 evaluations instead of k^2. With 4 | p a thread's four outputs
+    // share their higher digits, and with p | G (G column groups) all of a thread's columns
+    // share their digit 0: entry (nu, mu) = A_e B(mu) with A_e = F_0[nu_0(e)][mu_0] fixed
+    // per block and B(mu) = prod_{d>=1} F_d[nu_d][mu_d].
+    constexpr bool kSeparable = KIND == H2_K_GAUSS || KIND == H2_K_POLY;
+    __shared__ float row1d[3][8];   // the row cluster's grid coordinates per dimension
+    __shared__ float fac[2][3][64]; // factor tables, double-buffered by block parity
+    int fbuf = 0;
+    bool sep_row = false;
+    int nu0[4] = {0, 0, 0, 0}, nuhi[3] = {0, 0, 0};
     bool fresh = true;
     for (;;) {
         if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
@@ -169,6 +201,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         if (fresh) {
             acc.setup(d.rows, d.ld, tid);  // ld is a multiple of 4: four outputs per lane
             acc.zero();
+            sep_row = false;
             if (!(d.flags & kZero)) {
                 const float4 *rc = reinterpret_cast<const float4 *>(xs + seg + cb);
 #pragma unroll
@@ -178,21 +211,69 @@ __global__ void __launch_bounds__(kThreads, 4)
                     tc[e][1] = p.y;
                     tc[e][2] = p.z;
                 }
+                if constexpr (kSeparable) {
+                    const int P = ma.p;
+                    sep_row = !dense && ma.dim == DIM && ma.lp >= 2 && (acc.G % P) == 0 && P <= 8;
+                    if (sep_row) {
+                        if (tid < (DIM << ma.lp)) {
+                            const int dd = tid >> ma.lp, aa = tid & (P - 1);
+                            row1d[dd][aa] = coord(rc[aa << (ma.lp * dd)], dd);
+                        }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) nu0[e] = (acc.o0 + e) & (P - 1);
+#pragma unroll
+                        for (int dd = 1; dd < 3; ++dd) nuhi[dd] = (acc.o0 >> (ma.lp * dd)) & (P - 1);
+                        h2p::consumer_sync(kConsumers);
+                    }
+                }
             }
             fresh = false;
         }
-        if (!(d.flags & kZero) && acc.o0 < d.rows) {
+        if (!(d.flags & kZero)) {
+            bool done = false;
+            if constexpr (kSeparable) {
+                if (sep_row) {
+                    const int P = ma.p, lp = ma.lp;
+                    for (int e = tid; e < (DIM << (2 * lp)); e += kConsumers) {  // P is a power of two here
+                        const int dd = e >> (2 * lp), aa = (e >> lp) & (P - 1), bb = e & (P - 1);
+                        fac[fbuf][dd][(aa << lp) + bb] = mf_factor<KIND>(row1d[dd][aa], coord(cc[bb << (lp * dd)], dd), ma);
+                    }
+                    h2p::consumer_sync(kConsumers);
+                    if (acc.o0 < d.rows) {
+                        const int mu0 = acc.g & (P - 1);
+                        float A[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) A[e] = fac[fbuf][0][(nu0[e] << lp) + mu0];
 #pragma unroll 2
-            for (int j = acc.g; j < d.cols; j += acc.G) {
-                const float4 c = cc[j];
-                float xj[NVMAX];
+                        for (int j = acc.g; j < d.cols; j += acc.G) {
+                            float B = fac[fbuf][1][(nuhi[1] << lp) + ((j >> lp) & (P - 1))];
+                            if constexpr (DIM == 3) B *= fac[fbuf][2][(nuhi[2] << lp) + ((j >> (2 * lp)) & (P - 1))];
 #pragma unroll
-                for (int v = 0; v < NVMAX; ++v) xj[v] = v < nv ? xv[v * xld + j] : 0.f;
+                            for (int v = 0; v < NVMAX; ++v) {
+                                if (v >= nv) break;
+                                const float t = B * xv[v * xld + j];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float kv = mf_kernel<KIND, DIM>(tc[e], c, ma);
+                                for (int e = 0; e < 4; ++e) acc.a[v][e] += A[e] * t;
+                            }
+                        }
+                    }
+                    fbuf ^= 1;
+                    done = true;
+                }
+            }
+            if (!done && acc.o0 < d.rows) {
+#pragma unroll 2
+                for (int j = acc.g; j < d.cols; j += acc.G) {
+                    const float4 c = cc[j];
+                    float xj[NVMAX];
 #pragma unroll
-                    for (int v = 0; v < NVMAX; ++v) acc.a[v][e] += kv * xj[v];
+                    for (int v = 0; v < NVMAX; ++v) xj[v] = v < nv ? xv[v * xld + j] : 0.f;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float kv = mf_kernel<KIND, DIM>(tc[e], c, ma);
+#pragma unroll
+                        for (int v = 0; v < NVMAX; ++v) acc.a[v][e] += kv * xj[v];
+                    }
                 }
             }
         }
