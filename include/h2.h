@@ -57,6 +57,7 @@ typedef enum {
     H2_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
     H2_ETIMEOUT = -4, /* a bounded device-side wait ran out */
     H2_ESTATE = -5,   /* call not valid in the handle's state (e.g. no device copy) */
+    H2_ECANCELED = -6, /* a served request was cancelled before it finished */
     H2_ENOTCONV = 1   /* iterative solve stopped at maxit without reaching tol */
 } h2_status;
 
@@ -285,8 +286,20 @@ int h2_server_submit(h2_server_t s, h2_handle op, double sigma2, const double *b
 int h2_server_poll(h2_server_t s, h2_request_result *results, int max_results, int *n_results);
 /* Block until no request is queued or in flight; H2_ETIMEOUT after timeout_s seconds. */
 int h2_server_wait(h2_server_t s, double timeout_s);
+/* Cancel a request: a queued one completes at once with status H2_ECANCELED (x untouched);
+ * one in flight stops after the iterations already enqueued, and completes with status
+ * H2_ECANCELED, its current iterate in x and that iterate's true residual. H2_EINVAL if the
+ * id is unknown or its result is already available. */
+int h2_server_cancel(h2_server_t s, int64_t request_id);
 /* Drop queued requests, let the ones in flight finish, stop the scheduler, free all. */
 int h2_server_destroy(h2_server_t s);
+
+/* Self-test of the bounded device waits (no paper counterpart): launches one thread that
+ * waits on a shared-memory barrier nothing arrives on, with a budget of budget_cycles clock
+ * cycles; the wait gives up, records the failure in a device flag and returns, so the call
+ * returns H2_ETIMEOUT and the CUDA context stays usable. The kernels' own waits use the same
+ * mechanism with a budget of about one second. */
+int h2_selftest_wait_timeout(int64_t budget_cycles);
 
 /* Static description of a status code. */
 const char *h2_status_str(int status);

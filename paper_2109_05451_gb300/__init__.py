@@ -19,6 +19,7 @@ import numpy as np
 from . import build as _build
 
 H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ETIMEOUT, H2_ESTATE, H2_ENOTCONV = 0, -1, -2, -3, -4, -5, 1
+H2_ECANCELED = -6
 H2_FP64, H2_FP32, H2_BF16X2, H2_FP32_MF = 0, 1, 2, 3
 H2_K_EXP, H2_K_GAUSS, H2_K_IMQ, H2_K_POLY = 0, 1, 2, 3
 H2_MAX_LEVELS = 32
@@ -82,7 +83,9 @@ SIGNATURES = {
     "h2_server_submit": (_I, [_P, _P, _D, _P, _P, _D, _I, C.POINTER(_I64)]),
     "h2_server_poll": (_I, [_P, C.POINTER(h2_request_result), _I, C.POINTER(_I)]),
     "h2_server_wait": (_I, [_P, _D]),
+    "h2_server_cancel": (_I, [_P, _I64]),
     "h2_server_destroy": (_I, [_P]),
+    "h2_selftest_wait_timeout": (_I, [_I64]),
 }
 
 _lib = None
@@ -348,6 +351,10 @@ class H2Server:
             out.append({"id": r.request_id, "status": r.status, "iters": r.iters, "true_relres": r.true_relres,
                         "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done, "x": x})
         return out
+
+    def cancel(self, request_id: int) -> int:
+        """Cancel a queued or running request; its result (status H2_ECANCELED) is still polled."""
+        return int(load().h2_server_cancel(self.handle, int(request_id)))
 
     def wait(self, timeout_s: float = 600.0) -> int:
         rc = load().h2_server_wait(self.handle, float(timeout_s))

@@ -1666,6 +1666,7 @@ const char *h2_status_str(int status)
     case H2_ECUDA: return "CUDA error";
     case H2_ETIMEOUT: return "device wait timed out";
     case H2_ESTATE: return "invalid handle state";
+    case H2_ECANCELED: return "cancelled";
     case H2_ENOTCONV: return "not converged";
     default: return "unknown status";
     }

@@ -138,6 +138,7 @@ struct Request {
 
 struct Slot {
     bool busy = false, finishing = false;
+    bool cancel = false;  // stop after the iterations already enqueued
     Request req;
     double t_admit = 0;
     int enq = 0, done = 0;
@@ -177,6 +178,8 @@ struct h2_server {
     std::condition_variable cv;
     std::deque<Request> queue;
     std::vector<h2_request_result> results;
+    std::vector<int64_t> inflight;  // ids admitted and not yet completed
+    std::vector<int64_t> cancels;   // cancel requests for ids in flight
     int64_t next_id = 1;
     int64_t outstanding = 0;  // queued + in flight
     std::atomic<bool> stop{false};
@@ -208,6 +211,7 @@ struct h2_server {
     {
         s.busy = true;
         s.finishing = false;
+        s.cancel = false;
         s.req = q;
         s.enq = s.done = 0;
         s.t_admit = now();
@@ -290,7 +294,7 @@ struct h2_server {
         r.iters = rc == H2_OK ? h.iters : 0;
         const double bb = h.scal[3];
         r.true_relres = (rc == H2_OK && bb > 0.0) ? std::sqrt(h.scal[4] / bb) : 0.0;
-        r.status = rc != H2_OK ? rc : (h.flag == 1 ? H2_OK : H2_ENOTCONV);
+        r.status = rc != H2_OK ? rc : s.cancel ? H2_ECANCELED : (h.flag == 1 ? H2_OK : H2_ENOTCONV);
         if (rc == H2_OK) std::memcpy(s.req.x, s.stage, size_t(s.req.n) * 8);
         r.t_submit = s.req.t_submit;
         r.t_admit = s.t_admit;
@@ -301,6 +305,7 @@ struct h2_server {
         s.mem = nullptr;
         std::lock_guard<std::mutex> lk(mu);
         results.push_back(r);
+        inflight.erase(std::remove(inflight.begin(), inflight.end(), r.request_id), inflight.end());
         --outstanding;
         cv.notify_all();
     }
@@ -323,6 +328,7 @@ struct h2_server {
                 if (!mem) break;
                 const Request q = queue.front();
                 queue.pop_front();
+                inflight.push_back(q.id);
                 lk.unlock();
                 const int rc = admit(*free_slot, q, mem);
                 if (rc != H2_OK) complete(*free_slot, rc);
@@ -330,6 +336,15 @@ struct h2_server {
                 lk.lock();
             }
         }
+        std::vector<int64_t> cancel_now;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            cancel_now.swap(cancels);
+        }
+        for (Slot &s : slots)
+            if (s.busy && !s.finishing &&
+                std::find(cancel_now.begin(), cancel_now.end(), s.req.id) != cancel_now.end())
+                s.cancel = true;
         for (Slot &s : slots) {
             if (!s.busy) continue;
             if (s.finishing) {
@@ -356,6 +371,14 @@ struct h2_server {
                 }
             }
             if (!s.busy || s.finishing) continue;
+            if (s.cancel) {  // no new iterations; finish once the enqueued ones are done
+                if (s.done == s.enq) {
+                    const int rc = finish(s);
+                    if (rc != H2_OK) complete(s, rc);
+                    moved = true;
+                }
+                continue;
+            }
             while (s.enq - s.done < kAhead && s.enq < s.req.maxit) {
                 const int rc = enqueue_iteration(s);
                 moved = true;
@@ -471,6 +494,28 @@ int h2_server_wait(h2_server_t s, double timeout_s)
     std::unique_lock<std::mutex> lk(s->mu);
     const bool ok = s->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), [s] { return s->outstanding == 0; });
     return ok ? H2_OK : H2_ETIMEOUT;
+}
+
+int h2_server_cancel(h2_server_t s, int64_t request_id)
+{
+    if (!s) return H2_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if (it->id != request_id) continue;
+        h2_request_result r{};
+        r.request_id = request_id;
+        r.status = H2_ECANCELED;
+        r.t_submit = it->t_submit;
+        r.t_done = s->now();
+        s->queue.erase(it);
+        s->results.push_back(r);
+        --s->outstanding;
+        s->cv.notify_all();
+        return H2_OK;
+    }
+    if (std::find(s->inflight.begin(), s->inflight.end(), request_id) == s->inflight.end()) return H2_EINVAL;
+    s->cancels.push_back(request_id);
+    return H2_OK;
 }
 
 int h2_server_destroy(h2_server_t s)

@@ -143,3 +143,11 @@ def test_server_calls_reject_bad_arguments_before_cuda():
         assert lib.h2_server_request_bytes(h) == 0  # not uploaded
     finally:
         h2.h2_destroy(h)
+
+
+def test_cancel_and_selftest_reject_bad_arguments_before_cuda():
+    lib = h2.load()
+    assert lib.h2_server_cancel(None, 1) == h2.H2_EINVAL
+    assert lib.h2_selftest_wait_timeout(0) == h2.H2_EINVAL
+    assert lib.h2_selftest_wait_timeout(10 ** 12) == h2.H2_EINVAL
+    assert h2.h2_status_str(h2.H2_ECANCELED) == "cancelled"
