@@ -364,7 +364,7 @@ def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, 
     return out
 
 
-def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18):
+def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with_fp64=True):
     """Batched products of 64 uneven operators (synthetic_inputs.uneven_batch: N log-uniform
     in [2^12, 2^18], even members 2D grids with orders 4-8, odd members 3D clouds with orders
     3-4, exp(-r/l) with l in [0.05, 0.3], leaf 64, eta 0.7, nv in 1..16), FP32, as one
@@ -403,9 +403,28 @@ def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18):
 
         ms_batch = timed(batch.run)
         batch.check()
+        batch.run()
+        torch.cuda.synchronize()
+        y32 = [Y.double().cpu().numpy() for Y in Ys]
         ms_seq = timed(lambda: [op.matvec(X, Y) for op, X, Y in zip(ops, Xs, Ys)])
         batch.close()
         mb, msq = float(np.median(ms_batch)), float(np.median(ms_seq))
+        # the same batch with FP64 members: plain FP64 time and the FP32 results' error against it
+        fp64 = None
+        if with_fp64:
+            for op in ops:
+                op.upload("fp64")
+            X64 = [X.double() for X in Xs]
+            Y64 = [op.new_vectors(Y.shape[1] if Y.dim() > 1 else 1, fill=0.0) for op, Y in zip(ops, Ys)]
+            b64 = h2.H2Batch(ops, X64, Y64)
+            ms64 = float(np.median(timed(b64.run)))
+            b64.run()
+            torch.cuda.synchronize()
+            num = sum(float(np.sum((a - Y.cpu().numpy()) ** 2)) for a, Y in zip(y32, Y64))
+            den = sum(float(np.sum(Y.cpu().numpy() ** 2)) for Y in Y64)
+            b64.close()
+            fp64 = {"batched_ms": ms64, "batched_GB/s": 2 * total_bytes / (ms64 * 1e-3) / 1e9,
+                    "fp32_speedup": ms64 / mb, "fp32_relerr_vs_fp64": float(np.sqrt(num / den))}
         return {"workload": f"uneven_batch: {count} operators, N log-uniform [2^12, {n_max}], 2D grids / 3D "
                             "clouds, exp(-r/l), rank 16-64, nv 1-16, FP32",
                 "points": int(sum(len(m.points) for m in members)), "vectors": int(sum(m.nv for m in members)),
@@ -414,7 +433,7 @@ def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18):
                 "batched_gflops": total_flops / (mb * 1e-3) / 1e9,
                 "sequential_ms": msq, "sequential_GB/s": total_bytes / (msq * 1e-3) / 1e9,
                 "speedup_vs_sequential": msq / mb, "create_s": create_s, "configuration": desc,
-                "l2": "inputs larger than L2, no flush"}
+                "fp64": fp64, "l2": "inputs larger than L2, no flush"}
     finally:
         for op in ops:
             op.close()
@@ -615,7 +634,8 @@ def main():
             line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batch:
         try:
-            line["batch"] = batch_benchmark(h2, torch, count=args.batch_count, n_max=args.batch_nmax)
+            line["batch"] = batch_benchmark(h2, torch, count=args.batch_count, n_max=args.batch_nmax,
+                                            with_fp64=not args.no_fp64)
         except Exception as exc:  # reported, never silently dropped
             line["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_serve:

@@ -62,6 +62,7 @@ using Clock = std::chrono::steady_clock;
 constexpr int kRing = 4;      // iteration snapshots per slot (> kAhead)
 constexpr int kAhead = 2;     // iterations enqueued ahead of the host's look at their state
 constexpr size_t kAl = 256;   // alignment of every region of slot memory
+constexpr int kGraphMinIters = 8;  // requests allowing fewer iterations are launched eagerly
 
 size_t al(size_t b) { return (b + kAl - 1) / kAl * kAl; }
 
@@ -146,6 +147,7 @@ struct Slot {
     h2_exec ex;
     cudaEvent_t ev[kRing] = {};
     cudaEvent_t ev_fin = nullptr;
+    cudaGraphExec_t iter = nullptr;  // the captured iteration of the admitted request
     Head *ring = nullptr;     // pinned, kRing + 1 (the last: after the true residual)
     double *stage = nullptr;  // pinned, max_points doubles (b in, x out)
     // device regions, carved from the arena per request
@@ -252,7 +254,8 @@ struct h2_server {
         return rc;
     }
 
-    int enqueue_iteration(Slot &s)
+    // One CG iteration's device work (product, inner products, updates, stopping test).
+    int iteration_body(Slot &s)
     {
         const Request &q = s.req;
         const int64_t n = q.n;
@@ -265,6 +268,37 @@ struct h2_server {
         k_check<<<1, 1, 0, s.st>>>(scal, &s.head->flag, &s.head->iters, q.tol);
         k_update_p_if<<<grid_for(n), kThreads, 0, s.st>>>(s.p, s.r, scal, &s.head->flag, n);
         k_roll_if<<<1, 1, 0, s.st>>>(scal, &s.head->flag);
+        return status_of(cudaGetLastError());
+    }
+
+    // The iteration as a CUDA graph (its arguments are fixed for the request), captured after
+    // one eager iteration has set up every kernel it launches; replaying it replaces about two
+    // dozen launches per iteration. Without a graph the iteration is launched eagerly.
+    void capture_iteration(Slot &s)
+    {
+        if (s.iter || s.req.maxit < kGraphMinIters) return;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        const int rc = iteration_body(s);
+        const cudaError_t e = cudaStreamEndCapture(s.st, &g);
+        if (rc == H2_OK && e == cudaSuccess && g && cudaGraphInstantiate(&s.iter, g, 0) != cudaSuccess) s.iter = nullptr;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
+
+    int enqueue_iteration(Slot &s)
+    {
+        int rc;
+        if (s.iter) {
+            rc = status_of(cudaGraphLaunch(s.iter, s.st));
+        } else {
+            rc = iteration_body(s);
+            if (rc == H2_OK && s.enq == 0) capture_iteration(s);
+        }
+        if (rc != H2_OK) return rc;
         const int i = s.enq % kRing;
         cudaMemcpyAsync(&s.ring[i], s.head, sizeof(Head), cudaMemcpyDeviceToHost, s.st);
         cudaEventRecord(s.ev[i], s.st);
@@ -300,6 +334,10 @@ struct h2_server {
         r.t_admit = s.t_admit;
         r.t_done = now();
         if (rc != H2_OK) cudaStreamSynchronize(s.st);  // nothing of this request may still run
+        if (s.iter) {
+            cudaGraphExecDestroy(s.iter);
+            s.iter = nullptr;
+        }
         arena.release(s.mem, s.req.bytes);
         s.busy = false;
         s.mem = nullptr;
