@@ -212,6 +212,13 @@ int h2_get_bases(h2_handle h, double *U, double *E);
 int h2_set_timing(h2_handle h, int enable);
 int h2_get_timing(h2_handle h, double *phase_ms, int64_t *phase_launches, int64_t *products);
 
+/* Checkpoint of the host operator (no paper counterpart): h2_save writes the construction
+ * (parameters, points, tree, partition, bases and transfers; not the device copy) to a binary
+ * file; h2_load reads such a file into a new handle, ready for h2_upload, without rebuilding.
+ * H2_EINVAL if the file cannot be written or read, or is not a consistent operator file. */
+int h2_save(h2_handle h, const char *path);
+int h2_load(const char *path, h2_handle *out);
+
 /* Free the host operator, its device copy and its workspace. NULL is accepted. */
 int h2_destroy(h2_handle h);
 

@@ -78,6 +78,8 @@ SIGNATURES = {
     "h2_batch_check": (_I, [_P]),
     "h2_batch_describe": (_I, [_P, C.c_char_p, _SZ]),
     "h2_batch_destroy": (_I, [_P]),
+    "h2_save": (_I, [_P, C.c_char_p]),
+    "h2_load": (_I, [C.c_char_p, C.POINTER(_P)]),
     "h2_server_create": (_I, [_SZ, _I, _I64, C.POINTER(_P)]),
     "h2_server_request_bytes": (_SZ, [_P]),
     "h2_server_submit": (_I, [_P, _P, _D, _P, _P, _D, _I, C.POINTER(_I64)]),
@@ -190,6 +192,16 @@ def h2_cg_solve(h: int, sigma2: float, b, x, tol: float, maxit: int, stream=None
     return rc, it.value, rr.value
 
 
+def h2_save(h: int, path: str):
+    _check(load().h2_save(h, os.fsencode(path)), "h2_save")
+
+
+def h2_load(path: str) -> int:
+    h = C.c_void_p()
+    _check(load().h2_load(os.fsencode(path), C.byref(h)), "h2_load")
+    return h.value
+
+
 def h2_get_info(h: int) -> h2_info:
     info = h2_info()
     _check(load().h2_get_info(h, C.byref(info)), "h2_get_info")
@@ -255,11 +267,19 @@ class H2Operator:
     """Owns one handle. ``matvec`` takes torch tensors of shape (n, nv) in column-major
     (Fortran) layout or (n,) vectors; the dtype must match the uploaded precision."""
 
-    def __init__(self, points, kernel, leaf_size: int, cheb_order: int, eta: float):
-        self.handle = h2_build(points, kernel, leaf_size, cheb_order, eta)
+    def __init__(self, points, kernel, leaf_size: int, cheb_order: int, eta: float, *, _handle=None):
+        self.handle = _handle if _handle is not None else h2_build(points, kernel, leaf_size, cheb_order, eta)
         self.info = h2_get_info(self.handle)
         self.n = int(self.info.n)
         self.prec = None
+
+    @classmethod
+    def load(cls, path: str) -> "H2Operator":
+        """An operator read from a file written by ``save`` (not uploaded)."""
+        return cls(None, None, 0, 0, 0.0, _handle=h2_load(path))
+
+    def save(self, path: str) -> None:
+        h2_save(self.handle, path)
 
     def upload(self, prec="fp32", stream=None):
         h2_upload(self.handle, prec, stream)

@@ -14,6 +14,7 @@
 
 #include "h2_cgk.cuh"
 #include "h2_internal.h"
+#include "h2_nvtx.h"
 
 namespace {
 
@@ -60,6 +61,7 @@ double read_scalar(const CgState &c, int idx, int *rc)
 extern "C" int h2_cg_solve(h2_handle h, double sigma2, const double *b, double *x, double tol, int maxit,
                            int *iters, double *true_relres, void *cuda_stream)
 {
+    h2n::Range range("h2_cg_solve");
     if (iters) *iters = 0;
     if (true_relres) *true_relres = 0.0;
     if (!h || !b || !x || maxit < 0 || !(tol >= 0) || !(sigma2 >= 0)) return H2_EINVAL;

@@ -28,6 +28,7 @@
 #include "h2_tcstream.cuh"
 #include "h2_batch.cuh"
 #include "h2_mf.cuh"
+#include "h2_nvtx.h"
 
 #include <dlfcn.h>
 
@@ -349,8 +350,11 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
 
     // ---- stream A: gather + bottom upsweep (leaf projections and the lowest Lbot levels)
     cudaEvent_t ev = dv.begin(st);
-    k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
-    k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
+    {
+        h2n::Range r("upsweep: leaf subtrees");
+        k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
+        k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
+    }
     dv.end(0, ev, st, 2);
     const bool top = Lb >= 1;
     cudaEvent_t ev_topup = static_cast<cudaEvent_t>(ex.ev_topup);
@@ -362,6 +366,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     int top_launches = 0;
     // ---- stream B, part 1: upsweep of the levels above the bottom subtrees
     auto top_up = [&]() {
+        h2n::Range r("upsweep: upper levels");
         eb = dv.begin(side);
         for (int lin = Lb; lin > 0;) {
             const int L = std::min(Ltop, lin), lr = lin - L;
@@ -383,6 +388,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     // ---- stream A: coupling rows of the lower levels + dense rows
     ev = dv.begin(st);
     if (dv.n_chunks_bottom > 0) {
+        h2n::Range r("tree multiply + dense: lower levels");
         if constexpr (sizeof(T) == 4 && NVMAX <= kChunk) {
             if (mf) {
                 launch_mf<NVMAX>(op, o, v, dv.mfa, p_bot, sm_bot, grid_bot, dv.desc_bottom, dv.chunks_bottom,
@@ -401,6 +407,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     if (top) {
         cudaStream_t sb = side;
         if (!mf) top_up();
+        h2n::Range r("tree multiply + downsweep: upper levels");
         if (dv.n_chunks_top > 0) {
             k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
                                                                       dv.n_chunks_top, 1);
@@ -420,7 +427,10 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     }
     // ---- stream A: bottom downsweep + leaf expansion + epilogue
     ev = dv.begin(st);
-    k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
+    {
+        h2n::Range r("downsweep: leaf subtrees");
+        k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
+    }
     dv.end(3, ev, st, 1);
     return cuda_status(cudaGetLastError());
 }
@@ -1193,6 +1203,7 @@ void h2_exec_destroy(h2_exec *ex)
 int h2_matvec_exec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *workspace,
                    size_t ws_bytes, void *cuda_stream, const h2_exec *exp)
 {
+    h2n::Range range("h2_matvec");
     if (!h || !X || !Y || nv < 1 || !workspace) return H2_EINVAL;
     if (!h->dev) return H2_ESTATE;
     h2_device &dv = *h->dev;
@@ -1221,6 +1232,7 @@ extern "C" {
 
 int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
 {
+    h2n::Range range("h2_upload");
     if (!h) return H2_EINVAL;
     if (prec != H2_FP64 && prec != H2_FP32 && prec != H2_BF16X2 && prec != H2_FP32_MF) return H2_EINVAL;
     h2_op &op = *h;
@@ -1568,6 +1580,7 @@ int h2_destroy(h2_handle h)
 int h2_build(const double *points, int64_t n, int dim, h2_kernel kernel, int leaf_size, int cheb_order, double eta,
              h2_handle *out)
 {
+    h2n::Range range("h2_build");
     if (!out) return H2_EINVAL;
     *out = nullptr;
     if (leaf_size > kMaxLeaf) return H2_EINVAL;
@@ -1677,6 +1690,7 @@ const char *h2_status_str(int status)
 int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void *const *Y, const int *nv, double alpha,
                     double beta, int flags, h2_batch_t *out)
 {
+    h2n::Range range("h2_batch_create");
     if (!out) return H2_EINVAL;
     *out = nullptr;
     if (!ops || count < 1 || !X || !Y || !nv) return H2_EINVAL;
@@ -1835,6 +1849,7 @@ int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void 
 
 int h2_batch_run(h2_batch_t b, void *cuda_stream)
 {
+    h2n::Range range("h2_batch_run");
     if (!b || !b->exec) return H2_EINVAL;
     return cuda_status(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)));
 }

@@ -13,6 +13,7 @@
 // block-row CSR arrays that the device kernels stream.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <utility>
@@ -261,5 +262,128 @@ int h2_host_build(h2_op *op, const double *points, int64_t n, int dim, h2_kernel
     } catch (const std::bad_alloc &) {
         return H2_ENOMEM;
     }
+    return H2_OK;
+}
+
+// ---------------------------------------------------------------- save / load
+
+namespace {
+
+constexpr char kMagic[8] = {'H', '2', 'G', 'B', '3', '0', '0', 'o'};
+constexpr uint32_t kFormat = 1;
+
+template <typename V>
+bool put_vec(FILE *f, const std::vector<V> &v)
+{
+    const uint64_t n = v.size();
+    return std::fwrite(&n, sizeof(n), 1, f) == 1 && (n == 0 || std::fwrite(v.data(), sizeof(V), n, f) == n);
+}
+
+template <typename V>
+bool get_vec(FILE *f, std::vector<V> &v, uint64_t expect)
+{
+    uint64_t n = 0;
+    if (std::fread(&n, sizeof(n), 1, f) != 1 || n != expect) return false;
+    v.resize(n);
+    return n == 0 || std::fread(v.data(), sizeof(V), n, f) == n;
+}
+
+// Every index a loaded operator hands to the device (permutation, ranges, block columns)
+// stays inside its array, so a damaged file is refused on the host.
+bool consistent(const h2_op &o)
+{
+    const int64_t n = o.n, nn = o.nnodes, first = o.first_leaf(), leaves = o.nleaves();
+    int64_t k = 1;
+    for (int d = 0; d < o.dim; ++d) k *= o.p;
+    if (o.p < 1 || o.k != k || o.m < 1) return false;
+    std::vector<char> seen(size_t(n), 0);
+    for (int64_t v : o.perm) {
+        if (v < 0 || v >= n || seen[size_t(v)]) return false;
+        seen[size_t(v)] = 1;
+    }
+    if (o.lo[1] != 0 || o.hi[1] != n) return false;
+    for (int64_t c = 1; c <= nn; ++c) {
+        if (o.lo[c] < 0 || o.lo[c] > o.hi[c] || o.hi[c] > n) return false;
+        if (c < first && (o.lo[2 * c] != o.lo[c] || o.hi[2 * c] != o.lo[2 * c + 1] || o.hi[2 * c + 1] != o.hi[c]))
+            return false;
+        if (c >= first && o.hi[c] - o.lo[c] > o.m) return false;
+    }
+    auto csr_ok = [](const std::vector<int64_t> &rp, const auto &col, int64_t lo, int64_t hi) {
+        if (rp.front() != 0) return false;
+        for (size_t i = 1; i < rp.size(); ++i)
+            if (rp[i] < rp[i - 1]) return false;
+        for (auto c : col)
+            if (int64_t(c) < lo || int64_t(c) > hi) return false;
+        return true;
+    };
+    return csr_ok(o.cpl_rowptr, o.cpl_col, 1, nn) && csr_ok(o.dns_rowptr, o.dns_col, 0, leaves - 1);
+}
+
+}  // namespace
+
+extern "C" int h2_save(h2_handle h, const char *path)
+{
+    if (!h || !path) return H2_EINVAL;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return H2_EINVAL;
+    const h2_op &o = *h;
+    const int64_t ints[7] = {o.n, o.dim, o.m, o.p, o.k, o.q, o.nnodes};
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&kFormat, sizeof(kFormat), 1, f) == 1 &&
+              std::fwrite(ints, sizeof(ints), 1, f) == 1 && std::fwrite(&o.eta, sizeof(o.eta), 1, f) == 1 &&
+              std::fwrite(&o.ker, sizeof(o.ker), 1, f) == 1;
+    ok = ok && put_vec(f, o.pts) && put_vec(f, o.perm) && put_vec(f, o.lo) && put_vec(f, o.hi) &&
+         put_vec(f, o.bmin) && put_vec(f, o.bmax) && put_vec(f, o.cheb) && put_vec(f, o.U) && put_vec(f, o.E) &&
+         put_vec(f, o.cpl_rowptr) && put_vec(f, o.cpl_col) && put_vec(f, o.dns_rowptr) && put_vec(f, o.dns_col);
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? H2_OK : H2_EINVAL;
+}
+
+extern "C" int h2_load(const char *path, h2_handle *out)
+{
+    if (!out) return H2_EINVAL;
+    *out = nullptr;
+    if (!path) return H2_EINVAL;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return H2_EINVAL;
+    h2_op *o = new (std::nothrow) h2_op;
+    if (!o) {
+        std::fclose(f);
+        return H2_ENOMEM;
+    }
+    char magic[8];
+    uint32_t format = 0;
+    int64_t ints[7];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(&format, sizeof(format), 1, f) == 1 && format == kFormat &&
+              std::fread(ints, sizeof(ints), 1, f) == 1 && std::fread(&o->eta, sizeof(o->eta), 1, f) == 1 &&
+              std::fread(&o->ker, sizeof(o->ker), 1, f) == 1;
+    if (ok) {
+        o->n = ints[0];
+        o->dim = int(ints[1]);
+        o->m = int(ints[2]);
+        o->p = int(ints[3]);
+        o->k = int(ints[4]);
+        o->q = int(ints[5]);
+        o->nnodes = ints[6];
+        ok = o->n >= 1 && o->dim >= 1 && o->dim <= 3 && o->q >= 0 && o->q < 40 && o->nnodes == (int64_t(2) << o->q) - 1;
+    }
+    if (ok) {
+        const uint64_t n = uint64_t(o->n), nodes = uint64_t(o->nnodes + 1), k = uint64_t(o->k);
+        const uint64_t leaves = uint64_t(1) << o->q;
+        ok = get_vec(f, o->pts, n * o->dim) && get_vec(f, o->perm, n) && get_vec(f, o->lo, nodes) &&
+             get_vec(f, o->hi, nodes) && get_vec(f, o->bmin, nodes * o->dim) && get_vec(f, o->bmax, nodes * o->dim) &&
+             get_vec(f, o->cheb, nodes * o->dim * o->p) && get_vec(f, o->U, n * k) && get_vec(f, o->E, nodes * k * k) &&
+             get_vec(f, o->cpl_rowptr, nodes + 1);
+        if (ok) ok = get_vec(f, o->cpl_col, uint64_t(o->cpl_rowptr.back()));
+        if (ok) ok = get_vec(f, o->dns_rowptr, leaves + 1);
+        if (ok) ok = get_vec(f, o->dns_col, uint64_t(o->dns_rowptr.back()));
+    }
+    std::fclose(f);
+    if (ok) ok = consistent(*o);
+    if (!ok) {
+        delete o;
+        return H2_EINVAL;
+    }
+    *out = o;
     return H2_OK;
 }

@@ -31,6 +31,7 @@
 
 #include "h2_cgk.cuh"
 #include "h2_internal.h"
+#include "h2_nvtx.h"
 
 // device side of the server (a named namespace: nvcc's host stubs of kernels whose types
 // live in an unnamed namespace clash with the unnamed namespace of h2_cgk.cuh)
@@ -211,6 +212,7 @@ struct h2_server {
 
     int admit(Slot &s, const Request &q, char *mem)
     {
+        h2n::Range range("h2_server: admit");
         s.busy = true;
         s.finishing = false;
         s.cancel = false;
@@ -291,6 +293,7 @@ struct h2_server {
 
     int enqueue_iteration(Slot &s)
     {
+        h2n::Range range("h2_server: CG iteration");
         int rc;
         if (s.iter) {
             rc = status_of(cudaGraphLaunch(s.iter, s.st));
@@ -309,6 +312,7 @@ struct h2_server {
     // true residual with one more product, then x and the final state to the host
     int finish(Slot &s)
     {
+        h2n::Range range("h2_server: finish");
         s.finishing = true;
         int rc = apply(s, s.x, s.Ap);
         if (rc != H2_OK) return rc;

@@ -234,3 +234,19 @@ def test_cloud3d_multi_rhs_sampled_leaves(cloud3d_medium, prec, tol):
     got = gpu_matvec(op, X, "fp32")
     assert np.all(np.isfinite(got))
     assert relerr(got[rows], ref) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32mf"])
+def test_loaded_operator_gives_the_same_product(built, prec, tmp_path):
+    pts, ker, orc, op = built("cloud3d_k27_ragged")
+    path = str(tmp_path / "op.h2")
+    op.save(path)
+    g = h2.H2Operator.load(path).upload(prec)
+    try:
+        op.upload(prec)
+        X = si.gaussian_vectors(len(pts), 3, 8)
+        Y = gpu_matvec(op, X, prec)
+        assert np.array_equal(gpu_matvec(g, X, prec), Y)
+        assert relerr(Y, orc.matvec(X)) <= TOL[prec]
+    finally:
+        g.close()
