@@ -219,6 +219,47 @@ int h2_get_timing(h2_handle h, double *phase_ms, int64_t *phase_launches, int64_
 int h2_save(h2_handle h, const char *path);
 int h2_load(const char *path, h2_handle *out);
 
+/* ---------------------------------------------------------------- algebraic recompression
+ * Sec. 5 on the current CUDA device, in FP64 (the paper's precision):
+ *   1. orthogonalization of the basis tree: an upsweep of QR factorizations of the leaf bases
+ *      and of each sibling pair's stacked, reweighted transfers; every coupling block is
+ *      re-expressed in the orthogonal bases (S <- R_t S R_s^T);
+ *   2. the new-basis downsweep: for every node the R factor of the stack of Eq. for B_i^q
+ *      (the parent's factor times the transposed transfer, then the transposed blocks of the
+ *      node's block row), folded one block at a time;
+ *   3. the truncation upsweep: SVDs of the reweighted leaf bases and of the stacked
+ *      projected transfers; singular values above cut = tau * ||A_lr||_F are kept (A_lr: the
+ *      low-rank part; ||A_lr||_F^2 = sum over leaves of ||R_t||_F^2); each level keeps the
+ *      largest count over its nodes (one rank per level);
+ *   4. projection of every coupling block on the new bases (S' = T_t S T_s^T).
+ * Dense blocks are unchanged. The result is a new handle holding the compressed operator on
+ * the host in FP64 (bases, transfers and coupling blocks stored at one rank, the largest level
+ * rank, smaller levels zero-padded), ready for h2_upload at H2_FP64 or H2_FP32 (not H2_BF16X2 or
+ * H2_FP32_MF) and for h2_save, or for another h2_compress. The input handle is unchanged and
+ * need not be uploaded. Requires rank <= 64 and leaves of at most 128 points.
+ *   tau: relative tolerance, >= 0 (0 keeps every nonzero singular value).
+ *   out: receives the new handle. info (host, may be NULL): see h2_compress_info.
+ * Synchronises the stream. Errors: H2_EINVAL, H2_ENOMEM, H2_ECUDA. */
+typedef struct {
+    double tau;
+    double norm_lowrank;           /* ||A_lr||_F */
+    double cut;                    /* tau * norm_lowrank */
+    int depth;
+    int rank_in;                   /* rank of the input */
+    int rank_out;                  /* stored rank of the result: max of level_rank, >= 1 */
+    int level_rank[H2_MAX_LEVELS]; /* rank of each level after truncation */
+    double ms[4];                  /* device time of steps 1-4 (CUDA events) */
+    double flops[4];               /* floating-point operations of steps 1-4 */
+    int64_t jacobi_sweeps;         /* one-sided Jacobi sweeps over all SVDs of step 3 */
+    size_t lowrank_bytes_in;       /* FP64 bytes of bases, transfers and coupling blocks */
+    size_t lowrank_bytes_out;      /* the same at the level ranks of the result */
+} h2_compress_info;
+int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle *out, h2_compress_info *info);
+
+/* Rank of each level (host array of depth + 1 ints): the build's uniform rank, or the
+ * level ranks of a compressed operator. */
+int h2_get_level_ranks(h2_handle h, int *ranks);
+
 /* Free the host operator, its device copy and its workspace. NULL is accepted. */
 int h2_destroy(h2_handle h);
 

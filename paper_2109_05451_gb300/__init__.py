@@ -53,6 +53,13 @@ class h2_request_result(C.Structure):
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
 
 
+class h2_compress_info(C.Structure):
+    _fields_ = [("tau", C.c_double), ("norm_lowrank", C.c_double), ("cut", C.c_double), ("depth", C.c_int),
+                ("rank_in", C.c_int), ("rank_out", C.c_int), ("level_rank", C.c_int * H2_MAX_LEVELS),
+                ("ms", C.c_double * 4), ("flops", C.c_double * 4), ("jacobi_sweeps", C.c_int64),
+                ("lowrank_bytes_in", C.c_size_t), ("lowrank_bytes_out", C.c_size_t)]
+
+
 # name -> (restype, argtypes); every symbol declared in include/h2.h
 _P, _I64, _I, _D, _SZ = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_size_t
 SIGNATURES = {
@@ -79,6 +86,8 @@ SIGNATURES = {
     "h2_batch_describe": (_I, [_P, C.c_char_p, _SZ]),
     "h2_batch_destroy": (_I, [_P]),
     "h2_save": (_I, [_P, C.c_char_p]),
+    "h2_compress": (_I, [_P, _D, _P, C.POINTER(_P), C.POINTER(h2_compress_info)]),
+    "h2_get_level_ranks": (_I, [_P, C.POINTER(C.c_int)]),
     "h2_load": (_I, [C.c_char_p, C.POINTER(_P)]),
     "h2_server_create": (_I, [_SZ, _I, _I64, C.POINTER(_P)]),
     "h2_server_request_bytes": (_SZ, [_P]),
@@ -202,6 +211,21 @@ def h2_load(path: str) -> int:
     return h.value
 
 
+def h2_compress(h: int, tau: float, stream=None):
+    """Sec. 5 recompression on the GPU: (new handle, h2_compress_info)."""
+    out = C.c_void_p()
+    info = h2_compress_info()
+    _check(load().h2_compress(h, float(tau), _stream_ptr(stream), C.byref(out), C.byref(info)), "h2_compress")
+    return out.value, info
+
+
+def h2_get_level_ranks(h: int) -> list:
+    depth = h2_get_info(h).depth
+    r = (C.c_int * (depth + 1))()
+    _check(load().h2_get_level_ranks(h, r), "h2_get_level_ranks")
+    return list(r)
+
+
 def h2_get_info(h: int) -> h2_info:
     info = h2_info()
     _check(load().h2_get_info(h, C.byref(info)), "h2_get_info")
@@ -280,6 +304,18 @@ class H2Operator:
 
     def save(self, path: str) -> None:
         h2_save(self.handle, path)
+
+    def compress(self, tau: float, stream=None) -> "H2Operator":
+        """A new operator compressed to relative tolerance tau (Sec. 5, on the GPU, FP64);
+        not uploaded. Its h2_compress_info is kept as ``compress_info``."""
+        hc, info = h2_compress(self.handle, tau, stream)
+        op = H2Operator(None, None, 0, 0, 0.0, _handle=hc)
+        op.compress_info = info
+        return op
+
+    @property
+    def level_ranks(self) -> list:
+        return h2_get_level_ranks(self.handle)
 
     def upload(self, prec="fp32", stream=None):
         h2_upload(self.handle, prec, stream)

@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-I", INCLUDE] + ARCH
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-I", INCLUDE]
 
-CU_SOURCES = ["h2_device.cu", "h2_noalloc.cu", "h2_cg.cu", "h2_serve.cu", "h2_selftest.cu"]
+CU_SOURCES = ["h2_device.cu", "h2_noalloc.cu", "h2_cg.cu", "h2_serve.cu", "h2_selftest.cu", "h2_compress.cu"]
 CPP_SOURCES = ["h2_host.cpp"]
 
 

@@ -1,0 +1,656 @@
+// h2_cmpk.cuh -- FP64 kernels of the algebraic recompression (Sec. 5).
+//
+// One CTA of 256 threads per node or per coupling block; every matrix of a step sits in
+// shared memory (row-major, leading dimension k + 1). The building blocks:
+//   * Householder QR (reflectors below the diagonal, R above) and the explicit Q by backward
+//     accumulation of the reflectors (Golub & Van Loan, Alg. 5.1.1 / 5.2.1);
+//   * the QR update of an upper-triangular R by a dense k x k block, R <- R-factor of
+//     [R; B]: the new-basis downsweep folds the stack of Eq. for B_i^q into R one block at a
+//     time, so a stack of any length needs k x k of memory;
+//   * one-sided (Hestenes) Jacobi SVD with round-robin pair ordering, 8 threads per pair;
+//   * small products with triangular or rectangular factors.
+// The rank of every level is decided on the device (atomicMax of the per-node counts), read
+// by the next kernel, and never sent to the host until the end.
+#pragma once
+
+#include <cstdint>
+
+namespace h2c {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxK = 64;      // rank of the operator being compressed
+constexpr int kMaxRows = 128;  // points of a leaf; rows of a sibling pair's stack (2k)
+constexpr int kMaxSweeps = 40;
+constexpr double kJacobiTol = 1e-14;  // rotate while |a_p . a_q| > tol * |a_p| |a_q|
+
+// Shared-memory bytes of each kernel (ld = k + 1 doubles per matrix row).
+__host__ __device__ constexpr size_t mat_bytes(int rows, int k) { return size_t(rows) * (k + 1) * 8; }
+__host__ __device__ constexpr size_t scratch_bytes() { return size_t(2 * kMaxK + 8) * 8 + 4 * 8; }
+__host__ __device__ constexpr size_t smem_leaf_qr(int M, int k) { return 2 * mat_bytes(M, k) + scratch_bytes(); }
+__host__ __device__ constexpr size_t smem_transfer_qr(int k) { return 2 * mat_bytes(2 * k, k) + scratch_bytes(); }
+__host__ __device__ constexpr size_t smem_sandwich(int k) { return 4 * mat_bytes(k, k) + scratch_bytes(); }
+__host__ __device__ constexpr size_t smem_down(int k) { return 4 * mat_bytes(k, k) + scratch_bytes(); }
+__host__ __device__ constexpr size_t smem_leaf_svd(int M, int k) { return 2 * mat_bytes(M, k) + mat_bytes(k, k) + scratch_bytes(); }
+__host__ __device__ constexpr size_t smem_node_svd(int k) { return 2 * mat_bytes(2 * k, k) + mat_bytes(k, k) + scratch_bytes(); }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double group8_sum(double v)
+{
+#pragma unroll
+    for (int o = 4; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int level_of(int64_t t) { return 63 - __clzll(t); }
+
+// Householder QR of the rows x cols matrix A in place: R on and above the diagonal, the
+// reflectors' tails below it (leading entry 1 implicit), their scalars in tau.
+// red: 2 doubles of scratch. All threads of the CTA take part.
+__device__ void house_qr(double *A, int ld, int rows, int cols, double *tau, double *red)
+{
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int p = rows < cols ? rows : cols;
+    for (int j = 0; j < p; ++j) {
+        if (warp == 0) {
+            double s = 0.0;
+            for (int i = j + 1 + lane; i < rows; i += 32) s += A[i * ld + j] * A[i * ld + j];
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double alpha = A[j * ld + j];
+                if (s == 0.0) {
+                    tau[j] = 0.0;
+                    red[0] = 0.0;
+                } else {
+                    const double beta = -copysign(sqrt(alpha * alpha + s), alpha);
+                    tau[j] = (beta - alpha) / beta;
+                    red[0] = 1.0 / (alpha - beta);
+                    A[j * ld + j] = beta;
+                }
+            }
+        }
+        __syncthreads();
+        const double tj = tau[j];
+        if (tj != 0.0) {
+            const double sc = red[0];
+            for (int i = j + 1 + threadIdx.x; i < rows; i += kThreads) A[i * ld + j] *= sc;
+            __syncthreads();
+            for (int c = j + 1 + warp; c < cols; c += kWarps) {
+                double w = lane == 0 ? A[j * ld + c] : 0.0;
+                for (int i = j + 1 + lane; i < rows; i += 32) w += A[i * ld + j] * A[i * ld + c];
+                w = warp_sum(w) * tj;
+                if (lane == 0) A[j * ld + c] -= w;
+                for (int i = j + 1 + lane; i < rows; i += 32) A[i * ld + c] -= A[i * ld + j] * w;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Explicit Q (rows x cols) of house_qr's factorization: H_0 ... H_{p-1} applied to the first
+// p columns of the identity, p = min(rows, cols); columns p..cols-1 are zero.
+__device__ void house_form_q(const double *A, int ld, int rows, int cols, const double *tau, double *Q, int ldq)
+{
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int p = rows < cols ? rows : cols;
+    for (int idx = threadIdx.x; idx < rows * cols; idx += kThreads) {
+        const int i = idx / cols, c = idx % cols;
+        Q[i * ldq + c] = (i == c && c < p) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = p - 1; j >= 0; --j) {
+        const double tj = tau[j];
+        if (tj != 0.0) {
+            for (int c = j + warp; c < p; c += kWarps) {
+                double w = lane == 0 ? Q[j * ldq + c] : 0.0;
+                for (int i = j + 1 + lane; i < rows; i += 32) w += A[i * ld + j] * Q[i * ldq + c];
+                w = warp_sum(w) * tj;
+                if (lane == 0) Q[j * ldq + c] -= w;
+                for (int i = j + 1 + lane; i < rows; i += 32) Q[i * ldq + c] -= A[i * ld + j] * w;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// R <- R-factor of [R; B] for an upper-triangular k x k R and a dense k x k B (both in shared
+// memory; B is destroyed). The reflector of column j touches row j of R and all of B.
+__device__ void qr_fold(double *R, double *B, int ld, int k, double *red)
+{
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int j = 0; j < k; ++j) {
+        if (warp == 0) {
+            double s = 0.0;
+            for (int i = lane; i < k; i += 32) s += B[i * ld + j] * B[i * ld + j];
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double alpha = R[j * ld + j];
+                if (s == 0.0) {
+                    red[0] = 0.0;
+                } else {
+                    const double beta = -copysign(sqrt(alpha * alpha + s), alpha);
+                    red[0] = (beta - alpha) / beta;
+                    red[1] = 1.0 / (alpha - beta);
+                    R[j * ld + j] = beta;
+                }
+            }
+        }
+        __syncthreads();
+        const double tj = red[0];
+        if (tj != 0.0) {
+            const double sc = red[1];
+            for (int i = threadIdx.x; i < k; i += kThreads) B[i * ld + j] *= sc;
+            __syncthreads();
+            for (int c = j + 1 + warp; c < k; c += kWarps) {
+                double w = lane == 0 ? R[j * ld + c] : 0.0;
+                for (int i = lane; i < k; i += 32) w += B[i * ld + j] * B[i * ld + c];
+                w = warp_sum(w) * tj;
+                if (lane == 0) R[j * ld + c] -= w;
+                for (int i = lane; i < k; i += 32) B[i * ld + c] -= B[i * ld + j] * w;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One-sided Jacobi on the columns of A (rows x cols, shared memory) until every pair is
+// orthogonal to kJacobiTol (at most kMaxSweeps sweeps). Returns the sweeps taken.
+// flag: one int of shared memory.
+__device__ int jacobi_columns(double *A, int ld, int rows, int cols, int *flag)
+{
+    const int n2 = cols + (cols & 1);  // an odd column count plays against an absent column
+    const int npairs = n2 / 2;
+    const int g = threadIdx.x / 8, gl = threadIdx.x % 8;
+    int sweep = 0;
+    for (; sweep < kMaxSweeps; ++sweep) {
+        if (threadIdx.x == 0) *flag = 0;
+        __syncthreads();
+        for (int r = 0; r < n2 - 1; ++r) {
+            int p, q;
+            if (g == 0) {
+                p = r;
+                q = n2 - 1;
+            } else {
+                p = (r + g) % (n2 - 1);
+                q = (r - g + n2 - 1) % (n2 - 1);
+            }
+            if (p > q) {
+                const int tmp = p;
+                p = q;
+                q = tmp;
+            }
+            // every lane takes part in the group reductions (shuffles need the whole warp)
+            const bool active = g < npairs && q < cols;
+            double al = 0.0, be = 0.0, ga = 0.0;
+            if (active)
+                for (int i = gl; i < rows; i += 8) {
+                    const double x = A[i * ld + p], y = A[i * ld + q];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+            al = group8_sum(al);
+            be = group8_sum(be);
+            ga = group8_sum(ga);
+            if (active && al > 0.0 && be > 0.0 && fabs(ga) > kJacobiTol * sqrt(al) * sqrt(be)) {
+                const double zeta = (be - al) / (2.0 * ga);
+                const double az = fabs(zeta);  // zeta^2 would overflow above ~1e154
+                const double t = az > 1e150 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                for (int i = gl; i < rows; i += 8) {
+                    const double x = A[i * ld + p], y = A[i * ld + q];
+                    A[i * ld + p] = c * x - s * y;
+                    A[i * ld + q] = s * x + c * y;
+                }
+                if (gl == 0) *flag = 1;
+            }
+            __syncthreads();
+        }
+        const int any = *flag;
+        __syncthreads();
+        if (!any) break;
+    }
+    return sweep + 1;
+}
+
+// After jacobi_columns: the singular values (column norms) in descending order into sig[],
+// the normalized columns in that order into W (rows x cols, global, leading dimension ldw),
+// and the count of singular values above cut. sv, pos: cols doubles / ints of scratch.
+__device__ int sort_columns(const double *A, int ld, int rows, int cols, double *sv, int *pos, double *W, int ldw,
+                            int wrows, double *sig, double cut)
+{
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int j = warp; j < cols; j += kWarps) {
+        double s = 0.0;
+        for (int i = lane; i < rows; i += 32) s += A[i * ld + j] * A[i * ld + j];
+        s = warp_sum(s);
+        if (lane == 0) sv[j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cols; j += kThreads) {
+        int r = 0;
+        for (int i = 0; i < cols; ++i) r += (sv[i] > sv[j]) || (sv[i] == sv[j] && i < j);
+        pos[j] = r;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < wrows * cols; idx += kThreads) {
+        const int i = idx / cols, j = idx % cols;
+        const double s = sv[j];
+        W[int64_t(i) * ldw + pos[j]] = (i < rows && s > 0.0) ? A[i * ld + j] / s : 0.0;
+    }
+    for (int j = threadIdx.x; j < cols; j += kThreads) sig[pos[j]] = sv[j];
+    int count = 0;
+    for (int j = 0; j < cols; ++j) count += sv[j] > cut;
+    __syncthreads();
+    return count;
+}
+
+// Carve helpers: matrices of `rows` rows at leading dimension k + 1.
+struct Carve {
+    double *p;
+    __device__ double *take(int rows, int k)
+    {
+        double *r = p;
+        p += size_t(rows) * (k + 1);
+        return r;
+    }
+};
+
+// ---------------------------------------------------------------- 1. orthogonalization
+
+// Leaf bases: U_t = Q_t R_t. U: n x k in tree order; Q: per leaf an M x k slab.
+__global__ void __launch_bounds__(kThreads) k_leaf_qr(const double *__restrict__ U, const int32_t *__restrict__ leaf_lo,
+                                                      int64_t nleaves, int k, int M, double *__restrict__ Q,
+                                                      double *__restrict__ R, int64_t first)
+{
+    extern __shared__ double sm[];
+    const int ld = k + 1;
+    Carve cv{sm};
+    double *A = cv.take(M, k), *Qs = cv.take(M, k), *tau = cv.p, *red = tau + kMaxK;
+    for (int64_t t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        const int lo = leaf_lo[t], rows = leaf_lo[t + 1] - lo;
+        for (int idx = threadIdx.x; idx < rows * k; idx += kThreads) A[(idx / k) * ld + idx % k] = U[int64_t(lo) * k + idx];
+        __syncthreads();
+        house_qr(A, ld, rows, k, tau, red);
+        house_form_q(A, ld, rows, k, tau, Qs, ld);
+        double *Rt = R + (first + t) * k * k;
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+            const int i = idx / k, j = idx % k;
+            Rt[idx] = (i < rows && j >= i) ? A[i * ld + j] : 0.0;
+        }
+        double *Qt = Q + t * int64_t(M) * k;
+        for (int idx = threadIdx.x; idx < M * k; idx += kThreads) {
+            const int i = idx / k, j = idx % k;
+            Qt[idx] = i < rows ? Qs[i * ld + j] : 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// Parents at level lp: [R_c1 E_c1; R_c2 E_c2] = Q R_t; the row blocks of Q are the
+// orthogonal transfers E1 of the two children.
+__global__ void __launch_bounds__(kThreads) k_transfer_qr(int lp, int k, const double *__restrict__ E0,
+                                                          double *__restrict__ E1, double *__restrict__ R)
+{
+    extern __shared__ double sm[];
+    const int ld = k + 1;
+    Carve cv{sm};
+    double *Z = cv.take(2 * k, k), *X = cv.take(2 * k, k), *tau = cv.p, *red = tau + kMaxK;
+    double *Rc = X, *Ec = X + size_t(k) * ld;  // staging, then the explicit Q
+    const int64_t p0 = int64_t(1) << lp;
+    for (int64_t t = p0 + blockIdx.x; t < 2 * p0; t += gridDim.x) {
+        for (int h = 0; h < 2; ++h) {
+            const int64_t c = 2 * t + h;
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+                Rc[(idx / k) * ld + idx % k] = R[c * k * k + idx];
+                Ec[(idx / k) * ld + idx % k] = E0[c * k * k + idx];
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+                const int i = idx / k, j = idx % k;
+                double s = 0.0;
+                for (int m = i; m < k; ++m) s += Rc[i * ld + m] * Ec[m * ld + j];
+                Z[(h * k + i) * ld + j] = s;
+            }
+            __syncthreads();
+        }
+        house_qr(Z, ld, 2 * k, k, tau, red);
+        house_form_q(Z, ld, 2 * k, k, tau, X, ld);
+        double *Eo = E1 + (2 * t) * k * k;  // E1[2t] and E1[2t+1] are adjacent
+        for (int idx = threadIdx.x; idx < 2 * k * k; idx += kThreads) Eo[idx] = X[(idx / k) * ld + idx % k];
+        double *Rt = R + t * k * k;
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+            const int i = idx / k, j = idx % k;
+            Rt[idx] = j >= i ? Z[i * ld + j] : 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// Every coupling block re-expressed in the orthogonal bases: S <- R_t S R_s^T (in place;
+// R upper triangular).
+__global__ void __launch_bounds__(kThreads) k_orth_blocks(double *__restrict__ S, const int32_t *__restrict__ brow,
+                                                          const int32_t *__restrict__ bcol, int64_t nb,
+                                                          const double *__restrict__ R, int k)
+{
+    extern __shared__ double sm[];
+    const int ld = k + 1;
+    Carve cv{sm};
+    double *Ss = cv.take(k, k), *Rt = cv.take(k, k), *Rs = cv.take(k, k), *Tm = cv.take(k, k);
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t t = brow[b], s = bcol[b];
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+            const int o = (idx / k) * ld + idx % k;
+            Ss[o] = S[b * k * k + idx];
+            Rt[o] = R[t * k * k + idx];
+            Rs[o] = R[s * k * k + idx];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {  // Tm = S R_s^T
+            const int i = idx / k, j = idx % k;
+            double v = 0.0;
+            for (int m = j; m < k; ++m) v += Ss[i * ld + m] * Rs[j * ld + m];
+            Tm[i * ld + j] = v;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {  // R_t Tm
+            const int i = idx / k, j = idx % k;
+            double v = 0.0;
+            for (int m = i; m < k; ++m) v += Rt[i * ld + m] * Tm[m * ld + j];
+            S[b * k * k + idx] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- 2. new-basis downsweep
+
+// Nodes of level l: Rh_i = R-factor of [Rh_{i+} E1_i^T; S_{i j1}^T; ...], folded one block
+// at a time (the parent's term first, then the block row in CSR order).
+__global__ void __launch_bounds__(kThreads) k_down_qr(int l, int k, const int64_t *__restrict__ rowptr,
+                                                      const double *__restrict__ S, const double *__restrict__ E1,
+                                                      double *__restrict__ Rh)
+{
+    extern __shared__ double sm[];
+    const int ld = k + 1;
+    Carve cv{sm};
+    double *Rm = cv.take(k, k), *B = cv.take(k, k), *P = cv.take(k, k), *X = cv.take(k, k), *red = cv.p;
+    const int64_t n0 = int64_t(1) << l;
+    for (int64_t i = n0 + blockIdx.x; i < 2 * n0; i += gridDim.x) {
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) Rm[(idx / k) * ld + idx % k] = 0.0;
+        if (i > 1) {
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+                P[(idx / k) * ld + idx % k] = Rh[(i / 2) * k * k + idx];
+                X[(idx / k) * ld + idx % k] = E1[i * k * k + idx];
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {  // B = Rh_p E1_i^T
+                const int a = idx / k, c = idx % k;
+                double v = 0.0;
+                for (int m = a; m < k; ++m) v += P[a * ld + m] * X[c * ld + m];
+                B[a * ld + c] = v;
+            }
+            __syncthreads();
+            qr_fold(Rm, B, ld, k, red);
+        }
+        for (int64_t b = rowptr[i]; b < rowptr[i + 1]; ++b) {
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+                const int a = idx / k, c = idx % k;
+                B[c * ld + a] = S[b * k * k + idx];  // S_ij^T
+            }
+            __syncthreads();
+            qr_fold(Rm, B, ld, k, red);
+        }
+        double *Ro = Rh + i * k * k;
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+            const int a = idx / k, c = idx % k;
+            Ro[idx] = c >= a ? Rm[a * ld + c] : 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// ||A_lr||_F^2 = sum over leaves of ||Rh_t||_F^2, summed in a fixed order by one CTA; the
+// cut tau * ||A_lr||_F is left in cut[0], the norm in cut[1].
+__global__ void __launch_bounds__(kThreads) k_cut(const double *__restrict__ Rh, int64_t first, int64_t nleaves, int k,
+                                                  double tau, double *__restrict__ cut)
+{
+    __shared__ double part[kThreads];
+    double s = 0.0;
+    const int64_t n = nleaves * k * k;
+    const double *base = Rh + first * k * k;
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) s += base[i] * base[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kThreads / 2; w; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        cut[1] = sqrt(part[0]);
+        cut[0] = tau * cut[1];
+    }
+}
+
+// ---------------------------------------------------------------- 3. truncation upsweep
+
+// Leaves: SVD of the reweighted basis Q_t Rh_t^T (rows x k). W: per leaf an M x k slab of
+// left singular vectors by descending singular value; sig: k per leaf; the count above the
+// cut raises rank[q].
+__global__ void __launch_bounds__(kThreads) k_leaf_svd(const double *__restrict__ Q, const int32_t *__restrict__ leaf_lo,
+                                                       int64_t nleaves, int k, int M, const double *__restrict__ Rh,
+                                                       int64_t first, const double *__restrict__ cut,
+                                                       double *__restrict__ W, double *__restrict__ sig,
+                                                       int *__restrict__ rank, int q, unsigned long long *sweeps)
+{
+    extern __shared__ double sm[];
+    const int ld = k + 1;
+    Carve cv{sm};
+    double *A = cv.take(M, k), *Qs = cv.take(M, k), *Rs = cv.take(k, k), *sv = cv.p;
+    int *pos = reinterpret_cast<int *>(sv + kMaxK), *flag = pos + kMaxK;
+    const double c0 = cut[0];
+    for (int64_t t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        const int rows = leaf_lo[t + 1] - leaf_lo[t];
+        const double *Qt = Q + t * int64_t(M) * k;
+        for (int idx = threadIdx.x; idx < rows * k; idx += kThreads) Qs[(idx / k) * ld + idx % k] = Qt[idx];
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads)
+            Rs[(idx / k) * ld + idx % k] = Rh[(first + t) * k * k + idx];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < rows * k; idx += kThreads) {  // A = Q Rh^T
+            const int i = idx / k, j = idx % k;
+            double v = 0.0;
+            for (int m = j; m < k; ++m) v += Qs[i * ld + m] * Rs[j * ld + m];
+            A[i * ld + j] = v;
+        }
+        __syncthreads();
+        const int sw = jacobi_columns(A, ld, rows, k, flag);
+        const int count = sort_columns(A, ld, rows, k, sv, pos, W + t * int64_t(M) * k, k, M, sig + t * k, c0);
+        if (threadIdx.x == 0) {
+            atomicMax(rank + q, count);
+            atomicAdd(sweeps, (unsigned long long)sw);
+        }
+    }
+}
+
+// Leaves, once rank[q] is known: T_t = U'_t^T Q_t (r x k), U'_t the first r columns of W.
+__global__ void __launch_bounds__(kThreads) k_leaf_t(const double *__restrict__ Q, const double *__restrict__ W,
+                                                     const int32_t *__restrict__ leaf_lo, int64_t nleaves, int k, int M,
+                                                     const int *__restrict__ rank, int q, int64_t first,
+                                                     double *__restrict__ T)
+{
+    const int r = rank[q];
+    for (int64_t t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        const int rows = leaf_lo[t + 1] - leaf_lo[t];
+        const double *Qt = Q + t * int64_t(M) * k, *Wt = W + t * int64_t(M) * k;
+        double *Tt = T + (first + t) * k * k;
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+            const int a = idx / k, j = idx % k;
+            double v = 0.0;
+            if (a < r)
+                for (int i = 0; i < rows; ++i) v += Wt[int64_t(i) * k + a] * Qt[int64_t(i) * k + j];
+            Tt[idx] = v;
+        }
+    }
+}
+
+// Parents at level lp (children at lp + 1 with rank r = rank[lp+1]): Z = [T_c1 E1_c1;
+// T_c2 E1_c2] (2r x k), SVD of Z Rh_t^T; Z and the sorted left singular vectors are kept
+// for k_node_t; the count above the cut raises rank[lp].
+__global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const double *__restrict__ T,
+                                                       const double *__restrict__ E1, const double *__restrict__ Rh,
+                                                       const double *__restrict__ cut, double *__restrict__ Zb,
+                                                       double *__restrict__ Wb, double *__restrict__ sig,
+                                                       int *__restrict__ rank, unsigned long long *sweeps)
+{
+    extern __shared__ double sm[];
+    const int ld = k + 1;
+    Carve cv{sm};
+    double *Z = cv.take(2 * k, k), *X = cv.take(2 * k, k), *Rs = cv.take(k, k), *sv = cv.p;
+    int *pos = reinterpret_cast<int *>(sv + kMaxK), *flag = pos + kMaxK;
+    double *Tc = X, *Ec = X + size_t(k) * ld;  // staging; then X holds Z Rh^T
+    const double c0 = cut[0];
+    const int r = rank[lp + 1];
+    const int64_t p0 = int64_t(1) << lp;
+    for (int64_t t = p0 + blockIdx.x; t < 2 * p0; t += gridDim.x) {
+        const int64_t slot = t - p0;
+        for (int h = 0; h < 2; ++h) {
+            const int64_t c = 2 * t + h;
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+                Tc[(idx / k) * ld + idx % k] = T[c * k * k + idx];
+                Ec[(idx / k) * ld + idx % k] = E1[c * k * k + idx];
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < r * k; idx += kThreads) {
+                const int i = idx / k, j = idx % k;
+                double v = 0.0;
+                for (int m = 0; m < k; ++m) v += Tc[i * ld + m] * Ec[m * ld + j];
+                Z[(h * r + i) * ld + j] = v;
+            }
+            __syncthreads();
+        }
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads)
+            Rs[(idx / k) * ld + idx % k] = Rh[t * k * k + idx];
+        double *Zo = Zb + slot * 2 * k * k;
+        for (int idx = threadIdx.x; idx < 2 * r * k; idx += kThreads) Zo[idx] = Z[(idx / k) * ld + idx % k];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 2 * r * k; idx += kThreads) {  // X = Z Rh^T
+            const int i = idx / k, j = idx % k;
+            double v = 0.0;
+            for (int m = j; m < k; ++m) v += Z[i * ld + m] * Rs[j * ld + m];
+            X[i * ld + j] = v;
+        }
+        __syncthreads();
+        int count = 0;
+        if (r > 0) {
+            const int sw = jacobi_columns(X, ld, 2 * r, k, flag);
+            count = sort_columns(X, ld, 2 * r, k, sv, pos, Wb + slot * 2 * k * k, k, 2 * r, sig + t * k, c0);
+            if (threadIdx.x == 0) atomicAdd(sweeps, (unsigned long long)sw);
+        } else {
+            for (int j = threadIdx.x; j < k; j += kThreads) sig[t * k + j] = 0.0;
+        }
+        if (threadIdx.x == 0) atomicMax(rank + lp, count);
+        __syncthreads();
+    }
+}
+
+// Parents at level lp, once rank[lp] = rp is known: E'_c1, E'_c2 = the two row blocks of the
+// first rp singular vectors; T_t = W^T Z (rp x k).
+__global__ void __launch_bounds__(kThreads) k_node_t(int lp, int k, const double *__restrict__ Zb,
+                                                     const double *__restrict__ Wb, const int *__restrict__ rank,
+                                                     double *__restrict__ E2, double *__restrict__ T)
+{
+    const int r = rank[lp + 1], rp = rank[lp];
+    const int64_t p0 = int64_t(1) << lp;
+    for (int64_t t = p0 + blockIdx.x; t < 2 * p0; t += gridDim.x) {
+        const int64_t slot = t - p0;
+        const double *Zo = Zb + slot * 2 * k * k, *Wo = Wb + slot * 2 * k * k;
+        for (int h = 0; h < 2; ++h) {
+            double *Ec = E2 + (2 * t + h) * k * k;
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+                const int i = idx / k, j = idx % k;
+                Ec[idx] = (i < r && j < rp) ? Wo[int64_t(h * r + i) * k + j] : 0.0;
+            }
+        }
+        double *Tt = T + t * k * k;
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+            const int a = idx / k, j = idx % k;
+            double v = 0.0;
+            if (a < rp)
+                for (int i = 0; i < 2 * r; ++i) v += Wo[int64_t(i) * k + a] * Zo[int64_t(i) * k + j];
+            Tt[idx] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- 4. projection
+
+// S'_ts = T_t S_ts T_s^T (r x r at the block's level, zero elsewhere in the k x k slab).
+__global__ void __launch_bounds__(kThreads) k_project(double *__restrict__ S, const int32_t *__restrict__ brow,
+                                                      const int32_t *__restrict__ bcol, int64_t nb,
+                                                      const double *__restrict__ T, const int *__restrict__ rank, int k)
+{
+    extern __shared__ double sm[];
+    const int ld = k + 1;
+    Carve cv{sm};
+    double *Ss = cv.take(k, k), *Tt = cv.take(k, k), *Ts = cv.take(k, k), *Tm = cv.take(k, k);
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t t = brow[b], s = bcol[b];
+        const int r = rank[level_of(t)];
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+            const int o = (idx / k) * ld + idx % k;
+            Ss[o] = S[b * k * k + idx];
+            Tt[o] = T[t * k * k + idx];
+            Ts[o] = T[s * k * k + idx];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * r; idx += kThreads) {  // Tm = S T_s^T (k x r)
+            const int i = idx / r, j = idx % r;
+            double v = 0.0;
+            for (int m = 0; m < k; ++m) v += Ss[i * ld + m] * Ts[j * ld + m];
+            Tm[i * ld + j] = v;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {  // T_t Tm
+            const int i = idx / k, j = idx % k;
+            double v = 0.0;
+            if (i < r && j < r)
+                for (int m = 0; m < k; ++m) v += Tt[i * ld + m] * Tm[m * ld + j];
+            S[b * k * k + idx] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- compaction to rank kc
+
+__global__ void k_compact_u(const double *__restrict__ W, const int32_t *__restrict__ leaf_lo, int64_t nleaves, int k,
+                            int M, const int *__restrict__ rank, int q, int kc, double *__restrict__ U)
+{
+    const int r = rank[q];
+    for (int64_t t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        const int lo = leaf_lo[t], rows = leaf_lo[t + 1] - lo;
+        for (int idx = threadIdx.x; idx < rows * kc; idx += blockDim.x) {
+            const int i = idx / kc, j = idx % kc;
+            U[(int64_t(lo) + i) * kc + j] = j < r ? W[(t * int64_t(M) + i) * k + j] : 0.0;
+        }
+    }
+}
+
+// k x k slabs -> kc x kc (top-left), for the transfers and the coupling blocks.
+__global__ void k_compact_slabs(const double *__restrict__ src, int64_t count, int k, int kc, double *__restrict__ dst)
+{
+    const int64_t n = count * kc * kc;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < n; idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t b = idx / (int64_t(kc) * kc);
+        const int i = int((idx / kc) % kc), j = int(idx % kc);
+        dst[idx] = (i < k && j < k) ? src[(b * k + i) * k + j] : 0.0;
+    }
+}
+
+}  // namespace h2c

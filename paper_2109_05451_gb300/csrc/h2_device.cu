@@ -1170,6 +1170,44 @@ void h2_device_free(h2_op *op)
 
 // ---------------------------------------------------------------- internal entry points (h2_internal.h)
 
+int h2_coupling_fp64(const h2_op &op, double *dS, void *cuda_stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t ncpl = int64_t(op.cpl_col.size());
+    if (ncpl == 0) return H2_OK;
+    if (!op.S.empty()) {
+        int rc = cuda_status(cudaMemcpyAsync(dS, op.S.data(), op.S.size() * 8, cudaMemcpyHostToDevice, st));
+        return rc == H2_OK ? cuda_status(cudaStreamSynchronize(st)) : rc;
+    }
+    std::vector<int32_t> row(ncpl);
+    for (int64_t t = 1; t <= op.nnodes; ++t)
+        for (int64_t b = op.cpl_rowptr[t]; b < op.cpl_rowptr[t + 1]; ++b) row[b] = int32_t(t);
+    char *tmp = nullptr;
+    const size_t b_rows = align_up(size_t(ncpl) * 4), b_cheb = align_up(op.cheb.size() * 8);
+    if (cudaMalloc(&tmp, 2 * b_rows + b_cheb) != cudaSuccess) {
+        cudaGetLastError();
+        return H2_ENOMEM;
+    }
+    int32_t *d_row = reinterpret_cast<int32_t *>(tmp), *d_col = reinterpret_cast<int32_t *>(tmp + b_rows);
+    double *d_cheb = reinterpret_cast<double *>(tmp + 2 * b_rows);
+    int rc = cuda_status(cudaMemcpyAsync(d_row, row.data(), ncpl * 4, cudaMemcpyHostToDevice, st));
+    if (rc == H2_OK) rc = cuda_status(cudaMemcpyAsync(d_col, op.cpl_col.data(), ncpl * 4, cudaMemcpyHostToDevice, st));
+    if (rc == H2_OK)
+        rc = cuda_status(cudaMemcpyAsync(d_cheb, op.cheb.data(), op.cheb.size() * 8, cudaMemcpyHostToDevice, st));
+    if (rc == H2_OK) {
+        h2k::KernelFn f{int(op.ker.kind), op.ker.a, op.ker.b, op.ker.deg};
+        // gen_coupling stores kappa(xi^t_nu, xi^s_mu) at mu * k + nu; with the roles of row
+        // and column swapped it stores kappa(xi^s_nu, xi^t_mu) = S_ts[mu][nu] (kappa is
+        // symmetric) at mu * k + nu: S_ts row-major
+        h2k::gen_coupling<double><<<unsigned(std::min<int64_t>(ncpl, 1 << 20)), 256, 0, st>>>(
+            dS, d_col, d_row, ncpl, d_cheb, op.dim, op.p, op.k, op.k, f);
+        rc = cuda_status(cudaGetLastError());
+    }
+    if (rc == H2_OK) rc = cuda_status(cudaStreamSynchronize(st));
+    cudaFree(tmp);
+    return rc;
+}
+
 int h2_exec_create(h2_exec *ex)
 {
     if (!ex) return H2_EINVAL;
@@ -1236,6 +1274,9 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     if (!h) return H2_EINVAL;
     if (prec != H2_FP64 && prec != H2_FP32 && prec != H2_BF16X2 && prec != H2_FP32_MF) return H2_EINVAL;
     h2_op &op = *h;
+    // explicit coupling blocks (a compressed operator) exist in FP64 / FP32 tiles only: the
+    // tensor tiles are 64 x 64 and the matrix-free precision needs the Chebyshev points
+    if (!op.S.empty() && (prec == H2_BF16X2 || prec == H2_FP32_MF)) return H2_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     h2_device_free(&op);
     h2_device *dv = new (std::nothrow) h2_device;
@@ -1481,13 +1522,25 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     cp(d_dcol, op.dns_col.data(), ndns * 4);
     cp(d_doff, dns_off.data(), (ndns + 1) * 8);
     if (rc == H2_OK) rc = cuda_status(cudaMemsetAsync(dv->err, 0, 16, st));
+    // explicit coupling blocks, rounded once to the precision, in the tile layout (ld kx)
+    const bool explicit_s = !op.S.empty();
+    std::vector<unsigned char> Sb(explicit_s ? size_t(ncpl) * dv->kkp * es : 0, 0);
+    if (explicit_s) {
+        // op.S holds S_ts[nu][mu] row-major; the tiles hold each block transposed (entry
+        // (nu, mu) at mu * kx + nu), as gen_coupling writes them
+        for (int64_t b = 0; b < ncpl; ++b)
+            for (int mu = 0; mu < k; ++mu)
+                for (int nu = 0; nu < k; ++nu) put(Sb, (size_t(b) * k + mu) * kx + nu, op.S[(size_t(b) * k + nu) * k + mu]);
+        cp(dv->vals, Sb.data(), Sb.size());
+    }
+    const int64_t ncpl_gen = explicit_s ? 0 : ncpl;
     if (rc == H2_OK)
         rc = dv->mf ? generate_mf_points(op, *dv, d_cheb, d_pts, st)
              : dv->tc ? generate_tc_blocks(op, *dv, d_crow, d_drow, d_dcol, d_ccol, d_cheb, d_pts, s_bytes, st)
              : es == 8 ? generate_blocks<double>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st,
-                                                 ncpl, ndns)
+                                                 ncpl_gen, ndns)
                        : generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st,
-                                                ncpl, ndns);
+                                                ncpl_gen, ndns);
     if (rc == H2_OK && dv->mf && ncpl_top > 0)
         rc = generate_blocks<float>(op, *dv, d_crow, d_drow, d_dcol, d_doff, d_ccol, d_cheb, d_pts, s_bytes, st,
                                     ncpl_top, 0);
@@ -1636,6 +1689,13 @@ int h2_get_info(h2_handle h, h2_info *info)
     info->transfer_entries = (op.nnodes - 1) * op.k * op.k;
     info->uploaded_prec = op.dev ? int(op.dev->prec) : -1;
     info->device_bytes = op.dev ? op.dev->arena_bytes + op.dev->ws_bytes : 0;
+    return H2_OK;
+}
+
+int h2_get_level_ranks(h2_handle h, int *ranks)
+{
+    if (!h || !ranks) return H2_EINVAL;
+    for (int l = 0; l <= h->q; ++l) ranks[l] = h->level_rank.empty() ? h->k : h->level_rank[l];
     return H2_OK;
 }
 

@@ -295,7 +295,13 @@ bool consistent(const h2_op &o)
     const int64_t n = o.n, nn = o.nnodes, first = o.first_leaf(), leaves = o.nleaves();
     int64_t k = 1;
     for (int d = 0; d < o.dim; ++d) k *= o.p;
-    if (o.p < 1 || o.k != k || o.m < 1) return false;
+    if (o.m < 1 || o.k < 1) return false;
+    if (o.p == 0) {  // compressed: explicit blocks, level ranks within the stored rank
+        for (int r : o.level_rank)
+            if (r < 0 || r > o.k) return false;
+    } else if (o.p < 0 || o.k != k) {
+        return false;
+    }
     std::vector<char> seen(size_t(n), 0);
     for (int64_t v : o.perm) {
         if (v < 0 || v >= n || seen[size_t(v)]) return false;
@@ -333,7 +339,8 @@ extern "C" int h2_save(h2_handle h, const char *path)
               std::fwrite(&o.ker, sizeof(o.ker), 1, f) == 1;
     ok = ok && put_vec(f, o.pts) && put_vec(f, o.perm) && put_vec(f, o.lo) && put_vec(f, o.hi) &&
          put_vec(f, o.bmin) && put_vec(f, o.bmax) && put_vec(f, o.cheb) && put_vec(f, o.U) && put_vec(f, o.E) &&
-         put_vec(f, o.cpl_rowptr) && put_vec(f, o.cpl_col) && put_vec(f, o.dns_rowptr) && put_vec(f, o.dns_col);
+         put_vec(f, o.cpl_rowptr) && put_vec(f, o.cpl_col) && put_vec(f, o.dns_rowptr) && put_vec(f, o.dns_col) &&
+         put_vec(f, o.S) && put_vec(f, o.level_rank);
     ok = (std::fclose(f) == 0) && ok;
     return ok ? H2_OK : H2_EINVAL;
 }
@@ -365,7 +372,8 @@ extern "C" int h2_load(const char *path, h2_handle *out)
         o->k = int(ints[4]);
         o->q = int(ints[5]);
         o->nnodes = ints[6];
-        ok = o->n >= 1 && o->dim >= 1 && o->dim <= 3 && o->q >= 0 && o->q < 40 && o->nnodes == (int64_t(2) << o->q) - 1;
+        ok = o->n >= 1 && o->dim >= 1 && o->dim <= 3 && o->q >= 0 && o->q < 40 && o->nnodes == (int64_t(2) << o->q) - 1 &&
+             o->k >= 1 && o->k <= 4096 && o->p >= 0;
     }
     if (ok) {
         const uint64_t n = uint64_t(o->n), nodes = uint64_t(o->nnodes + 1), k = uint64_t(o->k);
@@ -377,6 +385,10 @@ extern "C" int h2_load(const char *path, h2_handle *out)
         if (ok) ok = get_vec(f, o->cpl_col, uint64_t(o->cpl_rowptr.back()));
         if (ok) ok = get_vec(f, o->dns_rowptr, leaves + 1);
         if (ok) ok = get_vec(f, o->dns_col, uint64_t(o->dns_rowptr.back()));
+        // a compressed operator carries its coupling blocks and level ranks (p = 0)
+        const bool compressed = o->p == 0;
+        if (ok) ok = get_vec(f, o->S, compressed ? uint64_t(o->cpl_col.size()) * k * k : 0);
+        if (ok) ok = get_vec(f, o->level_rank, compressed ? uint64_t(o->q + 1) : 0);
     }
     std::fclose(f);
     if (ok) ok = consistent(*o);

@@ -34,6 +34,12 @@ struct h2_op {
     std::vector<int64_t> dns_rowptr; // nleaves + 1
     std::vector<int32_t> dns_col;    // leaf index of the column cluster
 
+    // explicit coupling blocks of a compressed operator (n_coupling x k x k, CSR order,
+    // S_ts[nu][mu] row-major);
+    // empty when the blocks are the kernel at the clusters' Chebyshev points (then p > 0)
+    std::vector<double> S;
+    std::vector<int> level_rank;     // per level, compressed operators only
+
     int64_t nleaves() const { return int64_t(1) << q; }
     int64_t first_leaf() const { return int64_t(1) << q; }
 
@@ -57,6 +63,10 @@ void h2_exec_destroy(h2_exec *ex);
 // h2_matvec_ws with an explicit fork/join context (nullptr: the handle's own).
 int h2_matvec_exec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *workspace,
                    size_t ws_bytes, void *cuda_stream, const h2_exec *ex);
+
+// FP64 coupling blocks (n_coupling x k x k, CSR order, each S_ts[nu][mu] row-major) on the
+// device: generated from the kernel, or copied when explicit. Synchronises the stream.
+int h2_coupling_fp64(const h2_op &op, double *dS, void *cuda_stream);
 
 // h2_host.cpp
 int h2_host_build(h2_op *op, const double *points, int64_t n, int dim, h2_kernel kernel,

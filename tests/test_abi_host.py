@@ -151,3 +151,15 @@ def test_cancel_and_selftest_reject_bad_arguments_before_cuda():
     assert lib.h2_selftest_wait_timeout(0) == h2.H2_EINVAL
     assert lib.h2_selftest_wait_timeout(10 ** 12) == h2.H2_EINVAL
     assert h2.h2_status_str(h2.H2_ECANCELED) == "cancelled"
+
+
+def test_compress_rejects_bad_arguments_before_cuda():
+    h = h2.h2_build(si.grid_2d(16), ("exp", 0.1, 0, 0), 16, 4, 0.7)
+    try:
+        assert h2.h2_get_level_ranks(h) == [16] * (h2.h2_get_info(h).depth + 1)
+        for handle, tau in ((0, 1e-3), (h, -1.0), (h, float("nan")), (h, float("inf"))):
+            with pytest.raises(h2.H2Error) as e:
+                h2.h2_compress(handle, tau, stream=0)
+            assert e.value.status == h2.H2_EINVAL
+    finally:
+        h2.h2_destroy(h)
