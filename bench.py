@@ -364,6 +364,68 @@ def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, 
     return out
 
 
+FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the part (CUDA cores); no tensor-core FP64 path
+
+
+def compress_benchmark(h2, torch, steps=3, workloads=None):
+    """Algebraic recompression (Sec. 5) of the compression sets of Sec. 6 (synthetic_inputs
+    COMPRESS_2D at N = 2^20, COMPRESS_3D at N = 2^18) to tau = 1e-3 on the GPU in FP64. Per
+    set: device time of each step (CUDA events inside h2_compress, mean over `steps` calls
+    after one warm-up call), the whole call's wall time (with the copies of the operator to
+    and from the device), operation counts and rate against the FP64 peak (the path is bound
+    by FP64 arithmetic), level ranks, low-rank memory before and after, and the relative
+    error of the compressed FP64 product against the original's on one Gaussian vector."""
+    import time
+    out = {}
+    for w in workloads or (si.COMPRESS_2D, si.COMPRESS_3D):
+        pts = w.make_points()
+        op = h2.H2Operator(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+        g = op.compress(si.COMPRESS_TAU)  # warm-up (kernel attributes, allocator)
+        g.close()
+        ms = np.zeros(4)
+        wall = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = op.compress(si.COMPRESS_TAU)
+            wall.append(time.perf_counter() - t0)
+            ms += np.array(list(g.compress_info.ms))
+            info = g.compress_info
+            if _ + 1 < steps:
+                g.close()
+        ms /= steps
+        flops = np.array(list(info.flops))
+        x = si.gaussian_vectors(len(pts), 1, 1)
+        X = torch.from_numpy(x[:, 0]).cuda()
+        op.upload("fp64")
+        g.upload("fp64")
+        y0 = op.matvec(X).cpu().numpy()
+        y1 = g.matvec(X).cpu().numpy()
+        total_ms = float(ms.sum())
+        gflops = float(flops.sum()) / (total_ms * 1e-3) / 1e9
+        out[w.name] = {
+            "n": len(pts), "kernel": w.kernel[0], "rank_in": info.rank_in, "leaf": w.leaf_size, "eta": w.eta,
+            "tau": info.tau, "depth": info.depth, "level_ranks": list(info.level_rank)[:info.depth + 1],
+            "rank_out": info.rank_out,
+            "ms": {"orthogonalize": ms[0], "downsweep": ms[1], "truncate": ms[2], "project": ms[3], "total": total_ms},
+            "wall_s": float(np.mean(wall)),
+            "gflop": {"orthogonalize": flops[0] / 1e9, "downsweep": flops[1] / 1e9, "truncate": flops[2] / 1e9,
+                      "project": flops[3] / 1e9},
+            "gflops": gflops, "jacobi_sweeps": int(info.jacobi_sweeps),
+            "lowrank_GB_in": info.lowrank_bytes_in / 1e9, "lowrank_GB_out": info.lowrank_bytes_out / 1e9,
+            "lowrank_reduction": info.lowrank_bytes_in / max(info.lowrank_bytes_out, 1),
+            "relerr_vs_uncompressed": float(np.linalg.norm(y1 - y0) / np.linalg.norm(y0)),
+            "error_bound_rel": float(2 * np.sqrt(info.dropped_energy) * np.linalg.norm(x) / np.linalg.norm(y0)),
+            "roofline": {"kernel": "h2_compress (FP64 QR / Jacobi SVD / small products, CUDA cores)", "bound": "alu",
+                         "achieved": gflops / 1e3, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": gflops / 1e3 / FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 rate"},
+        }
+        g.close()
+        op.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with_fp64=True):
     """Batched products of 64 uneven operators (synthetic_inputs.uneven_batch: N log-uniform
     in [2^12, 2^18], even members 2D grids with orders 4-8, odd members 3D clouds with orders
@@ -474,6 +536,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the CG serving-loop measurement")
     ap.add_argument("--no-matrix-free", action="store_true", help="skip the matrix-free product measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-operator measurement")
+    ap.add_argument("--no-compress", action="store_true", help="skip the algebraic-compression measurement")
     ap.add_argument("--batch-count", type=int, default=64, help="operators of the batched measurement")
     ap.add_argument("--batch-nmax", type=int, default=2 ** 18,
                     help="largest N of the batched measurement (smaller values are for profiler captures)")
@@ -638,6 +701,11 @@ def main():
                                             with_fp64=not args.no_fp64)
         except Exception as exc:  # reported, never silently dropped
             line["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if not args.no_compress:
+        try:
+            line["compress"] = compress_benchmark(h2, torch)
+        except Exception as exc:  # reported, never silently dropped
+            line["compress"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_serve:
         try:
             line["serve"] = serve_benchmark(h2, torch, args.serve_requests, args.serve_maxit)

@@ -228,9 +228,9 @@ int h2_load(const char *path, h2_handle *out);
  *      (the parent's factor times the transposed transfer, then the transposed blocks of the
  *      node's block row), folded one block at a time;
  *   3. the truncation upsweep: SVDs of the reweighted leaf bases and of the stacked
- *      projected transfers; singular values above cut = tau * ||A_lr||_F are kept (A_lr: the
- *      low-rank part; ||A_lr||_F^2 = sum over leaves of ||R_t||_F^2); each level keeps the
- *      largest count over its nodes (one rank per level);
+ *      projected transfers; of each node, the singular values above tau times its largest
+ *      are kept (every block row keeps relative accuracy tau); each level keeps the largest
+ *      count over its nodes (one rank per level);
  *   4. projection of every coupling block on the new bases (S' = T_t S T_s^T).
  * Dense blocks are unchanged. The result is a new handle holding the compressed operator on
  * the host in FP64 (bases, transfers and coupling blocks stored at one rank, the largest level
@@ -242,8 +242,9 @@ int h2_load(const char *path, h2_handle *out);
  * Synchronises the stream. Errors: H2_EINVAL, H2_ENOMEM, H2_ECUDA. */
 typedef struct {
     double tau;
-    double norm_lowrank;           /* ||A_lr||_F */
-    double cut;                    /* tau * norm_lowrank */
+    double norm_lowrank;           /* ||A_lr||_F, A_lr the low-rank part (sum over leaves of ||R_t||_F^2) */
+    double dropped_energy;         /* sum of the squares of the singular values not kept:
+                                      ||A_lr - A'_lr||_F <= 2 sqrt(dropped_energy) */
     int depth;
     int rank_in;                   /* rank of the input */
     int rank_out;                  /* stored rank of the result: max of level_rank, >= 1 */

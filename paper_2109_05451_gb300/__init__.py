@@ -54,7 +54,7 @@ class h2_request_result(C.Structure):
 
 
 class h2_compress_info(C.Structure):
-    _fields_ = [("tau", C.c_double), ("norm_lowrank", C.c_double), ("cut", C.c_double), ("depth", C.c_int),
+    _fields_ = [("tau", C.c_double), ("norm_lowrank", C.c_double), ("dropped_energy", C.c_double), ("depth", C.c_int),
                 ("rank_in", C.c_int), ("rank_out", C.c_int), ("level_rank", C.c_int * H2_MAX_LEVELS),
                 ("ms", C.c_double * 4), ("flops", C.c_double * 4), ("jacobi_sweeps", C.c_int64),
                 ("lowrank_bytes_in", C.c_size_t), ("lowrank_bytes_out", C.c_size_t)]

@@ -221,9 +221,10 @@ __device__ int jacobi_columns(double *A, int ld, int rows, int cols, int *flag)
 
 // After jacobi_columns: the singular values (column norms) in descending order into sig[],
 // the normalized columns in that order into W (rows x cols, global, leading dimension ldw),
-// and the count of singular values above cut. sv, pos: cols doubles / ints of scratch.
+// and the count of singular values above tau times the largest. sv, pos: cols doubles /
+// ints of scratch.
 __device__ int sort_columns(const double *A, int ld, int rows, int cols, double *sv, int *pos, double *W, int ldw,
-                            int wrows, double *sig, double cut)
+                            int wrows, double *sig, double tau)
 {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int j = warp; j < cols; j += kWarps) {
@@ -245,8 +246,11 @@ __device__ int sort_columns(const double *A, int ld, int rows, int cols, double 
         W[int64_t(i) * ldw + pos[j]] = (i < rows && s > 0.0) ? A[i * ld + j] / s : 0.0;
     }
     for (int j = threadIdx.x; j < cols; j += kThreads) sig[pos[j]] = sv[j];
+    double smax = 0.0;
+    for (int j = 0; j < cols; ++j) smax = fmax(smax, sv[j]);
     int count = 0;
-    for (int j = 0; j < cols; ++j) count += sv[j] > cut;
+    if (smax > 0.0)
+        for (int j = 0; j < cols; ++j) count += sv[j] > tau * smax;
     __syncthreads();
     return count;
 }
@@ -416,10 +420,10 @@ __global__ void __launch_bounds__(kThreads) k_down_qr(int l, int k, const int64_
     }
 }
 
-// ||A_lr||_F^2 = sum over leaves of ||Rh_t||_F^2, summed in a fixed order by one CTA; the
-// cut tau * ||A_lr||_F is left in cut[0], the norm in cut[1].
-__global__ void __launch_bounds__(kThreads) k_cut(const double *__restrict__ Rh, int64_t first, int64_t nleaves, int k,
-                                                  double tau, double *__restrict__ cut)
+// ||A_lr||_F^2 = sum over leaves of ||Rh_t||_F^2 (A_lr the low-rank part), summed in a fixed
+// order by one CTA into norm[0] (a check of the downsweep; the cut is relative per node).
+__global__ void __launch_bounds__(kThreads) k_norm(const double *__restrict__ Rh, int64_t first, int64_t nleaves, int k,
+                                                   double *__restrict__ norm)
 {
     __shared__ double part[kThreads];
     double s = 0.0;
@@ -432,20 +436,17 @@ __global__ void __launch_bounds__(kThreads) k_cut(const double *__restrict__ Rh,
         if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        cut[1] = sqrt(part[0]);
-        cut[0] = tau * cut[1];
-    }
+    if (threadIdx.x == 0) norm[0] = sqrt(part[0]);
 }
 
 // ---------------------------------------------------------------- 3. truncation upsweep
 
 // Leaves: SVD of the reweighted basis Q_t Rh_t^T (rows x k). W: per leaf an M x k slab of
-// left singular vectors by descending singular value; sig: k per leaf; the count above the
-// cut raises rank[q].
+// left singular vectors by descending singular value; sig: k per leaf; the count above tau
+// times the largest raises rank[q].
 __global__ void __launch_bounds__(kThreads) k_leaf_svd(const double *__restrict__ Q, const int32_t *__restrict__ leaf_lo,
                                                        int64_t nleaves, int k, int M, const double *__restrict__ Rh,
-                                                       int64_t first, const double *__restrict__ cut,
+                                                       int64_t first, double tau,
                                                        double *__restrict__ W, double *__restrict__ sig,
                                                        int *__restrict__ rank, int q, unsigned long long *sweeps)
 {
@@ -454,7 +455,6 @@ __global__ void __launch_bounds__(kThreads) k_leaf_svd(const double *__restrict_
     Carve cv{sm};
     double *A = cv.take(M, k), *Qs = cv.take(M, k), *Rs = cv.take(k, k), *sv = cv.p;
     int *pos = reinterpret_cast<int *>(sv + kMaxK), *flag = pos + kMaxK;
-    const double c0 = cut[0];
     for (int64_t t = blockIdx.x; t < nleaves; t += gridDim.x) {
         const int rows = leaf_lo[t + 1] - leaf_lo[t];
         const double *Qt = Q + t * int64_t(M) * k;
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_svd(const double *__restrict_
         }
         __syncthreads();
         const int sw = jacobi_columns(A, ld, rows, k, flag);
-        const int count = sort_columns(A, ld, rows, k, sv, pos, W + t * int64_t(M) * k, k, M, sig + t * k, c0);
+        const int count = sort_columns(A, ld, rows, k, sv, pos, W + t * int64_t(M) * k, k, M, sig + t * k, tau);
         if (threadIdx.x == 0) {
             atomicMax(rank + q, count);
             atomicAdd(sweeps, (unsigned long long)sw);
@@ -478,14 +478,21 @@ __global__ void __launch_bounds__(kThreads) k_leaf_svd(const double *__restrict_
     }
 }
 
-// Leaves, once rank[q] is known: T_t = U'_t^T Q_t (r x k), U'_t the first r columns of W.
+// Leaves, once rank[q] is known: T_t = U'_t^T Q_t (r x k), U'_t the first r columns of W;
+// the squares of the singular values not kept are added to dropped[0].
 __global__ void __launch_bounds__(kThreads) k_leaf_t(const double *__restrict__ Q, const double *__restrict__ W,
                                                      const int32_t *__restrict__ leaf_lo, int64_t nleaves, int k, int M,
                                                      const int *__restrict__ rank, int q, int64_t first,
-                                                     double *__restrict__ T)
+                                                     double *__restrict__ T, const double *__restrict__ sig,
+                                                     double *__restrict__ dropped)
 {
     const int r = rank[q];
     for (int64_t t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            double d = 0.0;
+            for (int j = r; j < k; ++j) d += sig[(first + t) * k + j] * sig[(first + t) * k + j];
+            atomicAdd(dropped, d);
+        }
         const int rows = leaf_lo[t + 1] - leaf_lo[t];
         const double *Qt = Q + t * int64_t(M) * k, *Wt = W + t * int64_t(M) * k;
         double *Tt = T + (first + t) * k * k;
@@ -504,7 +511,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_t(const double *__restrict__ 
 // for k_node_t; the count above the cut raises rank[lp].
 __global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const double *__restrict__ T,
                                                        const double *__restrict__ E1, const double *__restrict__ Rh,
-                                                       const double *__restrict__ cut, double *__restrict__ Zb,
+                                                       double tau, double *__restrict__ Zb,
                                                        double *__restrict__ Wb, double *__restrict__ sig,
                                                        int *__restrict__ rank, unsigned long long *sweeps)
 {
@@ -514,7 +521,6 @@ __global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const doub
     double *Z = cv.take(2 * k, k), *X = cv.take(2 * k, k), *Rs = cv.take(k, k), *sv = cv.p;
     int *pos = reinterpret_cast<int *>(sv + kMaxK), *flag = pos + kMaxK;
     double *Tc = X, *Ec = X + size_t(k) * ld;  // staging; then X holds Z Rh^T
-    const double c0 = cut[0];
     const int r = rank[lp + 1];
     const int64_t p0 = int64_t(1) << lp;
     for (int64_t t = p0 + blockIdx.x; t < 2 * p0; t += gridDim.x) {
@@ -549,7 +555,7 @@ __global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const doub
         int count = 0;
         if (r > 0) {
             const int sw = jacobi_columns(X, ld, 2 * r, k, flag);
-            count = sort_columns(X, ld, 2 * r, k, sv, pos, Wb + slot * 2 * k * k, k, 2 * r, sig + t * k, c0);
+            count = sort_columns(X, ld, 2 * r, k, sv, pos, Wb + slot * 2 * k * k, k, 2 * r, sig + t * k, tau);
             if (threadIdx.x == 0) atomicAdd(sweeps, (unsigned long long)sw);
         } else {
             for (int j = threadIdx.x; j < k; j += kThreads) sig[t * k + j] = 0.0;
@@ -560,14 +566,20 @@ __global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const doub
 }
 
 // Parents at level lp, once rank[lp] = rp is known: E'_c1, E'_c2 = the two row blocks of the
-// first rp singular vectors; T_t = W^T Z (rp x k).
+// first rp singular vectors; T_t = W^T Z (rp x k); dropped energy as in k_leaf_t.
 __global__ void __launch_bounds__(kThreads) k_node_t(int lp, int k, const double *__restrict__ Zb,
                                                      const double *__restrict__ Wb, const int *__restrict__ rank,
-                                                     double *__restrict__ E2, double *__restrict__ T)
+                                                     double *__restrict__ E2, double *__restrict__ T,
+                                                     const double *__restrict__ sig, double *__restrict__ dropped)
 {
     const int r = rank[lp + 1], rp = rank[lp];
     const int64_t p0 = int64_t(1) << lp;
     for (int64_t t = p0 + blockIdx.x; t < 2 * p0; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            double d = 0.0;
+            for (int j = rp; j < k; ++j) d += sig[t * k + j] * sig[t * k + j];
+            atomicAdd(dropped, d);
+        }
         const int64_t slot = t - p0;
         const double *Zo = Zb + slot * 2 * k * k, *Wo = Wb + slot * 2 * k * k;
         for (int h = 0; h < 2; ++h) {

@@ -3,9 +3,10 @@
 // The four steps run level by level on one stream, every node or block of a level in its own
 // CTA (h2_cmpk.cuh): orthogonalization (leaf QR, the sibling-pair QR upsweep, S <- R S R^T),
 // the new-basis downsweep (Eq. for B_i^q, one QR update per stacked block), the truncation
-// upsweep (Jacobi SVDs; each level's rank is the largest count of singular values above the
-// cut over its nodes, decided on the device), and the projection S' = T_t S T_s^T. The result
-// is compacted to the largest level rank and copied into a new host operator.
+// upsweep (Jacobi SVDs; a node keeps the singular values above tau times its largest, and
+// each level's rank is the largest such count over its nodes, decided on the device), and the
+// projection S' = T_t S T_s^T. The result is compacted to the largest level rank and copied
+// into a new host operator.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -76,7 +77,7 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
     const size_t o_Zb = take(max_parents * 2 * kk * 8), o_Wb = take(max_parents * 2 * kk * 8);
     const size_t o_leaf = take((nleaves + 1) * 4), o_rp = take((nn + 2) * 8), o_brow = take(ncpl * 4),
                  o_bcol = take(ncpl * 4);
-    const size_t o_cut = take(16), o_rank = take(size_t(q + 1) * 4), o_sweeps = take(size_t(q + 1) * 8);
+    const size_t o_norm = take(16), o_rank = take(size_t(q + 1) * 4), o_sweeps = take(size_t(q + 1) * 8);
     char *arena = nullptr;
     if (cudaMalloc(&arena, off) != cudaSuccess) {
         cudaGetLastError();
@@ -85,7 +86,7 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
     auto D = [&](size_t o) { return reinterpret_cast<double *>(arena + o); };
     double *dU = D(o_U), *dE0 = D(o_E0), *dS = D(o_S), *dQ = D(o_Q), *dR = D(o_R), *dE1 = D(o_E1), *dRh = D(o_Rh),
            *dW = D(o_W), *dsig = D(o_sig), *dT = D(o_T), *dE2 = D(o_E2), *dZb = D(o_Zb), *dWb = D(o_Wb),
-           *dcut = D(o_cut);
+           *dnorm = D(o_norm);
     int32_t *dleaf = reinterpret_cast<int32_t *>(arena + o_leaf), *dbrow = reinterpret_cast<int32_t *>(arena + o_brow),
             *dbcol = reinterpret_cast<int32_t *>(arena + o_bcol);
     int64_t *drp = reinterpret_cast<int64_t *>(arena + o_rp);
@@ -118,6 +119,7 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
     zero(dE2, (nn + 1) * kk * 8);
     zero(drank, size_t(q + 1) * 4);
     zero(dsweeps, size_t(q + 1) * 8);
+    zero(dnorm, 16);
     if (rc == H2_OK) rc = h2_coupling_fp64(op, dS, st);
 
     using namespace h2c;
@@ -145,16 +147,17 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
         // 2. new-basis downsweep
         for (int l = 0; l <= q; ++l)
             k_down_qr<<<grid_for(int64_t(1) << l), kThreads, sm_dn, st>>>(l, k, drp, dS, dE1, dRh);
-        k_cut<<<1, kThreads, 0, st>>>(dRh, first, nleaves, k, tau, dcut);
+        k_norm<<<1, kThreads, 0, st>>>(dRh, first, nleaves, k, dnorm);
         cudaEventRecord(ev[2], st);
         // 3. truncation upsweep
-        k_leaf_svd<<<grid_for(nleaves), kThreads, sm_lsvd, st>>>(dQ, dleaf, nleaves, k, M, dRh, first, dcut, dW, dsig + first * k,
-                                                                 drank, q, dsweeps + q);
-        k_leaf_t<<<grid_for(nleaves), kThreads, 0, st>>>(dQ, dW, dleaf, nleaves, k, M, drank, q, first, dT);
+        k_leaf_svd<<<grid_for(nleaves), kThreads, sm_lsvd, st>>>(dQ, dleaf, nleaves, k, M, dRh, first, tau, dW,
+                                                                 dsig + first * k, drank, q, dsweeps + q);
+        k_leaf_t<<<grid_for(nleaves), kThreads, 0, st>>>(dQ, dW, dleaf, nleaves, k, M, drank, q, first, dT, dsig,
+                                                         dnorm + 1);
         for (int lp = q - 1; lp >= 0; --lp) {
-            k_node_svd<<<grid_for(int64_t(1) << lp), kThreads, sm_nsvd, st>>>(lp, k, dT, dE1, dRh, dcut, dZb, dWb, dsig,
+            k_node_svd<<<grid_for(int64_t(1) << lp), kThreads, sm_nsvd, st>>>(lp, k, dT, dE1, dRh, tau, dZb, dWb, dsig,
                                                                                drank, dsweeps + lp);
-            k_node_t<<<grid_for(int64_t(1) << lp), kThreads, 0, st>>>(lp, k, dZb, dWb, drank, dE2, dT);
+            k_node_t<<<grid_for(int64_t(1) << lp), kThreads, 0, st>>>(lp, k, dZb, dWb, drank, dE2, dT, dsig, dnorm + 1);
         }
         cudaEventRecord(ev[3], st);
         // 4. projection
@@ -164,10 +167,10 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
     }
     std::vector<int> ranks(q + 1, 0);
     std::vector<unsigned long long> sweeps(q + 1, 0);
-    double cut[2] = {0, 0};
+    double norms[2] = {0, 0};  // ||A_lr||_F, dropped energy
     if (rc == H2_OK) rc = cstat(cudaMemcpyAsync(ranks.data(), drank, size_t(q + 1) * 4, cudaMemcpyDeviceToHost, st));
     if (rc == H2_OK) rc = cstat(cudaMemcpyAsync(sweeps.data(), dsweeps, size_t(q + 1) * 8, cudaMemcpyDeviceToHost, st));
-    if (rc == H2_OK) rc = cstat(cudaMemcpyAsync(cut, dcut, 16, cudaMemcpyDeviceToHost, st));
+    if (rc == H2_OK) rc = cstat(cudaMemcpyAsync(norms, dnorm, 16, cudaMemcpyDeviceToHost, st));
     if (rc == H2_OK) rc = cstat(cudaStreamSynchronize(st));
     float ms[4] = {0, 0, 0, 0};
     if (rc == H2_OK)
@@ -237,8 +240,8 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->tau = tau;
-        info->cut = cut[0];
-        info->norm_lowrank = cut[1];
+        info->norm_lowrank = norms[0];
+        info->dropped_energy = norms[1];
         info->depth = q;
         info->rank_in = k;
         info->rank_out = kc;

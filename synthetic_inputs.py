@@ -114,7 +114,15 @@ def cloud3d(n: int, nv: int = 32) -> Workload:
     return dataclasses.replace(CLOUD3D_EXP, name=f"cloud3d_{n}", points=f"cloud:{n}:3:0", nv=nv)
 
 
-WORKLOADS = {w.name: w for w in (GRID64_EXP, GRID1024_GAUSS, CLOUD3D_EXP)}
+# The algebraic-compression sets of Sec. 6 (matrix compression): a 2D grid with a 6x6
+# Chebyshev grid (rank 36), exp(-r/0.1), leaf 64, eta 0.9 at N = 2^20; a 3D grid with
+# tri-cubic interpolation (rank 64), exp(-r/0.2), leaf 64, eta 0.95 at N = 2^18 (64^3). Both
+# are compressed to the relative tolerance COMPRESS_TAU.
+COMPRESS_2D = Workload("compress_grid2d_exp", "grid2d:1024", ("exp", 0.1, 0.0, 0), 64, 6, 0.9, 1, 1)
+COMPRESS_3D = Workload("compress_grid3d_exp", "grid3d:64", ("exp", 0.2, 0.0, 0), 64, 4, 0.95, 1, 1)
+COMPRESS_TAU = 1e-3
+
+WORKLOADS = {w.name: w for w in (GRID64_EXP, GRID1024_GAUSS, CLOUD3D_EXP, COMPRESS_2D, COMPRESS_3D)}
 
 
 @dataclasses.dataclass(frozen=True)
