@@ -226,7 +226,10 @@ int h2_load(const char *path, h2_handle *out);
  *      re-expressed in the orthogonal bases (S <- R_t S R_s^T);
  *   2. the new-basis downsweep: for every node the R factor of the stack of Eq. for B_i^q
  *      (the parent's factor times the transposed transfer, then the transposed blocks of the
- *      node's block row), folded one block at a time;
+ *      node's block row). For tau >= 1e-7 it is the Cholesky factor of the stack's Gram
+ *      matrix, accumulated block by block (FP64-lean; resolves a node's singular values down
+ *      to ~1e-8 of its largest, so results carry relative errors of order 1e-16 / tau); for
+ *      smaller tau each block is folded in by a QR update, as the paper writes it;
  *   3. the truncation upsweep: SVDs of the reweighted leaf bases and of the stacked
  *      projected transfers; of each node, the singular values above tau times its largest
  *      are kept (every block row keeps relative accuracy tau); each level keeps the largest

@@ -23,6 +23,7 @@ constexpr int kMaxK = 64;      // rank of the operator being compressed
 constexpr int kMaxRows = 128;  // points of a leaf; rows of a sibling pair's stack (2k)
 constexpr int kMaxSweeps = 40;
 constexpr double kJacobiTol = 1e-14;  // rotate while |a_p . a_q| > tol * |a_p| |a_q|
+constexpr double kGramMinTau = 1e-7;  // the downsweep takes the Gram route for tau >= this
 
 // Shared-memory bytes of each kernel (ld = k + 1 doubles per matrix row).
 __host__ __device__ constexpr size_t mat_bytes(int rows, int k) { return size_t(rows) * (k + 1) * 8; }
@@ -31,6 +32,7 @@ __host__ __device__ constexpr size_t smem_leaf_qr(int M, int k) { return 2 * mat
 __host__ __device__ constexpr size_t smem_transfer_qr(int k) { return 2 * mat_bytes(2 * k, k) + scratch_bytes(); }
 __host__ __device__ constexpr size_t smem_sandwich(int k) { return 4 * mat_bytes(k, k) + scratch_bytes(); }
 __host__ __device__ constexpr size_t smem_down(int k) { return 4 * mat_bytes(k, k) + scratch_bytes(); }
+__host__ __device__ constexpr size_t smem_down_gram(int k) { return 3 * mat_bytes(k, k) + scratch_bytes(); }
 __host__ __device__ constexpr size_t smem_leaf_svd(int M, int k) { return 2 * mat_bytes(M, k) + mat_bytes(k, k) + scratch_bytes(); }
 __host__ __device__ constexpr size_t smem_node_svd(int k) { return 2 * mat_bytes(2 * k, k) + mat_bytes(k, k) + scratch_bytes(); }
 
@@ -420,16 +422,136 @@ __global__ void __launch_bounds__(kThreads) k_down_qr(int l, int k, const int64_
     }
 }
 
-// ||A_lr||_F^2 = sum over leaves of ||Rh_t||_F^2 (A_lr the low-rank part), summed in a fixed
-// order by one CTA into norm[0] (a check of the downsweep; the cut is relative per node).
-__global__ void __launch_bounds__(kThreads) k_norm(const double *__restrict__ Rh, int64_t first, int64_t nleaves, int k,
-                                                   double *__restrict__ norm)
+// The same factors through their Gram matrices: only Rh_i^T Rh_i = B_i^T B_i enters the
+// truncation (the left singular vectors and values of U_i Rh_i^T), and
+//   G_i = B_i^T B_i = E1_i G_{i+} E1_i^T + sum_j S_ij S_ij^T
+// accumulates with every lane on a product term, where the QR update spends most of its
+// FP64 instructions on reductions. Rh_i is then the transposed Cholesky factor of G_i
+// (columns whose pivot falls under k * eps * max diag are set to zero: G_i is semidefinite).
+// Squaring the data limits what is resolved to singular values above ~1e-8 of a node's
+// largest. Nodes of level l; Gout keeps G_i for the next level.
+constexpr int kMaxOut = (kMaxK * (kMaxK + 1) / 2 + kThreads - 1) / kThreads;  // lower-triangle outputs per thread
+
+__device__ __forceinline__ void tri_index(int idx, int &a, int &b)
+{
+    a = int((sqrtf(8.0f * float(idx) + 1.0f) - 1.0f) * 0.5f);
+    while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+    while (a * (a + 1) / 2 > idx) --a;
+    b = idx - a * (a + 1) / 2;
+}
+
+__global__ void __launch_bounds__(kThreads) k_down_gram(int l, int k, const int64_t *__restrict__ rowptr,
+                                                        const double *__restrict__ S, const double *__restrict__ E1,
+                                                        double *__restrict__ Gout, double *__restrict__ Rh)
+{
+    extern __shared__ double sm[];
+    const int ld = k + 1;
+    Carve cv{sm};
+    double *B0 = cv.take(k, k), *B1 = cv.take(k, k), *X = cv.take(k, k), *red = cv.p;
+    const int np = k * (k + 1) / 2;
+    int oa[kMaxOut], ob[kMaxOut];
+#pragma unroll
+    for (int u = 0; u < kMaxOut; ++u) {
+        const int idx = threadIdx.x + u * kThreads;
+        if (idx < np) tri_index(idx, oa[u], ob[u]);
+        else oa[u] = ob[u] = 0;
+    }
+    const int64_t n0 = int64_t(1) << l;
+    for (int64_t i = n0 + blockIdx.x; i < 2 * n0; i += gridDim.x) {
+        double acc[kMaxOut];
+#pragma unroll
+        for (int u = 0; u < kMaxOut; ++u) acc[u] = 0.0;
+        if (i > 1) {  // E1_i G_p E1_i^T
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+                B0[(idx / k) * ld + idx % k] = Gout[(i / 2) * k * k + idx];
+                B1[(idx / k) * ld + idx % k] = E1[i * k * k + idx];
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {  // X = E1_i G_p
+                const int a = idx / k, c = idx % k;
+                double v = 0.0;
+                for (int m = 0; m < k; ++m) v += B1[a * ld + m] * B0[m * ld + c];
+                X[a * ld + c] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kMaxOut; ++u)
+                if (threadIdx.x + u * kThreads < np) {
+                    const double *xa = X + oa[u] * ld, *eb = B1 + ob[u] * ld;
+                    double v = 0.0;
+                    for (int m = 0; m < k; ++m) v += xa[m] * eb[m];
+                    acc[u] = v;
+                }
+            __syncthreads();
+        }
+        for (int64_t b = rowptr[i]; b < rowptr[i + 1]; ++b) {  // + S_ij S_ij^T
+            for (int idx = threadIdx.x; idx < k * k; idx += kThreads) B0[(idx / k) * ld + idx % k] = S[b * k * k + idx];
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kMaxOut; ++u)
+                if (threadIdx.x + u * kThreads < np) {
+                    const double *sa = B0 + oa[u] * ld, *sb = B0 + ob[u] * ld;
+                    double v = 0.0;
+                    for (int m = 0; m < k; ++m) v += sa[m] * sb[m];
+                    acc[u] += v;
+                }
+            __syncthreads();
+        }
+        // G_i (full, symmetric) to global and shared memory
+#pragma unroll
+        for (int u = 0; u < kMaxOut; ++u)
+            if (threadIdx.x + u * kThreads < np) {
+                const int a = oa[u], c = ob[u];
+                Gout[i * k * k + a * k + c] = acc[u];
+                Gout[i * k * k + c * k + a] = acc[u];
+                X[a * ld + c] = acc[u];
+                X[c * ld + a] = acc[u];
+            }
+        __syncthreads();
+        // Cholesky G = L L^T in place (lower triangle of X), columns in order
+        if (threadIdx.x == 0) {
+            double dmax = 0.0;
+            for (int j = 0; j < k; ++j) dmax = fmax(dmax, X[j * ld + j]);
+            red[0] = double(k) * 2.220446049250313e-16 * dmax;
+        }
+        __syncthreads();
+        const double delta = red[0];
+        for (int j = 0; j < k; ++j) {
+            const double d = X[j * ld + j];
+            const double piv = d > delta ? sqrt(d) : 0.0;
+            const double inv = piv > 0.0 ? 1.0 / piv : 0.0;
+            __syncthreads();
+            for (int r = j + threadIdx.x; r < k; r += kThreads) X[r * ld + j] = r == j ? piv : X[r * ld + j] * inv;
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < (k - j - 1) * (k - j - 1); idx += kThreads) {
+                const int r = j + 1 + idx / (k - j - 1), c = j + 1 + idx % (k - j - 1);
+                if (c <= r) X[r * ld + c] -= X[r * ld + j] * X[c * ld + j];
+            }
+            __syncthreads();
+        }
+        double *Ro = Rh + i * k * k;  // Rh = L^T
+        for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {
+            const int a = idx / k, c = idx % k;
+            Ro[idx] = c >= a ? X[c * ld + a] : 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// ||A_lr||_F^2 = sum over leaves of trace(G_t) = ||Rh_t||_F^2 (A_lr the low-rank part), summed
+// in a fixed order by one CTA into norm[0] (a check of the downsweep).
+// gram: G holds the Gram matrices (sum of the diagonals), else the R factors (sum of squares).
+__global__ void __launch_bounds__(kThreads) k_norm(const double *__restrict__ G, int64_t first, int64_t nleaves, int k,
+                                                   bool gram, double *__restrict__ norm)
 {
     __shared__ double part[kThreads];
     double s = 0.0;
-    const int64_t n = nleaves * k * k;
-    const double *base = Rh + first * k * k;
-    for (int64_t i = threadIdx.x; i < n; i += kThreads) s += base[i] * base[i];
+    const double *base = G + first * k * k;
+    if (gram) {
+        for (int64_t i = threadIdx.x; i < nleaves * k; i += kThreads) s += base[(i / k) * k * k + (i % k) * (k + 1)];
+    } else {
+        for (int64_t i = threadIdx.x; i < nleaves * k * k; i += kThreads) s += base[i] * base[i];
+    }
     part[threadIdx.x] = s;
     __syncthreads();
     for (int w = kThreads / 2; w; w >>= 1) {

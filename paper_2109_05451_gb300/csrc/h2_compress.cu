@@ -72,7 +72,8 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
     const int64_t max_parents = std::max<int64_t>(1, nleaves / 2);
     const size_t o_U = take(size_t(op.n) * k * 8), o_E0 = take((nn + 1) * kk * 8), o_S = take(ncpl * kk * 8);
     const size_t o_Q = take(size_t(nleaves) * M * k * 8), o_R = take((nn + 1) * kk * 8), o_E1 = take((nn + 1) * kk * 8);
-    const size_t o_Rh = take((nn + 1) * kk * 8), o_W = take(size_t(nleaves) * M * k * 8);
+    const bool gram_route = tau >= h2c::kGramMinTau;
+    const size_t o_Rh = take((nn + 1) * kk * 8), o_G = take(gram_route ? (nn + 1) * kk * 8 : 0), o_W = take(size_t(nleaves) * M * k * 8);
     const size_t o_sig = take((nn + 1) * k * 8), o_T = take((nn + 1) * kk * 8), o_E2 = take((nn + 1) * kk * 8);
     const size_t o_Zb = take(max_parents * 2 * kk * 8), o_Wb = take(max_parents * 2 * kk * 8);
     const size_t o_leaf = take((nleaves + 1) * 4), o_rp = take((nn + 2) * 8), o_brow = take(ncpl * 4),
@@ -84,7 +85,7 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
         return H2_ENOMEM;
     }
     auto D = [&](size_t o) { return reinterpret_cast<double *>(arena + o); };
-    double *dU = D(o_U), *dE0 = D(o_E0), *dS = D(o_S), *dQ = D(o_Q), *dR = D(o_R), *dE1 = D(o_E1), *dRh = D(o_Rh),
+    double *dU = D(o_U), *dE0 = D(o_E0), *dS = D(o_S), *dQ = D(o_Q), *dR = D(o_R), *dE1 = D(o_E1), *dRh = D(o_Rh), *dG = D(o_G),
            *dW = D(o_W), *dsig = D(o_sig), *dT = D(o_T), *dE2 = D(o_E2), *dZb = D(o_Zb), *dWb = D(o_Wb),
            *dnorm = D(o_norm);
     int32_t *dleaf = reinterpret_cast<int32_t *>(arena + o_leaf), *dbrow = reinterpret_cast<int32_t *>(arena + o_brow),
@@ -124,11 +125,13 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
 
     using namespace h2c;
     const size_t sm_lqr = smem_leaf_qr(M, k), sm_tqr = smem_transfer_qr(k), sm_sw = smem_sandwich(k),
-                 sm_dn = smem_down(k), sm_lsvd = smem_leaf_svd(M, k), sm_nsvd = smem_node_svd(k);
+                 sm_dn = smem_down_gram(k), sm_dq = smem_down(k), sm_lsvd = smem_leaf_svd(M, k), sm_nsvd = smem_node_svd(k);
     if (rc == H2_OK) rc = allow_smem(k_leaf_qr, sm_lqr);
     if (rc == H2_OK) rc = allow_smem(k_transfer_qr, sm_tqr);
     if (rc == H2_OK) rc = allow_smem(k_orth_blocks, sm_sw);
-    if (rc == H2_OK) rc = allow_smem(k_down_qr, sm_dn);
+    if (rc == H2_OK) rc = allow_smem(k_down_gram, sm_dn);
+    if (rc == H2_OK) rc = allow_smem(k_down_qr, sm_dq);
+    const bool gram = tau >= kGramMinTau;
     if (rc == H2_OK) rc = allow_smem(k_leaf_svd, sm_lsvd);
     if (rc == H2_OK) rc = allow_smem(k_node_svd, sm_nsvd);
     if (rc == H2_OK) rc = allow_smem(k_project, sm_sw);
@@ -145,9 +148,15 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
         if (ncpl > 0) k_orth_blocks<<<grid_for(ncpl, 65535), kThreads, sm_sw, st>>>(dS, dbrow, dbcol, ncpl, dR, k);
         cudaEventRecord(ev[1], st);
         // 2. new-basis downsweep
-        for (int l = 0; l <= q; ++l)
-            k_down_qr<<<grid_for(int64_t(1) << l), kThreads, sm_dn, st>>>(l, k, drp, dS, dE1, dRh);
-        k_norm<<<1, kThreads, 0, st>>>(dRh, first, nleaves, k, dnorm);
+        // Gram route for tolerances it resolves (singular values down to ~1e-8 of a node's
+        // largest), else the QR updates of the stacked block rows as the paper writes them
+        for (int l = 0; l <= q; ++l) {
+            if (gram)
+                k_down_gram<<<grid_for(int64_t(1) << l), kThreads, sm_dn, st>>>(l, k, drp, dS, dE1, dG, dRh);
+            else
+                k_down_qr<<<grid_for(int64_t(1) << l), kThreads, sm_dq, st>>>(l, k, drp, dS, dE1, dRh);
+        }
+        k_norm<<<1, kThreads, 0, st>>>(gram ? dG : dRh, first, nleaves, k, gram, dnorm);
         cudaEventRecord(ev[2], st);
         // 3. truncation upsweep
         k_leaf_svd<<<grid_for(nleaves), kThreads, sm_lsvd, st>>>(dQ, dleaf, nleaves, k, M, dRh, first, tau, dW,
