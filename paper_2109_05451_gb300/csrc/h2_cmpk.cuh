@@ -27,14 +27,20 @@ constexpr double kGramMinTau = 1e-7;  // the downsweep takes the Gram route for 
 
 // Shared-memory bytes of each kernel (ld = k + 1 doubles per matrix row).
 __host__ __device__ constexpr size_t mat_bytes(int rows, int k) { return size_t(rows) * (k + 1) * 8; }
-__host__ __device__ constexpr size_t scratch_bytes() { return size_t(2 * kMaxK + 8) * 8 + 4 * 8; }
+__host__ __device__ constexpr size_t scratch_bytes() { return size_t(4 * kMaxK + 16) * 8; }
 __host__ __device__ constexpr size_t smem_leaf_qr(int M, int k) { return 2 * mat_bytes(M, k) + scratch_bytes(); }
 __host__ __device__ constexpr size_t smem_transfer_qr(int k) { return 2 * mat_bytes(2 * k, k) + scratch_bytes(); }
 __host__ __device__ constexpr size_t smem_sandwich(int k) { return 4 * mat_bytes(k, k) + scratch_bytes(); }
 __host__ __device__ constexpr size_t smem_down(int k) { return 4 * mat_bytes(k, k) + scratch_bytes(); }
 __host__ __device__ constexpr size_t smem_down_gram(int k) { return 3 * mat_bytes(k, k) + scratch_bytes(); }
-__host__ __device__ constexpr size_t smem_leaf_svd(int M, int k) { return 2 * mat_bytes(M, k) + mat_bytes(k, k) + scratch_bytes(); }
-__host__ __device__ constexpr size_t smem_node_svd(int k) { return 2 * mat_bytes(2 * k, k) + mat_bytes(k, k) + scratch_bytes(); }
+// leaf SVD: A (max(M, k): Rh^T rows, then the leaf's Q), B (k: A32 + V32, then the result),
+// V64 (k), Vq (k: then W')
+__host__ __device__ constexpr size_t smem_leaf_svd(int M, int k)
+{
+    return mat_bytes(M > k ? M : k, k) + 3 * mat_bytes(k, k) + scratch_bytes();
+}
+// node SVD: Z (2k: then A32 + V32, then the result), X (2k), Rh / V64 (k), Vq (k)
+__host__ __device__ constexpr size_t smem_node_svd(int k) { return 2 * mat_bytes(2 * k, k) + 2 * mat_bytes(k, k) + scratch_bytes(); }
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -161,16 +167,30 @@ __device__ void qr_fold(double *R, double *B, int ld, int k, double *red)
     }
 }
 
-// One-sided Jacobi on the columns of A (rows x cols, shared memory) until every pair is
-// orthogonal to kJacobiTol (at most kMaxSweeps sweeps). Returns the sweeps taken.
-// flag: one int of shared memory.
-__device__ int jacobi_columns(double *A, int ld, int rows, int cols, int *flag)
+template <typename T>
+__device__ __forceinline__ T group8_sum_t(T v)
+{
+#pragma unroll
+    for (int o = 4; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One-sided (Hestenes) Jacobi on the columns of A (rows x cols, shared memory, leading
+// dimension lda): sweeps of round-robin pairs until every pair is orthogonal to tol
+// (|a_p . a_q| <= tol |a_p| |a_q|) or max_sweeps. Columns whose squared norm is under null2
+// are left alone (the numerical null space of a rank-deficient A would otherwise keep
+// rotating). With V (cols x cols, leading dimension ldv) the rotations are accumulated,
+// V <- V J. 8 threads per pair. Returns the sweeps taken. flag: one int of shared memory.
+template <typename T>
+__device__ int jacobi_columns(T *A, int lda, int rows, int cols, T *V, int ldv, T tol, T null2, int max_sweeps,
+                              int *flag)
 {
     const int n2 = cols + (cols & 1);  // an odd column count plays against an absent column
     const int npairs = n2 / 2;
     const int g = threadIdx.x / 8, gl = threadIdx.x % 8;
+    const T tol2 = tol * tol, huge = sizeof(T) == 8 ? T(1e150) : T(1e18);
     int sweep = 0;
-    for (; sweep < kMaxSweeps; ++sweep) {
+    for (; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) *flag = 0;
         __syncthreads();
         for (int r = 0; r < n2 - 1; ++r) {
@@ -189,27 +209,33 @@ __device__ int jacobi_columns(double *A, int ld, int rows, int cols, int *flag)
             }
             // every lane takes part in the group reductions (shuffles need the whole warp)
             const bool active = g < npairs && q < cols;
-            double al = 0.0, be = 0.0, ga = 0.0;
+            T al = 0, be = 0, ga = 0;
             if (active)
                 for (int i = gl; i < rows; i += 8) {
-                    const double x = A[i * ld + p], y = A[i * ld + q];
+                    const T x = A[i * lda + p], y = A[i * lda + q];
                     al += x * x;
                     be += y * y;
                     ga += x * y;
                 }
-            al = group8_sum(al);
-            be = group8_sum(be);
-            ga = group8_sum(ga);
-            if (active && al > 0.0 && be > 0.0 && fabs(ga) > kJacobiTol * sqrt(al) * sqrt(be)) {
-                const double zeta = (be - al) / (2.0 * ga);
-                const double az = fabs(zeta);  // zeta^2 would overflow above ~1e154
-                const double t = az > 1e150 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+            al = group8_sum_t(al);
+            be = group8_sum_t(be);
+            ga = group8_sum_t(ga);
+            if (active && al > null2 && be > null2 && ga * ga > tol2 * al * be) {
+                const T zeta = (be - al) / (T(2) * ga);
+                const T az = fabs(zeta);  // zeta^2 would overflow
+                const T t = az > huge ? T(0.5) / zeta : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
+                const T c = rsqrt(T(1) + t * t), s = c * t;
                 for (int i = gl; i < rows; i += 8) {
-                    const double x = A[i * ld + p], y = A[i * ld + q];
-                    A[i * ld + p] = c * x - s * y;
-                    A[i * ld + q] = s * x + c * y;
+                    const T x = A[i * lda + p], y = A[i * lda + q];
+                    A[i * lda + p] = c * x - s * y;
+                    A[i * lda + q] = s * x + c * y;
                 }
+                if (V)
+                    for (int i = gl; i < cols; i += 8) {
+                        const T x = V[i * ldv + p], y = V[i * ldv + q];
+                        V[i * ldv + p] = c * x - s * y;
+                        V[i * ldv + q] = s * x + c * y;
+                    }
                 if (gl == 0) *flag = 1;
             }
             __syncthreads();
@@ -221,12 +247,80 @@ __device__ int jacobi_columns(double *A, int ld, int rows, int cols, int *flag)
     return sweep + 1;
 }
 
+// Relative size under which a singular vector is taken as numerical null space: far below
+// any cut tau * sigma_1 the truncation can make (and the rounding level for tau = 0).
+__device__ __forceinline__ double null_floor(double tau) { return tau > 0.0 ? fmin(1e-10, 1e-2 * tau) : 1e-13; }
+
+// SVD of A (rows x cols, FP64, shared memory) by one-sided Jacobi in two precisions: sweeps
+// on an FP32 copy (scaled to unit largest entry) accumulate the rotations in V32; V32, made
+// orthogonal again in FP64 by a Householder QR, is applied to A (into B, rows x cols, which
+// becomes the result); FP64 sweeps from there need one to three passes instead of about ten,
+// and every FP64 rotation costs 64x an FP32 one on this part. A32 and V32 share the region
+// f32 (rows + cols) * ld floats; V64 and Vq are cols x ld doubles. Columns under
+// floor_rel * |A|_F are the numerical null space: the FP64 sweeps leave them alone. Returns
+// the FP64 sweeps; the result's columns are in B, and scr[kMaxK + 1] holds |A|_F^2.
+__device__ int svd_columns_mixed(const double *A, double *B, int ld, int rows, int cols, float *f32, double *V64,
+                                 double *Vq, double *scr, double floor_rel, int *flag)
+{
+    float *A32 = f32, *V32 = f32 + size_t(rows) * ld;
+    double *tau = scr, *red = scr + kMaxK;
+    // scale: the largest magnitude (rotations do not depend on it); the squared Frobenius
+    // norm sets the null-column threshold
+    if (threadIdx.x == 0) red[0] = red[1] = 0.0;
+    __syncthreads();
+    {
+        double m = 0.0, f = 0.0;
+        for (int idx = threadIdx.x; idx < rows * cols; idx += kThreads) {
+            const double v = A[(idx / cols) * ld + idx % cols];
+            m = fmax(m, fabs(v));
+            f += v * v;
+        }
+        for (int o = 16; o; o >>= 1) {
+            m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            f += __shfl_xor_sync(0xffffffffu, f, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(reinterpret_cast<unsigned long long *>(red), __double_as_longlong(m));
+            atomicAdd(red + 1, f);
+        }
+    }
+    __syncthreads();
+    const double mx = red[0], fro2 = red[1], inv = mx > 0.0 ? 1.0 / mx : 0.0;
+    for (int idx = threadIdx.x; idx < rows * cols; idx += kThreads) {
+        const int i = idx / cols, j = idx % cols;
+        A32[i * ld + j] = float(A[i * ld + j] * inv);
+    }
+    for (int idx = threadIdx.x; idx < cols * cols; idx += kThreads) {
+        const int i = idx / cols, j = idx % cols;
+        V32[i * ld + j] = i == j ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    jacobi_columns<float>(A32, ld, rows, cols, V32, ld, 1e-5f, float(1e-12 * fro2 * inv * inv), 20, flag);
+    for (int idx = threadIdx.x; idx < cols * cols; idx += kThreads) {
+        const int i = idx / cols, j = idx % cols;
+        V64[i * ld + j] = double(V32[i * ld + j]);
+    }
+    __syncthreads();
+    house_qr(V64, ld, cols, cols, tau, red + 2);  // (red[1] = |A|_F^2 stays for the caller)
+    house_form_q(V64, ld, cols, cols, tau, Vq, ld);
+    for (int idx = threadIdx.x; idx < rows * cols; idx += kThreads) {  // B = A Vq
+        const int i = idx / cols, j = idx % cols;
+        double v = 0.0;
+        for (int m = 0; m < cols; ++m) v += A[i * ld + m] * Vq[m * ld + j];
+        B[i * ld + j] = v;
+    }
+    __syncthreads();
+    return jacobi_columns<double>(B, ld, rows, cols, nullptr, 0, kJacobiTol, floor_rel * floor_rel * fro2, kMaxSweeps,
+                                  flag);
+}
+
 // After jacobi_columns: the singular values (column norms) in descending order into sig[],
 // the normalized columns in that order into W (rows x cols, global, leading dimension ldw),
-// and the count of singular values above tau times the largest. sv, pos: cols doubles /
-// ints of scratch.
+// and the count of singular values above tau times the largest. Columns under floor_abs
+// (the numerical null space, left out of the Jacobi sweeps) are neither normalized nor
+// counted, and at most min(rows, cols) are. sv, pos: cols doubles / ints of scratch.
 __device__ int sort_columns(const double *A, int ld, int rows, int cols, double *sv, int *pos, double *W, int ldw,
-                            int wrows, double *sig, double tau)
+                            int wrows, double *sig, double tau, double floor_abs)
 {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int j = warp; j < cols; j += kWarps) {
@@ -242,17 +336,19 @@ __device__ int sort_columns(const double *A, int ld, int rows, int cols, double 
         pos[j] = r;
     }
     __syncthreads();
+    double smax = 0.0;
+    for (int j = 0; j < cols; ++j) smax = fmax(smax, sv[j]);
+    const double floor_ = fmax(floor_abs, 1e-13 * smax);
     for (int idx = threadIdx.x; idx < wrows * cols; idx += kThreads) {
         const int i = idx / cols, j = idx % cols;
         const double s = sv[j];
-        W[int64_t(i) * ldw + pos[j]] = (i < rows && s > 0.0) ? A[i * ld + j] / s : 0.0;
+        W[int64_t(i) * ldw + pos[j]] = (i < rows && s > floor_) ? A[i * ld + j] / s : 0.0;
     }
     for (int j = threadIdx.x; j < cols; j += kThreads) sig[pos[j]] = sv[j];
-    double smax = 0.0;
-    for (int j = 0; j < cols; ++j) smax = fmax(smax, sv[j]);
     int count = 0;
     if (smax > 0.0)
-        for (int j = 0; j < cols; ++j) count += sv[j] > tau * smax;
+        for (int j = 0; j < cols; ++j) count += sv[j] > fmax(tau * smax, floor_);
+    count = min(count, min(rows, cols));
     __syncthreads();
     return count;
 }
@@ -563,9 +659,12 @@ __global__ void __launch_bounds__(kThreads) k_norm(const double *__restrict__ G,
 
 // ---------------------------------------------------------------- 3. truncation upsweep
 
-// Leaves: SVD of the reweighted basis Q_t Rh_t^T (rows x k). W: per leaf an M x k slab of
-// left singular vectors by descending singular value; sig: k per leaf; the count above tau
-// times the largest raises rank[q].
+// Leaves: SVD of the reweighted basis Q_t Rh_t^T (rows x k). Q_t has orthonormal columns
+// (then zero columns from p = min(rows, k) on), so its left singular vectors are Q_t W' with
+// W' those of the p x k matrix Rh_t^T[0:p, :], which the Jacobi sweeps take instead (k rows
+// instead of the leaf's points). W: per leaf an M x k slab of left singular vectors by
+// descending singular value; sig: k per leaf; the count above tau times the largest raises
+// rank[q].
 __global__ void __launch_bounds__(kThreads) k_leaf_svd(const double *__restrict__ Q, const int32_t *__restrict__ leaf_lo,
                                                        int64_t nleaves, int k, int M, const double *__restrict__ Rh,
                                                        int64_t first, double tau,
@@ -575,28 +674,36 @@ __global__ void __launch_bounds__(kThreads) k_leaf_svd(const double *__restrict_
     extern __shared__ double sm[];
     const int ld = k + 1;
     Carve cv{sm};
-    double *A = cv.take(M, k), *Qs = cv.take(M, k), *Rs = cv.take(k, k), *sv = cv.p;
+    double *A = cv.take(M > k ? M : k, k), *B = cv.take(k, k), *Rs = cv.take(k, k), *Vq = cv.take(k, k);
+    double *sv = cv.p, *qscr = sv + 2 * kMaxK;
     int *pos = reinterpret_cast<int *>(sv + kMaxK), *flag = pos + kMaxK;
+    const double floor_rel = null_floor(tau);
     for (int64_t t = blockIdx.x; t < nleaves; t += gridDim.x) {
-        const int rows = leaf_lo[t + 1] - leaf_lo[t];
-        const double *Qt = Q + t * int64_t(M) * k;
-        for (int idx = threadIdx.x; idx < rows * k; idx += kThreads) Qs[(idx / k) * ld + idx % k] = Qt[idx];
-        for (int idx = threadIdx.x; idx < k * k; idx += kThreads)
-            Rs[(idx / k) * ld + idx % k] = Rh[(first + t) * k * k + idx];
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < rows * k; idx += kThreads) {  // A = Q Rh^T
+        const int rows = leaf_lo[t + 1] - leaf_lo[t], p = rows < k ? rows : k;
+        for (int idx = threadIdx.x; idx < p * k; idx += kThreads) {  // A = Rh^T[0:p, :]
             const int i = idx / k, j = idx % k;
-            double v = 0.0;
-            for (int m = j; m < k; ++m) v += Qs[i * ld + m] * Rs[j * ld + m];
-            A[i * ld + j] = v;
+            A[i * ld + j] = Rh[(first + t) * k * k + j * k + i];
         }
         __syncthreads();
-        const int sw = jacobi_columns(A, ld, rows, k, flag);
-        const int count = sort_columns(A, ld, rows, k, sv, pos, W + t * int64_t(M) * k, k, M, sig + t * k, tau);
+        const int sw = svd_columns_mixed(A, B, ld, p, k, reinterpret_cast<float *>(B), Rs, Vq, qscr, floor_rel, flag);
+        const int count = sort_columns(B, ld, p, k, sv, pos, Vq, ld, p, sig + t * k, tau,
+                                       floor_rel * sqrt(qscr[kMaxK + 1]));
+        const double *Qt = Q + t * int64_t(M) * k;  // W = Q[:, 0:p] W'
+        for (int idx = threadIdx.x; idx < rows * k; idx += kThreads) A[(idx / k) * ld + idx % k] = Qt[idx];
+        __syncthreads();
+        double *Wt = W + t * int64_t(M) * k;
+        for (int idx = threadIdx.x; idx < M * k; idx += kThreads) {
+            const int i = idx / k, j = idx % k;
+            double v = 0.0;
+            if (i < rows)
+                for (int m = 0; m < p; ++m) v += A[i * ld + m] * Vq[m * ld + j];
+            Wt[idx] = v;
+        }
         if (threadIdx.x == 0) {
             atomicMax(rank + q, count);
             atomicAdd(sweeps, (unsigned long long)sw);
         }
+        __syncthreads();
     }
 }
 
@@ -640,10 +747,12 @@ __global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const doub
     extern __shared__ double sm[];
     const int ld = k + 1;
     Carve cv{sm};
-    double *Z = cv.take(2 * k, k), *X = cv.take(2 * k, k), *Rs = cv.take(k, k), *sv = cv.p;
+    double *Z = cv.take(2 * k, k), *X = cv.take(2 * k, k), *Rs = cv.take(k, k), *Vq = cv.take(k, k);
+    double *sv = cv.p, *qscr = sv + 2 * kMaxK;
     int *pos = reinterpret_cast<int *>(sv + kMaxK), *flag = pos + kMaxK;
     double *Tc = X, *Ec = X + size_t(k) * ld;  // staging; then X holds Z Rh^T
     const int r = rank[lp + 1];
+    const double floor_rel = null_floor(tau);
     const int64_t p0 = int64_t(1) << lp;
     for (int64_t t = p0 + blockIdx.x; t < 2 * p0; t += gridDim.x) {
         const int64_t slot = t - p0;
@@ -676,8 +785,10 @@ __global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const doub
         __syncthreads();
         int count = 0;
         if (r > 0) {
-            const int sw = jacobi_columns(X, ld, 2 * r, k, flag);
-            count = sort_columns(X, ld, 2 * r, k, sv, pos, Wb + slot * 2 * k * k, k, 2 * r, sig + t * k, tau);
+            const int sw = svd_columns_mixed(X, Z, ld, 2 * r, k, reinterpret_cast<float *>(Z), Rs, Vq, qscr, floor_rel,
+                                             flag);
+            count = sort_columns(Z, ld, 2 * r, k, sv, pos, Wb + slot * 2 * k * k, k, 2 * r, sig + t * k, tau,
+                                 floor_rel * sqrt(qscr[kMaxK + 1]));
             if (threadIdx.x == 0) atomicAdd(sweeps, (unsigned long long)sw);
         } else {
             for (int j = threadIdx.x; j < k; j += kThreads) sig[t * k + j] = 0.0;
