@@ -24,6 +24,7 @@ constexpr int kMaxRows = 128;  // points of a leaf; rows of a sibling pair's sta
 constexpr int kMaxSweeps = 40;
 constexpr double kJacobiTol = 1e-14;  // rotate while |a_p . a_q| > tol * |a_p| |a_q|
 constexpr double kGramMinTau = 1e-7;  // the downsweep takes the Gram route for tau >= this
+constexpr double kJacobiQuad = 1e-9;  // a sweep whose pairs were all this orthogonal ends the FP64 sweeps
 
 // Shared-memory bytes of each kernel (ld = k + 1 doubles per matrix row).
 __host__ __device__ constexpr size_t mat_bytes(int rows, int k) { return size_t(rows) * (k + 1) * 8; }
@@ -167,82 +168,91 @@ __device__ void qr_fold(double *R, double *B, int ld, int k, double *red)
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T group8_sum_t(T v)
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v)
 {
 #pragma unroll
-    for (int o = 4; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
 // One-sided (Hestenes) Jacobi on the columns of A (rows x cols, shared memory, leading
-// dimension lda): sweeps of round-robin pairs until every pair is orthogonal to tol
-// (|a_p . a_q| <= tol |a_p| |a_q|) or max_sweeps. Columns whose squared norm is under null2
-// are left alone (the numerical null space of a rank-deficient A would otherwise keep
-// rotating). With V (cols x cols, leading dimension ldv) the rotations are accumulated,
-// V <- V J. 8 threads per pair. Returns the sweeps taken. flag: one int of shared memory.
-template <typename T>
-__device__ int jacobi_columns(T *A, int lda, int rows, int cols, T *V, int ldv, T tol, T null2, int max_sweeps,
+// dimension lda): sweeps of round-robin pairs, G threads per pair, until every pair is
+// orthogonal to tol (|a_p . a_q| <= tol |a_p| |a_q|), or until a sweep's largest relative
+// |a_p . a_q| was under quad (convergence is quadratic from there: the next sweep would find
+// every pair below tol), or max_sweeps. Columns whose squared norm is under null2 are left
+// alone (the numerical null space of a rank-deficient A would otherwise keep rotating). With V
+// (cols x cols, leading dimension ldv) the rotations are accumulated, V <- V J. Returns the
+// sweeps taken. flag: two ints of shared memory.
+template <int G, typename T>
+__device__ int jacobi_columns(T *A, int lda, int rows, int cols, T *V, int ldv, T tol, T quad, T null2, int max_sweeps,
                               int *flag)
 {
     const int n2 = cols + (cols & 1);  // an odd column count plays against an absent column
     const int npairs = n2 / 2;
-    const int g = threadIdx.x / 8, gl = threadIdx.x % 8;
+    const int g = threadIdx.x / G, gl = threadIdx.x % G;
+    const bool warp_busy = (threadIdx.x / 32) * (32 / G) < npairs;  // uniform over the warp
     const T tol2 = tol * tol, huge = sizeof(T) == 8 ? T(1e150) : T(1e18);
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) *flag = 0;
+        if (threadIdx.x == 0) flag[0] = flag[1] = 0;
         __syncthreads();
         for (int r = 0; r < n2 - 1; ++r) {
-            int p, q;
-            if (g == 0) {
-                p = r;
-                q = n2 - 1;
-            } else {
-                p = (r + g) % (n2 - 1);
-                q = (r - g + n2 - 1) % (n2 - 1);
-            }
-            if (p > q) {
-                const int tmp = p;
-                p = q;
-                q = tmp;
-            }
-            // every lane takes part in the group reductions (shuffles need the whole warp)
-            const bool active = g < npairs && q < cols;
-            T al = 0, be = 0, ga = 0;
-            if (active)
-                for (int i = gl; i < rows; i += 8) {
-                    const T x = A[i * lda + p], y = A[i * lda + q];
-                    al += x * x;
-                    be += y * y;
-                    ga += x * y;
+            if (warp_busy) {
+                int p, q;
+                if (g == 0) {
+                    p = r;
+                    q = n2 - 1;
+                } else {
+                    p = (r + g) % (n2 - 1);
+                    q = (r - g + n2 - 1) % (n2 - 1);
                 }
-            al = group8_sum_t(al);
-            be = group8_sum_t(be);
-            ga = group8_sum_t(ga);
-            if (active && al > null2 && be > null2 && ga * ga > tol2 * al * be) {
-                const T zeta = (be - al) / (T(2) * ga);
-                const T az = fabs(zeta);  // zeta^2 would overflow
-                const T t = az > huge ? T(0.5) / zeta : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
-                const T c = rsqrt(T(1) + t * t), s = c * t;
-                for (int i = gl; i < rows; i += 8) {
-                    const T x = A[i * lda + p], y = A[i * lda + q];
-                    A[i * lda + p] = c * x - s * y;
-                    A[i * lda + q] = s * x + c * y;
+                if (p > q) {
+                    const int tmp = p;
+                    p = q;
+                    q = tmp;
                 }
-                if (V)
-                    for (int i = gl; i < cols; i += 8) {
-                        const T x = V[i * ldv + p], y = V[i * ldv + q];
-                        V[i * ldv + p] = c * x - s * y;
-                        V[i * ldv + q] = s * x + c * y;
+                // every lane of the warp takes part in the group reductions
+                const bool active = g < npairs && q < cols;
+                T al = 0, be = 0, ga = 0;
+                if (active)
+                    for (int i = gl; i < rows; i += G) {
+                        const T x = A[i * lda + p], y = A[i * lda + q];
+                        al += x * x;
+                        be += y * y;
+                        ga += x * y;
                     }
-                if (gl == 0) *flag = 1;
+                al = group_sum<G>(al);
+                be = group_sum<G>(be);
+                ga = group_sum<G>(ga);
+                if (active && al > null2 && be > null2) {
+                    const T off2 = ga * ga, ab = al * be;
+                    if (gl == 0 && off2 > quad * quad * ab) atomicOr(flag + 1, 1);
+                    if (off2 > tol2 * ab) {
+                        const T zeta = (be - al) / (T(2) * ga);
+                        const T az = fabs(zeta);  // zeta^2 would overflow
+                        const T t = az > huge ? T(0.5) / zeta : copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
+                        const T c = rsqrt(T(1) + t * t), s = c * t;
+                        for (int i = gl; i < rows; i += G) {
+                            const T x = A[i * lda + p], y = A[i * lda + q];
+                            A[i * lda + p] = c * x - s * y;
+                            A[i * lda + q] = s * x + c * y;
+                        }
+                        if (V)
+                            for (int i = gl; i < cols; i += G) {
+                                const T x = V[i * ldv + p], y = V[i * ldv + q];
+                                V[i * ldv + p] = c * x - s * y;
+                                V[i * ldv + q] = s * x + c * y;
+                            }
+                        if (gl == 0) flag[0] = 1;
+                    }
+                }
             }
             __syncthreads();
         }
-        const int any = *flag;
+        const int any = flag[0], large = flag[1];
         __syncthreads();
-        if (!any) break;
+        if (!any || !large) break;
     }
     return sweep + 1;
 }
@@ -295,7 +305,7 @@ __device__ int svd_columns_mixed(const double *A, double *B, int ld, int rows, i
         V32[i * ld + j] = i == j ? 1.0f : 0.0f;
     }
     __syncthreads();
-    jacobi_columns<float>(A32, ld, rows, cols, V32, ld, 1e-5f, float(1e-12 * fro2 * inv * inv), 20, flag);
+    jacobi_columns<8, float>(A32, ld, rows, cols, V32, ld, 1e-5f, 0.0f, float(1e-12 * fro2 * inv * inv), 20, flag);
     for (int idx = threadIdx.x; idx < cols * cols; idx += kThreads) {
         const int i = idx / cols, j = idx % cols;
         V64[i * ld + j] = double(V32[i * ld + j]);
@@ -310,8 +320,13 @@ __device__ int svd_columns_mixed(const double *A, double *B, int ld, int rows, i
         B[i * ld + j] = v;
     }
     __syncthreads();
-    return jacobi_columns<double>(B, ld, rows, cols, nullptr, 0, kJacobiTol, floor_rel * floor_rel * fro2, kMaxSweeps,
-                                  flag);
+    // threads per pair: few (fewer rotation parameters per pair) while the columns are short
+    const double null2 = floor_rel * floor_rel * fro2;
+    if (rows <= 40)
+        return jacobi_columns<2, double>(B, ld, rows, cols, nullptr, 0, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
+    if (rows <= 80)
+        return jacobi_columns<4, double>(B, ld, rows, cols, nullptr, 0, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
+    return jacobi_columns<8, double>(B, ld, rows, cols, nullptr, 0, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
 }
 
 // After jacobi_columns: the singular values (column norms) in descending order into sig[],
