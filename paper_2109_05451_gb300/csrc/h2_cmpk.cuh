@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kThreads) k_orth_blocks(double *__restrict__ S
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < k * k; idx += kThreads) {  // Tm = S R_s^T
-            const int i = idx / k, j = idx % k;
+            const int j = idx / k, i = idx % k;  // lanes along i: one trip count per warp
             double v = 0.0;
             for (int m = j; m < k; ++m) v += Ss[i * ld + m] * Rs[j * ld + m];
             Tm[i * ld + j] = v;
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const doub
         for (int idx = threadIdx.x; idx < 2 * r * k; idx += kThreads) Zo[idx] = Z[(idx / k) * ld + idx % k];
         __syncthreads();
         for (int idx = threadIdx.x; idx < 2 * r * k; idx += kThreads) {  // X = Z Rh^T
-            const int i = idx / k, j = idx % k;
+            const int j = idx / (2 * r), i = idx % (2 * r);  // lanes along i: one trip count per warp
             double v = 0.0;
             for (int m = j; m < k; ++m) v += Z[i * ld + m] * Rs[j * ld + m];
             X[i * ld + j] = v;
