@@ -20,6 +20,7 @@ family instead (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -367,7 +368,7 @@ def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, 
 FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the part (CUDA cores); no tensor-core FP64 path
 
 
-def compress_benchmark(h2, torch, steps=3, workloads=None):
+def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024):
     """Algebraic recompression (Sec. 5) of the compression sets of Sec. 6 (synthetic_inputs
     COMPRESS_2D at N = 2^20, COMPRESS_3D at N = 2^18) to tau = 1e-3 on the GPU in FP64. Per
     set: device time of each step (CUDA events inside h2_compress, mean over `steps` calls
@@ -377,7 +378,9 @@ def compress_benchmark(h2, torch, steps=3, workloads=None):
     error of the compressed FP64 product against the original's on one Gaussian vector."""
     import time
     out = {}
-    for w in workloads or (si.COMPRESS_2D, si.COMPRESS_3D):
+    chosen = {"2d": si.COMPRESS_2D if grid2d == 1024 else dataclasses.replace(
+        si.COMPRESS_2D, name=f"compress_grid2d_exp_{grid2d}", points=f"grid2d:{grid2d}"), "3d": si.COMPRESS_3D}
+    for w in (chosen[k] for k in sets):
         pts = w.make_points()
         op = h2.H2Operator(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
         g = op.compress(si.COMPRESS_TAU)  # warm-up (kernel attributes, allocator)
@@ -537,6 +540,9 @@ def main():
     ap.add_argument("--no-matrix-free", action="store_true", help="skip the matrix-free product measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-operator measurement")
     ap.add_argument("--no-compress", action="store_true", help="skip the algebraic-compression measurement")
+    ap.add_argument("--compress-sets", default="2d,3d", help="compression sets to time (2d, 3d)")
+    ap.add_argument("--compress-grid", type=int, default=1024, help="grid side of the 2D compression set")
+    ap.add_argument("--compress-steps", type=int, default=3, help="timed compressions per set")
     ap.add_argument("--batch-count", type=int, default=64, help="operators of the batched measurement")
     ap.add_argument("--batch-nmax", type=int, default=2 ** 18,
                     help="largest N of the batched measurement (smaller values are for profiler captures)")
@@ -703,7 +709,8 @@ def main():
             line["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_compress:
         try:
-            line["compress"] = compress_benchmark(h2, torch)
+            line["compress"] = compress_benchmark(h2, torch, args.compress_steps, tuple(args.compress_sets.split(",")),
+                                                  args.compress_grid)
         except Exception as exc:  # reported, never silently dropped
             line["compress"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_serve:
