@@ -253,7 +253,7 @@ typedef struct {
     int rank_out;                  /* stored rank of the result: max of level_rank, >= 1 */
     int level_rank[H2_MAX_LEVELS]; /* rank of each level after truncation */
     double ms[4];                  /* device time of steps 1-4 (CUDA events) */
-    double flops[4];               /* floating-point operations of steps 1-4 */
+    double flops[4];               /* FP64 operations of steps 1-4 as the kernels perform them */
     int64_t jacobi_sweeps;         /* one-sided Jacobi sweeps over all SVDs of step 3 */
     size_t lowrank_bytes_in;       /* FP64 bytes of bases, transfers and coupling blocks */
     size_t lowrank_bytes_out;      /* the same at the level ranks of the result */

@@ -268,9 +268,10 @@ __device__ __forceinline__ double null_floor(double tau) { return tau > 0.0 ? fm
 // and every FP64 rotation costs 64x an FP32 one on this part. A32 and V32 share the region
 // f32 (rows + cols) * ld floats; V64 and Vq are cols x ld doubles. Columns under
 // floor_rel * |A|_F are the numerical null space: the FP64 sweeps leave them alone. Returns
-// the FP64 sweeps; the result's columns are in B, and scr[kMaxK + 1] holds |A|_F^2.
+// the FP64 sweeps; the result's columns are in B, scr[kMaxK + 1] holds |A|_F^2, and with
+// keep_v Vq holds every rotation (A Vq = B).
 __device__ int svd_columns_mixed(const double *A, double *B, int ld, int rows, int cols, float *f32, double *V64,
-                                 double *Vq, double *scr, double floor_rel, int *flag)
+                                 double *Vq, double *scr, double floor_rel, int *flag, bool keep_v = false)
 {
     float *A32 = f32, *V32 = f32 + size_t(rows) * ld;
     double *tau = scr, *red = scr + kMaxK;
@@ -322,11 +323,12 @@ __device__ int svd_columns_mixed(const double *A, double *B, int ld, int rows, i
     __syncthreads();
     // threads per pair: few (fewer rotation parameters per pair) while the columns are short
     const double null2 = floor_rel * floor_rel * fro2;
+    double *V = keep_v ? Vq : nullptr;  // Vq J: all the rotations, when the caller needs them
     if (rows <= 40)
-        return jacobi_columns<2, double>(B, ld, rows, cols, nullptr, 0, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
+        return jacobi_columns<2, double>(B, ld, rows, cols, V, ld, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
     if (rows <= 80)
-        return jacobi_columns<4, double>(B, ld, rows, cols, nullptr, 0, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
-    return jacobi_columns<8, double>(B, ld, rows, cols, nullptr, 0, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
+        return jacobi_columns<4, double>(B, ld, rows, cols, V, ld, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
+    return jacobi_columns<8, double>(B, ld, rows, cols, V, ld, kJacobiTol, kJacobiQuad, null2, kMaxSweeps, flag);
 }
 
 // After jacobi_columns: the singular values (column norms) in descending order into sig[],
@@ -334,8 +336,10 @@ __device__ int svd_columns_mixed(const double *A, double *B, int ld, int rows, i
 // and the count of singular values above tau times the largest. Columns under floor_abs
 // (the numerical null space, left out of the Jacobi sweeps) are neither normalized nor
 // counted, and at most min(rows, cols) are. sv, pos: cols doubles / ints of scratch.
+// With Vsrc (cols x cols, leading dimension ld) the columns of Vsrc are written instead (the
+// right singular vectors; wrows = cols), unnormalized.
 __device__ int sort_columns(const double *A, int ld, int rows, int cols, double *sv, int *pos, double *W, int ldw,
-                            int wrows, double *sig, double tau, double floor_abs)
+                            int wrows, double *sig, double tau, double floor_abs, const double *Vsrc = nullptr)
 {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int j = warp; j < cols; j += kWarps) {
@@ -357,7 +361,10 @@ __device__ int sort_columns(const double *A, int ld, int rows, int cols, double 
     for (int idx = threadIdx.x; idx < wrows * cols; idx += kThreads) {
         const int i = idx / cols, j = idx % cols;
         const double s = sv[j];
-        W[int64_t(i) * ldw + pos[j]] = (i < rows && s > floor_) ? A[i * ld + j] / s : 0.0;
+        if (Vsrc)
+            W[int64_t(i) * ldw + pos[j]] = (i < cols && s > floor_) ? Vsrc[i * ld + j] : 0.0;
+        else
+            W[int64_t(i) * ldw + pos[j]] = (i < rows && s > floor_) ? A[i * ld + j] / s : 0.0;
     }
     for (int j = threadIdx.x; j < cols; j += kThreads) sig[pos[j]] = sv[j];
     int count = 0;
@@ -791,19 +798,28 @@ __global__ void __launch_bounds__(kThreads) k_node_svd(int lp, int k, const doub
         double *Zo = Zb + slot * 2 * k * k;
         for (int idx = threadIdx.x; idx < 2 * r * k; idx += kThreads) Zo[idx] = Z[(idx / k) * ld + idx % k];
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 2 * r * k; idx += kThreads) {  // X = Z Rh^T
-            const int j = idx / (2 * r), i = idx % (2 * r);  // lanes along i: one trip count per warp
+        // X = Z Rh^T (2r x k). With 2r < k the Jacobi sweeps take X^T (k x 2r: 2r columns of
+        // full rank, where X's k columns would carry k - 2r null ones) and the left singular
+        // vectors of X are the accumulated rotations.
+        const int n = 2 * r;
+        const bool wide = n < k;
+        for (int idx = threadIdx.x; idx < n * k; idx += kThreads) {
+            const int j = idx / n, i = idx % n;  // lanes along i: one trip count per warp
             double v = 0.0;
             for (int m = j; m < k; ++m) v += Z[i * ld + m] * Rs[j * ld + m];
-            X[i * ld + j] = v;
+            if (wide) X[j * ld + i] = v;
+            else X[i * ld + j] = v;
         }
         __syncthreads();
         int count = 0;
         if (r > 0) {
-            const int sw = svd_columns_mixed(X, Z, ld, 2 * r, k, reinterpret_cast<float *>(Z), Rs, Vq, qscr, floor_rel,
-                                             flag);
-            count = sort_columns(Z, ld, 2 * r, k, sv, pos, Wb + slot * 2 * k * k, k, 2 * r, sig + t * k, tau,
-                                 floor_rel * sqrt(qscr[kMaxK + 1]));
+            const int rows = wide ? k : n, cols = wide ? n : k;
+            const int sw = svd_columns_mixed(X, Z, ld, rows, cols, reinterpret_cast<float *>(Z), Rs, Vq, qscr, floor_rel,
+                                             flag, wide);
+            for (int j = threadIdx.x; j < k; j += kThreads) sig[t * k + j] = 0.0;
+            __syncthreads();
+            count = sort_columns(Z, ld, rows, cols, sv, pos, Wb + slot * 2 * k * k, k, n, sig + t * k, tau,
+                                 floor_rel * sqrt(qscr[kMaxK + 1]), wide ? Vq : nullptr);
             if (threadIdx.x == 0) atomicAdd(sweeps, (unsigned long long)sw);
         } else {
             for (int j = threadIdx.x; j < k; j += kThreads) sig[t * k + j] = 0.0;

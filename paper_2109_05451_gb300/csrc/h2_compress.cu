@@ -262,15 +262,27 @@ extern "C" int h2_compress(h2_handle h, double tau, void *cuda_stream, h2_handle
         for (int64_t t = 0; t < nleaves; ++t) f1 += qr_flops(double(leaf_lo[t + 1] - leaf_lo[t]), K);
         f1 += double(nn - nleaves) * (2 * dk3 + qr_flops(2 * K, K)) + double(ncpl) * 2 * dk3;
         f2 = double(nn - 1) * (dk3 + 2 * dk3) + double(ncpl) * 2 * dk3;
-        auto jac = [&](double sweeps_l, double rows) { return sweeps_l * (K * (K - 1) / 2) * 12.0 * rows; };
+        // one-sided Jacobi: 12 flops per row per pair and sweep (three dot products and the
+        // rotation), 8 per pair row more where the rotations are accumulated; FP32 sweeps are
+        // not counted
+        auto jac = [&](double sweeps_l, double rows, double cols, bool acc) {
+            return sweeps_l * (cols * (cols - 1) / 2) * (12.0 * rows + (acc ? 8.0 * cols : 0.0));
+        };
+        double leaf_p = 0;
         for (int64_t t = 0; t < nleaves; ++t) {
-            const double rows = leaf_lo[t + 1] - leaf_lo[t];
-            f3 += rows * K * K + 2.0 * ranks[q] * rows * K;
+            const double rows = leaf_lo[t + 1] - leaf_lo[t], p = std::min(rows, K);
+            leaf_p += p / double(nleaves);
+            // V re-orthogonalization, A Vq, W = Q W', T = W^T Q
+            f3 += qr_flops(K, K) + 2.0 * p * K * K + 2.0 * rows * p * K + 2.0 * ranks[q] * rows * K;
         }
-        f3 += jac(double(sweeps[q]), double(op.n) / double(nleaves));
+        f3 += jac(double(sweeps[q]), leaf_p, K, false);
         for (int lp = q - 1; lp >= 0; --lp) {
-            const double parents = double(int64_t(1) << lp), r = ranks[lp + 1], rp = ranks[lp];
-            f3 += parents * (2 * 2 * r * K * K + 2 * r * K * K + 2 * rp * 2 * r * K) + jac(double(sweeps[lp]), 2 * r);
+            const double parents = double(int64_t(1) << lp), r = ranks[lp + 1], rp = ranks[lp], n = 2 * r;
+            const bool wide = n < K;
+            const double cols = wide ? n : K, rows = wide ? K : n;
+            f3 += parents * (2 * 2 * r * K * K + n * K * K + qr_flops(cols, cols) + 2.0 * rows * cols * cols +
+                             2 * rp * n * K) +
+                  jac(double(sweeps[lp]), rows, cols, wide);
         }
         for (int64_t b = 0; b < ncpl; ++b) {
             int l = 0;
