@@ -59,6 +59,39 @@ __device__ __forceinline__ double group8_sum(double v)
 
 __device__ __forceinline__ int level_of(int64_t t) { return 63 - __clzll(t); }
 
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v)
+{
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+
+// Apply the reflector I - tau v v^T (v = e_j + the tail below row j of column j of V) to
+// the columns c0 .. c1-1 of A: 4 threads per column (8 columns per warp), each over a
+// quarter of the rows, so that nearly every lane of an FP64 instruction does useful work.
+__device__ __forceinline__ void reflect_columns(const double *V, int ldv, double *A, int lda, int rows, int j, int c0,
+                                                int c1, double tau)
+{
+    const int grp = threadIdx.x / 4, gl = threadIdx.x % 4;
+    for (int cb = c0; cb < c1; cb += kThreads / 4) {
+        if (cb + (threadIdx.x / 32) * 8 >= c1) continue;  // the whole warp is past the last column
+        const int c = cb + grp;
+        const bool act = c < c1;
+        double w = 0.0;
+        if (act) {
+            if (gl == 0) w = A[j * lda + c];
+            for (int i = j + 1 + gl; i < rows; i += 4) w += V[i * ldv + j] * A[i * lda + c];
+        }
+        w = group_sum<4>(w) * tau;
+        if (act) {
+            if (gl == 0) A[j * lda + c] -= w;
+            for (int i = j + 1 + gl; i < rows; i += 4) A[i * lda + c] -= V[i * ldv + j] * w;
+        }
+    }
+}
+
 // Householder QR of the rows x cols matrix A in place: R on and above the diagonal, the
 // reflectors' tails below it (leading entry 1 implicit), their scalars in tau.
 // red: 2 doubles of scratch. All threads of the CTA take part.
@@ -90,13 +123,7 @@ __device__ void house_qr(double *A, int ld, int rows, int cols, double *tau, dou
             const double sc = red[0];
             for (int i = j + 1 + threadIdx.x; i < rows; i += kThreads) A[i * ld + j] *= sc;
             __syncthreads();
-            for (int c = j + 1 + warp; c < cols; c += kWarps) {
-                double w = lane == 0 ? A[j * ld + c] : 0.0;
-                for (int i = j + 1 + lane; i < rows; i += 32) w += A[i * ld + j] * A[i * ld + c];
-                w = warp_sum(w) * tj;
-                if (lane == 0) A[j * ld + c] -= w;
-                for (int i = j + 1 + lane; i < rows; i += 32) A[i * ld + c] -= A[i * ld + j] * w;
-            }
+            reflect_columns(A, ld, A, ld, rows, j, j + 1, cols, tj);
         }
         __syncthreads();
     }
@@ -115,15 +142,7 @@ __device__ void house_form_q(const double *A, int ld, int rows, int cols, const 
     __syncthreads();
     for (int j = p - 1; j >= 0; --j) {
         const double tj = tau[j];
-        if (tj != 0.0) {
-            for (int c = j + warp; c < p; c += kWarps) {
-                double w = lane == 0 ? Q[j * ldq + c] : 0.0;
-                for (int i = j + 1 + lane; i < rows; i += 32) w += A[i * ld + j] * Q[i * ldq + c];
-                w = warp_sum(w) * tj;
-                if (lane == 0) Q[j * ldq + c] -= w;
-                for (int i = j + 1 + lane; i < rows; i += 32) Q[i * ldq + c] -= A[i * ld + j] * w;
-            }
-        }
+        if (tj != 0.0) reflect_columns(A, ld, Q, ldq, rows, j, j, p, tj);
         __syncthreads();
     }
 }
@@ -166,14 +185,6 @@ __device__ void qr_fold(double *R, double *B, int ld, int k, double *red)
         }
         __syncthreads();
     }
-}
-
-template <int G, typename T>
-__device__ __forceinline__ T group_sum(T v)
-{
-#pragma unroll
-    for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // One-sided (Hestenes) Jacobi on the columns of A (rows x cols, shared memory, leading
