@@ -1274,9 +1274,10 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     if (!h) return H2_EINVAL;
     if (prec != H2_FP64 && prec != H2_FP32 && prec != H2_BF16X2 && prec != H2_FP32_MF) return H2_EINVAL;
     h2_op &op = *h;
-    // explicit coupling blocks (a compressed operator) exist in FP64 / FP32 tiles only: the
-    // tensor tiles are 64 x 64 and the matrix-free precision needs the Chebyshev points
-    if (!op.S.empty() && (prec == H2_BF16X2 || prec == H2_FP32_MF)) return H2_EINVAL;
+    // a compressed operator (p = 0: explicit coupling blocks, no Chebyshev points) uploads in
+    // FP64 / FP32 tiles only: the tensor tiles are 64 x 64 and the matrix-free precision
+    // evaluates the kernel at the Chebyshev points
+    if (op.p == 0 && (prec == H2_BF16X2 || prec == H2_FP32_MF)) return H2_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     h2_device_free(&op);
     h2_device *dv = new (std::nothrow) h2_device;
