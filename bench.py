@@ -368,6 +368,30 @@ def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, 
 FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the part (CUDA cores); no tensor-core FP64 path
 
 
+def compress_oracle_sample(h2, torch):
+    """The oracle's recompression (numpy FP64, one Python thread driving LAPACK on small
+    matrices) timed on a bounded sample -- the 2D compression set at 128 x 128 points
+    (N = 2^14) -- beside the GPU's on the same sample."""
+    import time
+    import oracle
+    import oracle.compress as oc
+    w = dataclasses.replace(si.COMPRESS_2D, points="grid2d:128")
+    pts = w.make_points()
+    orc = oracle.OracleH2(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    t0 = time.perf_counter()
+    c = oc.CompressedH2(orc, si.COMPRESS_TAU)
+    cpu_s = time.perf_counter() - t0
+    op = h2.H2Operator(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    op.compress(si.COMPRESS_TAU).close()
+    g = op.compress(si.COMPRESS_TAU)
+    gpu_ms = float(sum(g.compress_info.ms))
+    same = g.level_ranks == c.ranks
+    g.close()
+    op.close()
+    return {"kind": "oracle", "sample": "2D compression set at 128 x 128 points (N = 2^14), tau = 1e-3",
+            "cores": 1, "oracle_s": cpu_s, "gpu_ms": gpu_ms, "ranks_equal": same}
+
+
 def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024):
     """Algebraic recompression (Sec. 5) of the compression sets of Sec. 6 (synthetic_inputs
     COMPRESS_2D at N = 2^20, COMPRESS_3D at N = 2^18) to tau = 1e-3 on the GPU in FP64. Per
@@ -711,6 +735,8 @@ def main():
         try:
             line["compress"] = compress_benchmark(h2, torch, args.compress_steps, tuple(args.compress_sets.split(",")),
                                                   args.compress_grid)
+            if rank == 0 and world == 1 and not args.no_cpu_baseline:
+                line["compress"]["cpu_baseline"] = compress_oracle_sample(h2, torch)
         except Exception as exc:  # reported, never silently dropped
             line["compress"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_serve:
