@@ -555,11 +555,16 @@ int launch_wide(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double
     const uint32_t tile_str = uint32_t(((std::max<size_t>(size_t(k) * kx, size_t(mp) * dv.max_leaf_rows) * es) + 15) /
                                        16 * 16);
     const uint32_t x_str = uint32_t(std::max(mp, kx) * NVMAX * es);
-    // two CTAs per SM where three stages fit in half of the shared memory: eight consumer
-    // warps hide the latency of the register-blocked products; else one CTA per SM
-    Pipe p_str = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 110 * 1024, 12);
-    int per_sm = 2;
-    if (p_str.ns < 3) {
+    // FP32: three CTAs per SM where two stages fit in a third of the shared memory (twelve
+    // consumer warps hide the shared-memory latency of the register-blocked products); else
+    // two CTAs per SM where three stages fit in half; else one CTA per SM
+    Pipe p_str = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 72 * 1024, 12);
+    int per_sm = 3;
+    if (sizeof(T) != 4 || p_str.ns < 2) {
+        p_str = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 110 * 1024, 12);
+        per_sm = 2;
+    }
+    if (p_str.ns < 3 && per_sm == 2) {
         p_str = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 200 * 1024, 12);
         per_sm = 1;
     }

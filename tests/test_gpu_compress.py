@@ -211,3 +211,27 @@ def test_full_size_2d_workload_error_bound_on_sampled_leaves():
     assert err <= 2 * np.sqrt(info.dropped_energy) * np.linalg.norm(x) * (1 + 1e-9)
     assert err / np.linalg.norm(ref) <= 1e-2
     assert np.all(np.isfinite(y))
+
+
+@pytest.mark.parametrize("pts,m,eta", [
+    (si.uniform_cloud(7, 2, 1), 64, 0.9),      # one leaf: no tree above it, no coupling block
+    (si.grid_2d(20), 16, 1e-9),                # nothing admissible: every block dense
+])
+def test_degenerate_partitions(pts, m, eta):
+    ker = ("exp", 0.1, 0, 0)
+    orc = oracle.OracleH2(pts, ker, m, 4, eta)
+    op = h2.H2Operator(pts, ker, m, 4, eta)
+    g = op.compress(1e-3)
+    info = g.compress_info
+    assert info.norm_lowrank == 0.0 and info.rank_out == 1 and max(g.level_ranks) == 0
+    g.upload("fp64")
+    X = si.gaussian_vectors(len(pts), 2, 4)
+    assert rel(gpu_matvec(g, X, "fp64"), orc.matvec(X)) <= 1e-13
+
+
+def test_coarse_tolerance_matches_the_oracle(built):
+    pts, orc, op, c, g = built("cloud3d_exp_k27", 0.5)
+    assert g.level_ranks == c.ranks and max(c.ranks) <= 3
+    g.upload("fp64")
+    X = si.gaussian_vectors(len(pts), 2, 6)
+    assert rel(gpu_matvec(g, X, "fp64"), c.matvec(X)) <= tol("fp64", 0.5)

@@ -145,3 +145,22 @@ def test_ranks_are_uniform_per_level_and_shrink_the_operator(built):
         assert c.S[b].shape == (c.ranks[l], c.ranks[l])
     before, after = c.lowrank_bytes()
     assert after < before
+
+
+@pytest.mark.parametrize("pts,m,eta", [
+    (si.uniform_cloud(7, 2, 1), 64, 0.9),      # one leaf: no tree above it, no coupling block
+    (si.grid_2d(20), 16, 1e-9),                # nothing admissible: every block dense
+])
+def test_degenerate_partitions_compress_to_the_same_operator(pts, m, eta):
+    orc = oracle.OracleH2(pts, ("exp", 0.1, 0, 0), m, 4, eta)
+    c = oc.CompressedH2(orc, 1e-3)
+    assert len(c.blk_t) == 0 and max(c.ranks) == 0 and c.norm_lr == 0.0
+    X = si.gaussian_vectors(len(pts), 2, 4)
+    assert rel(c.matvec(X), orc.matvec(X)) <= 1e-14
+
+
+def test_coarse_tolerance_keeps_the_bound(built):
+    orc, alr, c = built("cloud3d_exp_k27", 0.5)
+    err = np.linalg.norm(c.assemble_lowrank() - alr)
+    bound = 2.0 * np.sqrt(sum(float(np.sum(d ** 2)) for d in c.dropped.values()))
+    assert err <= bound * (1 + 1e-8) and max(c.ranks) <= 3
