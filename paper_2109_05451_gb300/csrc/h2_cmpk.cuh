@@ -7,8 +7,12 @@
 //   * the QR update of an upper-triangular R by a dense k x k block, R <- R-factor of
 //     [R; B]: the new-basis downsweep folds the stack of Eq. for B_i^q into R one block at a
 //     time, so a stack of any length needs k x k of memory;
-//   * one-sided (Hestenes) Jacobi SVD with round-robin pair ordering, 8 threads per pair;
+//   * the Gram-matrix form of that downsweep (Cholesky factor of the accumulated B^T B);
+//   * one-sided (Hestenes) Jacobi SVD with round-robin pair ordering, in two precisions;
 //   * small products with triangular or rectangular factors.
+// GB300 issues about two FP64 FMAs per clock per SM, so the kernels are laid out to keep
+// lanes on useful FP64 work: few threads per reduction, no FP64 shuffle trees where a
+// product term per lane will do.
 // The rank of every level is decided on the device (atomicMax of the per-node counts), read
 // by the next kernel, and never sent to the host until the end.
 #pragma once
@@ -47,13 +51,6 @@ __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ double group8_sum(double v)
-{
-#pragma unroll
-    for (int o = 4; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
@@ -133,7 +130,6 @@ __device__ void house_qr(double *A, int ld, int rows, int cols, double *tau, dou
 // p columns of the identity, p = min(rows, cols); columns p..cols-1 are zero.
 __device__ void house_form_q(const double *A, int ld, int rows, int cols, const double *tau, double *Q, int ldq)
 {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int p = rows < cols ? rows : cols;
     for (int idx = threadIdx.x; idx < rows * cols; idx += kThreads) {
         const int i = idx / cols, c = idx % cols;
