@@ -453,6 +453,19 @@ def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024):
     return out
 
 
+def batch_roofline(total_bytes, total_flops, ms):
+    """The batch's bound: its blocks streamed once at the measured copy bandwidth, or its
+    flops at the FP32 FMA peak, whichever takes longer; frac = that time / the measured one."""
+    peak_gbs, kind = measured_peaks()
+    t_hbm = total_bytes / (peak_gbs * 1e9) * 1e3
+    t_fma = total_flops / (FFMA_PEAK_TFLOPS * 1e12) * 1e3
+    bound = "hbm" if t_hbm >= t_fma else "alu"
+    return {"bound": bound, "bound_ms": max(t_hbm, t_fma), "hbm_ms": t_hbm, "fma_ms": t_fma,
+            "achieved": total_bytes / (ms * 1e-3) / 1e9 if bound == "hbm" else total_flops / (ms * 1e-3) / 1e12,
+            "peak": peak_gbs if bound == "hbm" else FFMA_PEAK_TFLOPS, "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
+            "frac": max(t_hbm, t_fma) / ms, "peak_kind": f"{kind} HBM / derived FP32 FMA"}
+
+
 def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with_fp64=True):
     """Batched products of 64 uneven operators (synthetic_inputs.uneven_batch: N log-uniform
     in [2^12, 2^18], even members 2D grids with orders 4-8, odd members 3D clouds with orders
@@ -522,6 +535,7 @@ def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with
                 "batched_gflops": total_flops / (mb * 1e-3) / 1e9,
                 "sequential_ms": msq, "sequential_GB/s": total_bytes / (msq * 1e-3) / 1e9,
                 "speedup_vs_sequential": msq / mb, "create_s": create_s, "configuration": desc,
+                "roofline": batch_roofline(total_bytes, total_flops, mb),
                 "fp64": fp64, "l2": "inputs larger than L2, no flush"}
     finally:
         for op in ops:
