@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     const int tid = threadIdx.x;
-    AccOf<T, NVMAX> acc;
+    AccStreamOf<T, NVMAX> acc;
     bool fresh = true;
     for (;;) {
         if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, err)) return;

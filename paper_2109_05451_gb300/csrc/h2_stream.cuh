@@ -117,11 +117,13 @@ struct Smem {
 // Vectors per pass from which the wide accumulator (AccW) replaces the group-reduced one.
 constexpr int kWideMin = 8;
 
-// Elements of the column-group exchange buffer per vector (the wide accumulator has none).
+// Elements of the column-group exchange buffer per vector: the narrow accumulator's groups,
+// or the split-column slices of the block streams' wide accumulator (AccWK: 32 / NV - 1
+// slices of 64 outputs); AccW at 32 vectors needs none.
 template <int NVMAX>
 __host__ __device__ constexpr int red_elems()
 {
-    return NVMAX >= kWideMin ? 0 : kRedElems;
+    return NVMAX >= 32 ? 0 : NVMAX >= kWideMin ? (32 / NVMAX - 1) * 64 : kRedElems;
 }
 
 template <typename T, int NVMAX>
@@ -607,6 +609,127 @@ struct AccW {
 template <typename T, int NVMAX>
 using AccOf = typename std::conditional<(NVMAX >= kWideMin), AccW<T, NVMAX>, Acc<T, NVMAX>>::type;
 
+// Wide accumulator of the block streams for passes of 8 or 16 vectors: every thread holds a
+// 4-output x 4-vector register block, as AccW does at 32 vectors, and the consumer threads
+// split the columns into S = 32 / NV slices of four-column steps (slice ks takes the steps
+// ks, ks + S, ...). Every loaded tile value then feeds 4 FMAs and every vector value 4, where
+// AccW's 4 x NV/8 block feeds NV/8 and 4. At the end of a row the slices are summed through
+// shared memory in a fixed order (slice 0 adds 1 .. S-1) and slice 0 stores, so the result
+// stays deterministic.
+template <typename T, int NV>
+struct AccWK {
+    static constexpr int VT = 4;
+    static constexpr int NVG = NV / 4;  // vector groups
+    static constexpr int S = 32 / NV;   // column slices
+    static_assert(NV == 8 || NV == 16, "split-column wide accumulator: 8 or 16 vectors");
+    T a[VT][4];
+    int o0, v0, ks;
+
+    __device__ __forceinline__ void setup(int /*R*/, int /*ld*/, int tid)
+    {
+        o0 = (tid & 15) * 4;
+        const int rest = tid >> 4;
+        v0 = (rest % NVG) * VT;
+        ks = rest / NVG;
+    }
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int v = 0; v < VT; ++v)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) a[v][e] = T(0);
+    }
+    __device__ __forceinline__ void step4(const T *__restrict__ tb, int ld, const T *__restrict__ xb, int xld)
+    {
+        T xv[VT][4];
+#pragma unroll
+        for (int v = 0; v < VT; ++v) AccW<T, 32>::load4(xv[v], xb + v * xld);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            T t[4];
+            AccW<T, 32>::load4(t, tb + jj * ld);
+#pragma unroll
+            for (int v = 0; v < VT; ++v)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) a[v][e] += t[e] * xv[v][jj];
+        }
+    }
+    __device__ __forceinline__ void column(const T *__restrict__ tb, int ld, int R, const T *__restrict__ xb, int xld,
+                                           int j, bool masked)
+    {
+        T t[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) t[e] = (!masked || o0 + e < R) ? tb[j * ld + e] : T(0);
+#pragma unroll
+        for (int v = 0; v < VT; ++v) {
+            const T xs = xb[v * xld + j];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) a[v][e] += t[e] * xs;
+        }
+    }
+    // out[o][v] += sum over this slice's columns j < C of tile[j*ld + o] * x[v*xld + j].
+    __device__ __forceinline__ void gemv(const T *__restrict__ tile, int ld, int R, int C, const T *__restrict__ x,
+                                         int xld, int nv)
+    {
+        if (o0 >= R || v0 >= nv) return;
+        const T *tb = tile + o0;
+        const T *xb = x + v0 * xld;
+        if (ld == 64 && xld == 64 && C == 64) {
+#pragma unroll
+            for (int j = 4 * ks; j < 64; j += 4 * S) step4(tb + j * 64, 64, xb + j, 64);
+            return;
+        }
+        if ((ld & 3) == 0 && (xld & 3) == 0 && o0 + 4 <= ld) {  // zero-padded, 16-byte aligned rows
+            for (int j = 4 * ks; j + 4 <= C; j += 4 * S) step4(tb + j * ld, ld, xb + j, xld);
+            const int jt = C & ~3;  // the partial last step belongs to slice (C / 4) % S
+            if (jt < C && (C >> 2) % S == ks)
+                for (int j = jt; j < C; ++j) column(tb, ld, R, xb, xld, j, false);
+            return;
+        }
+        for (int j = ks; j < C; j += S) column(tb, ld, R, xb, xld, j, true);  // unaligned rows
+    }
+    // Sum the slices (every consumer thread calls this; it holds a consumer barrier).
+    __device__ __forceinline__ bool reduce(int R, int nv, T *red)
+    {
+        const bool mine = o0 < R && v0 < nv;
+        if (ks > 0 && mine)
+#pragma unroll
+            for (int v = 0; v < VT; ++v)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) red[((ks - 1) * 64 + o0 + e) * NV + v0 + v] = a[v][e];
+        h2p::consumer_sync(kConsumers);
+        if (ks == 0 && mine)
+            for (int sl = 1; sl < S; ++sl)
+#pragma unroll
+                for (int v = 0; v < VT; ++v)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) a[v][e] += red[((sl - 1) * 64 + o0 + e) * NV + v0 + v];
+        return ks == 0 && mine;
+    }
+    __device__ __forceinline__ void store(T *dst, int ld, int nv, int R) const
+    {
+        const bool vec = (ld & 3) == 0 && o0 + 4 <= R;
+#pragma unroll
+        for (int v = 0; v < VT; ++v) {
+            if (v0 + v >= nv) break;
+            T *d = dst + (v0 + v) * ld + o0;
+            if (vec) {
+                AccW<T, 32>::store4(d, a[v]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (o0 + e < R) d[e] = a[v][e];
+            }
+        }
+    }
+};
+
+// Accumulator of the block streams (k_stream, k_stream_batch): the split-column form for 8
+// and 16 vectors.
+template <typename T, int NVMAX>
+using AccStreamOf =
+    typename std::conditional<(NVMAX >= kWideMin && NVMAX < 32), AccWK<T, NVMAX>, AccOf<T, NVMAX>>::type;
+
 // ------------------------------------------------------------------ gather
 
 // xt[leaf][v][i] = X[v*n + perm[leaf_lo[leaf] + i]]: one CTA per leaf (grid-stride). Also
@@ -902,7 +1025,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     const int tid = threadIdx.x;
-    AccOf<T, NVMAX> acc;
+    AccStreamOf<T, NVMAX> acc;
     bool fresh = true;
     for (;;) {
         if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
