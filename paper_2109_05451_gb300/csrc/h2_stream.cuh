@@ -118,12 +118,12 @@ struct Smem {
 constexpr int kWideMin = 8;
 
 // Elements of the column-group exchange buffer per vector: the narrow accumulator's groups,
-// or the split-column slices of the block streams' wide accumulator (AccWK: 32 / NV - 1
-// slices of 64 outputs); AccW at 32 vectors needs none.
+// or, in the block streams (stream = true), the split-column slices of AccWK (S - 1 slices
+// of 64 outputs: S = 4, 2 at 8, 16 vectors); AccW (sweeps; streams of 32 vectors) needs none.
 template <int NVMAX>
-__host__ __device__ constexpr int red_elems()
+__host__ __device__ constexpr int red_elems(bool stream)
 {
-    return NVMAX >= 32 ? 0 : NVMAX >= kWideMin ? (32 / NVMAX - 1) * 64 : kRedElems;
+    return NVMAX < kWideMin ? kRedElems : (!stream || NVMAX >= 32) ? 0 : NVMAX == 8 ? 3 * 64 : 64;
 }
 
 template <typename T, int NVMAX>
@@ -132,7 +132,7 @@ __host__ __device__ inline size_t smem_bytes(const Pipe &p, int sub_nodes, int k
     size_t b = size_t(p.ns) * (p.tile_bytes + p.x_bytes);
     b += size_t(p.ns) * sizeof(StreamDesc);
     b += size_t(2 * p.ns) * sizeof(uint64_t);
-    b += size_t(red_elems<NVMAX>()) * NVMAX * sizeof(T);
+    b += size_t(red_elems<NVMAX>(chunks)) * NVMAX * sizeof(T);
     b += size_t(sub_nodes) * kx * NVMAX * sizeof(T);
     if (chunks) b += 2 * kChunkDesc * sizeof(StreamDesc) + 2 * sizeof(uint64_t);
     b += 16;
@@ -154,7 +154,7 @@ __device__ inline Smem<T> carve(unsigned char *base, const Pipe &p, int sub_node
     s.empty = s.full + p.ns;
     c += size_t(2 * p.ns) * sizeof(uint64_t);
     s.red = reinterpret_cast<T *>(c);
-    c += size_t(red_elems<NVMAX>()) * NVMAX * sizeof(T);
+    c += size_t(red_elems<NVMAX>(chunks)) * NVMAX * sizeof(T);
     s.sub = reinterpret_cast<T *>(c);
     c += size_t(sub_nodes) * kx * NVMAX * sizeof(T);
     s.dbuf = nullptr;
@@ -609,26 +609,31 @@ struct AccW {
 template <typename T, int NVMAX>
 using AccOf = typename std::conditional<(NVMAX >= kWideMin), AccW<T, NVMAX>, Acc<T, NVMAX>>::type;
 
-// Wide accumulator of the block streams for passes of 8 or 16 vectors: every thread holds a
-// 4-output x 4-vector register block, as AccW does at 32 vectors, and the consumer threads
-// split the columns into S = 32 / NV slices of four-column steps (slice ks takes the steps
-// ks, ks + S, ...). Every loaded tile value then feeds 4 FMAs and every vector value 4, where
-// AccW's 4 x NV/8 block feeds NV/8 and 4. At the end of a row the slices are summed through
-// shared memory in a fixed order (slice 0 adds 1 .. S-1) and slice 0 stores, so the result
-// stays deterministic.
-template <typename T, int NV>
+// Wide accumulator of the block streams (k_stream, k_stream_batch): every thread holds an
+// OUT-output x 4-vector register block, and the 128 consumer threads split the columns into
+// S = 128 / ((64 / OUT) (NV / 4)) slices of four-column steps (slice ks takes the steps
+// ks, ks + S, ...). With 8 and 16 vectors (OUT = 4; S = 4, 2) every loaded tile value feeds
+// 4 FMAs where AccW's 4 x NV/8 block feeds 1 or 2. At the end of a row the slices are summed
+// through shared memory in a fixed order (slice 0 adds 1 .. S-1) and slice 0 stores, so the
+// result stays deterministic.
+template <typename T, int NV, int OUT>
 struct AccWK {
     static constexpr int VT = 4;
-    static constexpr int NVG = NV / 4;  // vector groups
-    static constexpr int S = 32 / NV;   // column slices
-    static_assert(NV == 8 || NV == 16, "split-column wide accumulator: 8 or 16 vectors");
-    T a[VT][4];
+    static constexpr int NVG = NV / 4;        // vector groups
+    static constexpr int OG = 64 / OUT;       // output groups
+    static constexpr int S = kConsumers / (OG * NVG);  // column slices
+    static constexpr int QS = 64 / (OUT / 4);  // distance between a thread's output quads
+    static_assert(S >= 2 && OG * NVG * S == kConsumers, "split-column wide accumulator: 8, 16 or 32 vectors");
+    // outputs of element e: quad e / 4 at o0 + QS * (e / 4) (16-byte loads of neighbouring
+    // threads stay adjacent in shared memory: no bank conflicts)
+    T a[VT][OUT];
     int o0, v0, ks;
 
+    __device__ __forceinline__ static int off(int e) { return (e & 3) + QS * (e >> 2); }
     __device__ __forceinline__ void setup(int /*R*/, int /*ld*/, int tid)
     {
-        o0 = (tid & 15) * 4;
-        const int rest = tid >> 4;
+        o0 = (tid % OG) * 4;
+        const int rest = tid / OG;
         v0 = (rest % NVG) * VT;
         ks = rest / NVG;
     }
@@ -637,7 +642,7 @@ struct AccWK {
 #pragma unroll
         for (int v = 0; v < VT; ++v)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) a[v][e] = T(0);
+            for (int e = 0; e < OUT; ++e) a[v][e] = T(0);
     }
     __device__ __forceinline__ void step4(const T *__restrict__ tb, int ld, const T *__restrict__ xb, int xld)
     {
@@ -646,25 +651,27 @@ struct AccWK {
         for (int v = 0; v < VT; ++v) AccW<T, 32>::load4(xv[v], xb + v * xld);
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-            T t[4];
-            AccW<T, 32>::load4(t, tb + jj * ld);
+            T t[OUT];
+#pragma unroll
+            for (int h = 0; h < OUT / 4; ++h)
+                AccW<T, 32>::load4(*reinterpret_cast<T(*)[4]>(t + 4 * h), tb + jj * ld + QS * h);
 #pragma unroll
             for (int v = 0; v < VT; ++v)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) a[v][e] += t[e] * xv[v][jj];
+                for (int e = 0; e < OUT; ++e) a[v][e] += t[e] * xv[v][jj];
         }
     }
     __device__ __forceinline__ void column(const T *__restrict__ tb, int ld, int R, const T *__restrict__ xb, int xld,
-                                           int j, bool masked)
+                                           int j)
     {
-        T t[4];
+        T t[OUT];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) t[e] = (!masked || o0 + e < R) ? tb[j * ld + e] : T(0);
+        for (int e = 0; e < OUT; ++e) t[e] = o0 + off(e) < R ? tb[j * ld + off(e)] : T(0);
 #pragma unroll
         for (int v = 0; v < VT; ++v) {
             const T xs = xb[v * xld + j];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) a[v][e] += t[e] * xs;
+            for (int e = 0; e < OUT; ++e) a[v][e] += t[e] * xs;
         }
     }
     // out[o][v] += sum over this slice's columns j < C of tile[j*ld + o] * x[v*xld + j].
@@ -679,14 +686,16 @@ struct AccWK {
             for (int j = 4 * ks; j < 64; j += 4 * S) step4(tb + j * 64, 64, xb + j, 64);
             return;
         }
-        if ((ld & 3) == 0 && (xld & 3) == 0 && o0 + 4 <= ld) {  // zero-padded, 16-byte aligned rows
+        // zero-padded, 16-byte aligned rows whose padding covers this thread's outputs
+        if ((ld & 3) == 0 && (xld & 3) == 0 && o0 + off(OUT - 1) < ld) {
             for (int j = 4 * ks; j + 4 <= C; j += 4 * S) step4(tb + j * ld, ld, xb + j, xld);
             const int jt = C & ~3;  // the partial last step belongs to slice (C / 4) % S
             if (jt < C && (C >> 2) % S == ks)
-                for (int j = jt; j < C; ++j) column(tb, ld, R, xb, xld, j, false);
+                for (int j = jt; j < C; ++j) column(tb, ld, R, xb, xld, j);
             return;
         }
-        for (int j = ks; j < C; j += S) column(tb, ld, R, xb, xld, j, true);  // unaligned rows
+        for (int q = ks; 4 * q < C; q += S)  // unaligned rows or outputs past the padding
+            for (int j = 4 * q; j < C && j < 4 * q + 4; ++j) column(tb, ld, R, xb, xld, j);
     }
     // Sum the slices (every consumer thread calls this; it holds a consumer barrier).
     __device__ __forceinline__ bool reduce(int R, int nv, T *red)
@@ -696,39 +705,43 @@ struct AccWK {
 #pragma unroll
             for (int v = 0; v < VT; ++v)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) red[((ks - 1) * 64 + o0 + e) * NV + v0 + v] = a[v][e];
+                for (int e = 0; e < OUT; ++e) red[((ks - 1) * 64 + o0 + off(e)) * NV + v0 + v] = a[v][e];
         h2p::consumer_sync(kConsumers);
         if (ks == 0 && mine)
             for (int sl = 1; sl < S; ++sl)
 #pragma unroll
                 for (int v = 0; v < VT; ++v)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) a[v][e] += red[((sl - 1) * 64 + o0 + e) * NV + v0 + v];
+                    for (int e = 0; e < OUT; ++e) a[v][e] += red[((sl - 1) * 64 + o0 + off(e)) * NV + v0 + v];
         return ks == 0 && mine;
     }
     __device__ __forceinline__ void store(T *dst, int ld, int nv, int R) const
     {
-        const bool vec = (ld & 3) == 0 && o0 + 4 <= R;
 #pragma unroll
         for (int v = 0; v < VT; ++v) {
             if (v0 + v >= nv) break;
             T *d = dst + (v0 + v) * ld + o0;
-            if (vec) {
-                AccW<T, 32>::store4(d, a[v]);
-            } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (o0 + e < R) d[e] = a[v][e];
+            for (int h = 0; h < OUT / 4; ++h) {
+                if ((ld & 3) == 0 && o0 + QS * h + 4 <= R) {
+                    AccW<T, 32>::store4(d + QS * h, *reinterpret_cast<const T(*)[4]>(a[v] + 4 * h));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (o0 + QS * h + e < R) d[QS * h + e] = a[v][4 * h + e];
+                }
             }
         }
     }
 };
 
 // Accumulator of the block streams (k_stream, k_stream_batch): the split-column form for 8
-// and 16 vectors.
+// and 16 vectors; at 32 vectors AccW's unsplit 4 x 4 block (the split 8 x 4 form measured
+// 41.8 against 38.7 ms for the 2^21-point FP32 product: its second output quad doubles the
+// tile loads per thread without raising the FMAs per vector load).
 template <typename T, int NVMAX>
 using AccStreamOf =
-    typename std::conditional<(NVMAX >= kWideMin && NVMAX < 32), AccWK<T, NVMAX>, AccOf<T, NVMAX>>::type;
+    typename std::conditional<(NVMAX >= kWideMin && NVMAX < 32), AccWK<T, NVMAX, 4>, AccOf<T, NVMAX>>::type;
 
 // ------------------------------------------------------------------ gather
 
