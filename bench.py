@@ -428,6 +428,26 @@ def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024):
         g.upload("fp64")
         y0 = op.matvec(X).cpu().numpy()
         y1 = g.matvec(X).cpu().numpy()
+        # what the compression buys: the FP32 product (nv = 1, L2 flushed) of both operators
+        prod = {}
+        X32 = X.float()
+        flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        for name, o in (("uncompressed", op), ("compressed", g)):
+            o.upload("fp32")
+            Y32 = torch.empty_like(X32)
+            for _ in range(3):
+                o.matvec(X32, Y32)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for a, b in evs:
+                flush.zero_()
+                a.record()
+                o.matvec(X32, Y32)
+                b.record()
+            torch.cuda.synchronize()
+            prod[name] = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+            prod[name + "_device_GB"] = h2.h2_get_info(o.handle).device_bytes / 1e9
+        prod["speedup"] = prod["uncompressed"] / prod["compressed"]
+        del flush
         total_ms = float(ms.sum())
         gflops = float(flops.sum()) / (total_ms * 1e-3) / 1e9
         out[w.name] = {
@@ -442,6 +462,7 @@ def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024):
             "lowrank_GB_in": info.lowrank_bytes_in / 1e9, "lowrank_GB_out": info.lowrank_bytes_out / 1e9,
             "lowrank_reduction": info.lowrank_bytes_in / max(info.lowrank_bytes_out, 1),
             "relerr_vs_uncompressed": float(np.linalg.norm(y1 - y0) / np.linalg.norm(y0)),
+            "product_fp32_ms": prod,
             "error_bound_rel": float(2 * np.sqrt(info.dropped_energy) * np.linalg.norm(x) / np.linalg.norm(y0)),
             "roofline": {"kernel": "h2_compress (FP64 QR / Jacobi SVD / small products, CUDA cores)", "bound": "alu",
                          "achieved": gflops / 1e3, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
