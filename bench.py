@@ -734,6 +734,10 @@ def main():
                    "dense_blocks": info.n_dense, "parallelism": f"replicas x{world}",
                    "l2": "flushed (512 MB write) before every timed product"},
         "gflops": world * flops / (ms_step * 1e-3) / 1e9,
+        # the paper's protocol (Sec. 6): the mean of the runs left after dropping the fastest
+        # and the slowest, here over this rank's timed products
+        "ms_trimmed_mean": float(np.mean(sorted(res["step_ms"])[1:-1])) if len(res["step_ms"]) > 2 else ms_step,
+        "ms_median": float(np.median(res["step_ms"])),
         "bytes_per_step": bytes_step,
         "frac_of_hbm": (bytes_step / (ms_step * 1e-3) / 1e9) / peak_hbm,
         "phases_ms": dict(zip(h2.PHASES, [float(v) for v in res["phase_ms"]])),
