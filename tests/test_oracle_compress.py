@@ -164,3 +164,17 @@ def test_coarse_tolerance_keeps_the_bound(built):
     err = np.linalg.norm(c.assemble_lowrank() - alr)
     bound = 2.0 * np.sqrt(sum(float(np.sum(d ** 2)) for d in c.dropped.values()))
     assert err <= bound * (1 + 1e-8) and max(c.ranks) <= 3
+
+
+def test_3d_grid_set_at_a_small_size():
+    # the 3D compression set's recipe (grid, exp(-r/0.2), leaf 64, tri-cubic, eta 0.95) at 12^3
+    w = si.COMPRESS_3D
+    pts = si.grid_3d(12)
+    orc = oracle.OracleH2(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    alr = oc.lowrank_part(orc)
+    c = oc.CompressedH2(orc, si.COMPRESS_TAU)
+    err = np.linalg.norm(c.assemble_lowrank() - alr)
+    bound = 2.0 * np.sqrt(sum(float(np.sum(d ** 2)) for d in c.dropped.values()))
+    assert err <= bound * (1 + 1e-8) + 1e-12 * np.linalg.norm(alr)
+    before, after = c.lowrank_bytes()
+    assert max(c.ranks) < c.k and after < before
