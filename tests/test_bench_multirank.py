@@ -75,12 +75,7 @@ def test_reference_arm_line_on_rank_zero():
 
 
 def test_batch_roofline_takes_the_slower_bound():
-    import importlib.util
-    import os
-    spec = importlib.util.spec_from_file_location(
-        "bench_mod", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
-    b = importlib.util.module_from_spec(spec)
-    spec.loader.exec_module(b)
+    b = bench
     peak, _ = b.measured_peaks()
     r = b.batch_roofline(peak * 1e9 * 1e-3, 0.0, 2.0)  # 1 ms of bytes, measured 2 ms
     assert r["bound"] == "hbm" and abs(r["frac"] - 0.5) < 1e-12 and abs(r["bound_ms"] - 1.0) < 1e-12
