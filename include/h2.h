@@ -245,7 +245,8 @@ int h2_load(const char *path, h2_handle *out);
  * Synchronises the stream. Errors: H2_EINVAL, H2_ENOMEM, H2_ECUDA. */
 typedef struct {
     double tau;
-    double norm_lowrank;           /* ||A_lr||_F, A_lr the low-rank part (sum over leaves of ||R_t||_F^2) */
+    double norm_lowrank;           /* ||A_lr||_F, A_lr the low-rank part: its square is the sum
+                                      over leaves of ||R_t||_F^2 */
     double dropped_energy;         /* sum of the squares of the singular values not kept:
                                       ||A_lr - A'_lr||_F <= 2 sqrt(dropped_energy) */
     int depth;
@@ -254,7 +255,8 @@ typedef struct {
     int level_rank[H2_MAX_LEVELS]; /* rank of each level after truncation */
     double ms[4];                  /* device time of steps 1-4 (CUDA events) */
     double flops[4];               /* FP64 operations of steps 1-4 as the kernels perform them */
-    int64_t jacobi_sweeps;         /* one-sided Jacobi sweeps over all SVDs of step 3 */
+    int64_t jacobi_sweeps;         /* FP64 one-sided Jacobi sweeps over all SVDs of step 3 (after
+                                      each SVD's FP32 sweeps, which are not counted) */
     size_t lowrank_bytes_in;       /* FP64 bytes of bases, transfers and coupling blocks */
     size_t lowrank_bytes_out;      /* the same at the level ranks of the result */
 } h2_compress_info;
