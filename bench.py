@@ -1,13 +1,17 @@
 #!/usr/bin/env python3
-"""Benchmark: H^2 matrix-vector product on GB300, memory-bound single-vector workload.
+"""Benchmark: H^2 matrix-vector product on GB300 at the paper's precision (FP64).
 
 Workload (default): N = 2^20 points on a 1024 x 1024 grid in [0,1]^2, Gaussian kernel
 exp(-r^2/0.01), leaf size 64, 8 x 8 Chebyshev grid (rank 64), eta = 0.7, nv = 1,
 x ~ N(0,1). A step is one full product Y = A_H2 X (upsweep, all-level coupling
-product, dense near field, downsweep, epilogue) in FP32. The headline metric is the
-algorithmic HBM throughput of the product: the operator entries it must stream (coupling
-blocks, dense blocks, leaf bases twice, transfers twice) plus X read and Y written,
-divided by the device time of one product. Gflop/s counts 2 flops per entry per vector.
+product, dense near field, downsweep, epilogue) in FP64, the precision of every product
+in the paper's experiments (Sec. 6). The headline metric is the algorithmic HBM throughput
+of the product: the operator entries it must stream (coupling blocks, dense blocks, leaf
+bases twice, transfers twice) plus X read and Y written, divided by the device time of one
+product. Gflop/s counts 2 flops per entry per vector. The FP64 product is bound by the FP64
+fused multiply-add rate of the part, which the bench measures first (h2_measure_peak); its
+roofline object compares the dominant kernel against that measured rate. The same product
+in FP32 (HBM-bound) is reported beside it under "fp32", with its own roofline and e2e.
 
 Timing: W warm-up products, then K timed products with the L2 flushed (a 512 MB write)
 before each one, outside the events; CUDA events on the launching stream; barrier and
@@ -15,7 +19,7 @@ synchronize on both sides; max over ranks. Several GPUs run independent replicas
 (no collective on the data path): the value is the sum over ranks.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload
-family instead (rank 0 only).
+family instead (rank 0 only), one oracle process per host core.
 """
 from __future__ import annotations
 
@@ -36,8 +40,10 @@ sys.path.insert(0, ROOT)
 
 import synthetic_inputs as si  # noqa: E402
 
-METRIC = "H2 matvec GB/s (nv=1, 2D Gaussian grid N=2^20, rank 64)"
-FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 CUDA-core peak at the maximum SM clock
+METRIC = "H2 matvec GB/s (nv=1, FP64, 2D Gaussian grid N=2^20, rank 64)"
+# FP32 CUDA-core rate from unit counts at the maximum SM clock; only used where no measured
+# rate is at hand (CPU-side tests of the roofline arithmetic)
+FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -133,11 +139,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(grid: int):
+def kernel_traffic(grid: int, prec: str = "fp32"):
     """DRAM bytes per launch of the streaming kernel from the committed ncu capture, or
     None when the capture was of another workload or the kernel source changed since."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_stream_traffic_grid1024_fp32.json")
+    path = os.path.join(ROOT, "profiles", f"k_stream_traffic_grid1024_{prec}.json")
     if grid != 1024 or not os.path.exists(path):
         return None
     rec = json.load(open(path))
@@ -149,14 +155,120 @@ def kernel_traffic(grid: int):
     return rec["traffic_bytes_per_launch"]
 
 
-def cpu_baseline(steps: int = 0):
-    """The oracle (plain FP64 C, 1 thread) on a bounded sample: the same workload family
-    at N = 2^16 (256 x 256 grid, same kernel, rank, leaf size and eta), blocks stored."""
+def measure_device_peaks(h2, gpu: int):
+    """Arithmetic rates of this GPU, measured by h2_measure_peak (register-resident chains of
+    one instruction kind on every SM, CUDA-event timed, nothing else running): the FP64 and
+    FP32 fused multiply-add rates and the special-function 2^x rate as bursts (fastest of five
+    30 ms launches), and the FP64 rate that bounds the headline product also sustained
+    (fastest of five 400 ms launches), with the SM clocks sampled meanwhile. No clock or power
+    setting is touched."""
+    with ClockSampler(gpu) as clk:
+        dfma, _ = h2.h2_measure_peak("dfma", 30.0)
+        ffma, _ = h2.h2_measure_peak("ffma", 30.0)
+        ex2, _ = h2.h2_measure_peak("ex2", 30.0)
+        dfma_s, _ = h2.h2_measure_peak("dfma", 400.0)
+    return {"dfma_tflops": dfma / 1e12, "dfma_tflops_sustained": dfma_s / 1e12, "ffma_tflops": ffma / 1e12,
+            "ex2_per_s": ex2, "clocks": clk.summary(),
+            "how": "h2_measure_peak: per thread 4 FMA accumulators with rotating multiplicands or 8 FMA chains "
+                   "(the faster form; 8 ex2 chains), 32 warps per SM on every SM, fastest of 5 launches of ~30 ms "
+                   "(burst) or ~400 ms (sustained) per form, CUDA events"}
+
+
+def bottom_stream_entries(info):
+    """Coupling entries of the levels the main streaming kernel takes (the lowest
+    min(depth, 4) + 1 levels; the upper levels run on the side stream) and dense entries."""
+    lb = info.depth - min(info.depth, 4)
+    blocks = sum(int(info.coupling_per_level[l]) for l in range(lb, info.depth + 1))
+    return blocks * info.rank * info.rank, int(info.dense_entries)
+
+
+def stream_roofline(kernel, nbytes, flops, ms, alu_peak_tflops, alu_kind, peak_hbm, hbm_kind, traffic=None):
+    """Roofline of one streaming launch: its algorithmic bytes at the measured copy bandwidth or
+    its flops at the measured arithmetic rate, whichever takes longer, against its measured
+    duration. achieved / peak in the bound's own unit; frac = achieved / peak."""
+    t_hbm = nbytes / (peak_hbm * 1e9)
+    t_alu = flops / (alu_peak_tflops * 1e12)
+    sec = ms * 1e-3
+    if t_alu > t_hbm:
+        r = {"kernel": kernel, "bound": "alu", "achieved": flops / sec / 1e12, "peak": alu_peak_tflops,
+             "unit": "TFLOP/s", "peak_kind": alu_kind}
+    else:
+        r = {"kernel": kernel, "bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peak_hbm, "unit": "GB/s",
+             "peak_kind": hbm_kind}
+    r["frac"] = r["achieved"] / r["peak"]
+    r["traffic"] = traffic
+    r.update({"algorithmic_bytes": int(nbytes), "algorithmic_flops": int(flops), "ms": ms,
+              "bound_ms": 1e3 * max(t_hbm, t_alu), "hbm_GB/s": nbytes / sec / 1e9,
+              "hbm_frac": nbytes / sec / 1e9 / peak_hbm})
+    return r
+
+
+def _oracle_sample(side: int):
     import oracle
-    w = si.grid_gauss(256)
+    w = si.grid_gauss(side)
     pts = w.make_points()
     h = oracle.OracleH2(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta, assemble=True)
     x = w.make_x(len(pts))
+    return h, x, 8 * (oracle_entry_counts(h) + 2 * len(pts)), 2 * oracle_entry_counts(h)
+
+
+def _oracle_worker(side, reps, barrier, queue):
+    """One oracle process of the all-cores baseline: build the sample, wait for the others,
+    time `reps` products back to back."""
+    try:
+        h, x, nbytes, flops = _oracle_sample(side)
+        h.matvec(x)  # warm-up
+        barrier.wait()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            h.matvec(x)
+        queue.put((time.perf_counter() - t0, reps, nbytes, flops, None))
+    except Exception as exc:  # reported to the parent, which fails loudly
+        try:
+            barrier.abort()
+        except Exception:
+            pass
+        queue.put((0.0, 0, 0, 0, f"{type(exc).__name__}: {exc}"))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_all_cores(side: int = 256, reps: int = 5, workers: int = 0):
+    """The oracle on every host core: `workers` independent processes (spawned, so that no
+    CUDA state is inherited), each running its own products of the sample; the aggregate is
+    the bytes of all products over the slowest process's time. The oracle itself is unchanged
+    (one thread per product)."""
+    import multiprocessing as mp
+    workers = workers or host_cores()
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(side, reps, barrier, queue)) for _ in range(workers)]
+    for p in procs:
+        p.start()
+    res = [queue.get(timeout=900) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    errs = [r[4] for r in res if r[4]]
+    if errs:
+        raise RuntimeError(f"oracle worker failed: {errs[0]}")
+    t = max(r[0] for r in res)
+    nbytes = sum(r[1] * r[2] for r in res)
+    flops = sum(r[1] * r[3] for r in res)
+    return {"value": nbytes / t / 1e9, "unit": "GB/s", "cores": workers, "gflops": flops / t / 1e9,
+            "wall_s": t, "products": sum(r[1] for r in res)}
+
+
+def cpu_baseline(steps: int = 0, all_cores: bool = True):
+    """The oracle (plain FP64 C, one thread per product) on a bounded sample: the same
+    workload family at N = 2^16 (256 x 256 grid, same kernel, rank, leaf size and eta),
+    blocks stored; one process on one core, and one process per host core."""
+    h, x, nbytes, flops = _oracle_sample(256)
     h.matvec(x)  # warm-up
     nrep = steps if steps > 0 else 5
     times = []
@@ -164,16 +276,24 @@ def cpu_baseline(steps: int = 0):
         t0 = time.perf_counter()
         h.matvec(x)
         times.append(time.perf_counter() - t0)
-    ent = oracle_entry_counts(h)
-    nbytes = 8 * (ent + 2 * len(pts))
     t = statistics.mean(times)
-    return {"value": nbytes / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"256x256 grid (N=65536) of the same kernel/rank/leaf/eta, FP64 blocks stored, "
-                      f"{nrep} products, mean {t * 1e3:.0f} ms", "ms_per_product": t * 1e3,
-            "gflops": 2 * ent / t / 1e9}
+    one = {"value": nbytes / t / 1e9, "unit": "GB/s", "cores": 1, "ms_per_product": t * 1e3,
+           "gflops": flops / t / 1e9}
+    out = {"value": one["value"], "unit": "GB/s", "cores": 1, "cores_available": host_cores(), "kind": "oracle",
+           "sample": f"256x256 grid (N=65536) of the same kernel/rank/leaf/eta, FP64 blocks stored, "
+                     f"{nrep} products, mean {t * 1e3:.0f} ms", "ms_per_product": t * 1e3, "one_core": one}
+    if all_cores:
+        allc = oracle_all_cores(256, nrep)
+        out.update({"value": allc["value"], "cores": allc["cores"],
+                    "sample": f"256x256 grid (N=65536) of the same kernel/rank/leaf/eta, FP64 blocks stored; "
+                              f"{allc['cores']} oracle processes, {nrep} products each, aggregate over "
+                              f"{allc['wall_s']:.1f} s (one core: {t * 1e3:.0f} ms per product)",
+                    "all_cores": allc})
+    return out
 
 
-def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with_fp64=True):
+def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with_fp64=True,
+              ffma_peak=FFMA_PEAK_TFLOPS, dfma_peak=None):
     """The multi-vector workload: N = 2^21 uniform random points in [0,1]^3, exp(-r/0.2),
     leaf 64, 4 x 4 x 4 Chebyshev grid (rank 64), eta 0.7, 32 vectors, in split-BF16 on the
     tensor cores and in FP32. Its ~113 GB of stored blocks exceed L2 by far, so no flush is
@@ -227,21 +347,23 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with
         seg = 4 * nv * ((info.n_nodes + 1) * info.rank + n)
         blk_bytes = 4 * (info.coupling_entries + info.dense_entries) + 2 * seg
         blk_gbs = blk_bytes / (float(phase_ms[1]) * 1e-3) / 1e9
+        blk_tflops = 2 * (info.coupling_entries + info.dense_entries) * nv / (float(phase_ms[1]) * 1e-3) / 1e12
         if prec == "bf16x2":
             roof = {"kernel": "k_stream_tc (split-BF16 tcgen05, 128x64x16 MMAs, FP32 accumulation in TMEM)",
                     "bound": "hbm", "achieved": blk_gbs, "peak": peak_hbm, "unit": "GB/s",
                     "frac": blk_gbs / peak_hbm, "peak_kind": peak_kind, "algorithmic_bytes": blk_bytes}
         else:
-            # 16 flop per byte at 32 vectors: the FP32 stream is bound by the CUDA-core FMA
-            # rate, 152 SMs x 128 lanes x 2 flop x the maximum SM clock
-            blk_tflops = 2 * (info.coupling_entries + info.dense_entries) * nv / (float(phase_ms[1]) * 1e-3) / 1e12
+            # 16 flop per byte at 32 vectors: the FP32 stream is bound by the CUDA-core FMA rate
             roof = {"kernel": "k_stream (FP32, register-blocked wide accumulator)", "bound": "alu",
-                    "achieved": blk_tflops, "peak": FFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": blk_tflops / FFMA_PEAK_TFLOPS, "peak_kind": "derived (unit counts x clock)",
+                    "achieved": blk_tflops, "peak": ffma_peak, "unit": "TFLOP/s",
+                    "frac": blk_tflops / ffma_peak, "peak_kind": "measured (h2_measure_peak, FP32 FMA chains)",
                     "hbm_GB/s": blk_gbs}
         if prec == "fp64":
+            # 8 flop per FP64 byte at 32 vectors: bound by the FP64 FMA rate
             roof = {"kernel": "k_stream (FP64, register-blocked wide accumulator)", "bound": "alu",
-                    "note": "DFMA-bound: 16 flop per FP64 byte at 32 vectors; FP64 rate is a small fraction of FP32"}
+                    "achieved": blk_tflops, "peak": dfma_peak, "unit": "TFLOP/s",
+                    "frac": blk_tflops / dfma_peak if dfma_peak else None,
+                    "peak_kind": "measured (h2_measure_peak, FP64 FMA chains)"}
             gbs = 8 * (mat_entries + vec_elems) / (ms_step * 1e-3) / 1e9
         out[prec] = {"ms_per_step": ms_step, "ms_median": float(np.median(ms)), "GB/s": gbs,
                      "gflops": flops / (ms_step * 1e-3) / 1e9, "frac_of_hbm": gbs / peak_hbm,
@@ -323,13 +445,14 @@ def serve_benchmark(h2, torch, requests_per_rate=32, maxit=100, rates=(0.5, 0.8,
             op.close()
 
 
-def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, Y_stored):
+def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, Y_stored, ex2_peak):
     """The same product with the coupling and dense entries evaluated in FP32 inside the
-    stream (H2_FP32_MF: no blocks stored; bases and transfers as in FP32). Its bound is the
-    arithmetic of the evaluations: one special-function operation per Gaussian entry, at
-    most 152 SMs x 16 per clock x 2.07 GHz; the measured rate is evaluations per second over
-    the block stream's time. The L2 is flushed before every timed product, as for the stored
-    path."""
+    stream (H2_FP32_MF: no blocks stored; bases and transfers as in FP32). The reported rate is
+    evaluations per second over the block stream's time, against the measured special-function
+    rate (2^x results per second, h2_measure_peak): one special-function operation per entry
+    for the exponential kernels' generic path (the separable Gaussian path forms its entries
+    from tables with multiplies, so for it this is a rate, not a bound). The L2 is flushed
+    before every timed product, as for the stored path."""
     info = op.info
     evals = info.coupling_entries + info.dense_entries
     ref = Y_stored.double().cpu().numpy()
@@ -353,7 +476,7 @@ def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, 
     phase_ms = phase_ms / max(prods, 1)
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     got = Y.double().cpu().numpy()
-    sfu_peak = 152 * 16 * 2.07e9
+    sfu_peak = ex2_peak
     stream_rate = evals / (float(phase_ms[1]) * 1e-3)
     out = {"ms_per_step": ms, "speedup_vs_stored": stored_ms / ms, "evaluations_per_step": evals,
            "evaluations_per_s": evals / (ms * 1e-3), "device_bytes": h2.h2_get_info(op.handle).device_bytes,
@@ -362,12 +485,12 @@ def matrix_free(h2, torch, op, x_host, flush, stream, steps, warmup, stored_ms, 
            "roofline": {"kernel": "k_stream_mf (FP32 evaluation of coupling and dense entries)", "bound": "alu",
                         "achieved": stream_rate, "peak": sfu_peak, "unit": "evaluations/s",
                         "frac": stream_rate / sfu_peak,
-                        "peak_kind": "derived: 152 SMs x 16 special-function results per clock x 2.07 GHz"}}
+                        "peak_kind": "measured (h2_measure_peak, ex2 chains)"}}
     op.upload("fp32")
     return out
 
 
-FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the part (CUDA cores); no tensor-core FP64 path
+FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the part; only used where no measured rate is at hand
 
 
 def compress_oracle_sample(h2, torch):
@@ -394,7 +517,7 @@ def compress_oracle_sample(h2, torch):
             "cores": 1, "oracle_s": cpu_s, "gpu_ms": gpu_ms, "ranks_equal": same}
 
 
-def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024):
+def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024, dfma_peak=None):
     """Algebraic recompression (Sec. 5) of the compression sets of Sec. 6 (synthetic_inputs
     COMPRESS_2D at N = 2^20, COMPRESS_3D at N = 2^18) to tau = 1e-3 on the GPU in FP64. Per
     set: device time of each step (CUDA events inside h2_compress, mean over `steps` calls
@@ -467,8 +590,10 @@ def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024):
             "product_fp32_ms": prod,
             "error_bound_rel": float(2 * np.sqrt(info.dropped_energy) * np.linalg.norm(x) / np.linalg.norm(y0)),
             "roofline": {"kernel": "h2_compress (FP64 QR / Jacobi SVD / small products, CUDA cores)", "bound": "alu",
-                         "achieved": gflops / 1e3, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": gflops / 1e3 / FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 rate"},
+                         "achieved": gflops / 1e3, "peak": dfma_peak or FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": gflops / 1e3 / (dfma_peak or FP64_PEAK_TFLOPS),
+                         "peak_kind": "measured (h2_measure_peak, FP64 FMA chains)" if dfma_peak
+                         else "nominal FP64 rate"},
         }
         g.close()
         op.close()
@@ -476,20 +601,23 @@ def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024):
     return out
 
 
-def batch_roofline(total_bytes, total_flops, ms):
+def batch_roofline(total_bytes, total_flops, ms, ffma_peak=None):
     """The batch's bound: its blocks streamed once at the measured copy bandwidth, or its
-    flops at the FP32 FMA peak, whichever takes longer; frac = that time / the measured one."""
+    flops at the FP32 FMA rate (measured when given), whichever takes longer; frac = that
+    time / the measured one."""
     peak_gbs, kind = measured_peaks()
+    fma = ffma_peak or FFMA_PEAK_TFLOPS
     t_hbm = total_bytes / (peak_gbs * 1e9) * 1e3
-    t_fma = total_flops / (FFMA_PEAK_TFLOPS * 1e12) * 1e3
+    t_fma = total_flops / (fma * 1e12) * 1e3
     bound = "hbm" if t_hbm >= t_fma else "alu"
     return {"bound": bound, "bound_ms": max(t_hbm, t_fma), "hbm_ms": t_hbm, "fma_ms": t_fma,
             "achieved": total_bytes / (ms * 1e-3) / 1e9 if bound == "hbm" else total_flops / (ms * 1e-3) / 1e12,
-            "peak": peak_gbs if bound == "hbm" else FFMA_PEAK_TFLOPS, "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
-            "frac": max(t_hbm, t_fma) / ms, "peak_kind": f"{kind} HBM / derived FP32 FMA"}
+            "peak": peak_gbs if bound == "hbm" else fma, "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
+            "frac": max(t_hbm, t_fma) / ms,
+            "peak_kind": f"{kind} HBM / {'measured' if ffma_peak else 'derived'} FP32 FMA"}
 
 
-def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with_fp64=True):
+def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with_fp64=True, ffma_peak=None):
     """Batched products of 64 uneven operators (synthetic_inputs.uneven_batch: N log-uniform
     in [2^12, 2^18], even members 2D grids with orders 4-8, odd members 3D clouds with orders
     3-4, exp(-r/l) with l in [0.05, 0.3], leaf 64, eta 0.7, nv in 1..16), FP32, as one
@@ -558,7 +686,7 @@ def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with
                 "batched_gflops": total_flops / (mb * 1e-3) / 1e9,
                 "sequential_ms": msq, "sequential_GB/s": total_bytes / (msq * 1e-3) / 1e9,
                 "speedup_vs_sequential": msq / mb, "create_s": create_s, "configuration": desc,
-                "roofline": batch_roofline(total_bytes, total_flops, mb),
+                "roofline": batch_roofline(total_bytes, total_flops, mb, ffma_peak),
                 "fp64": fp64, "l2": "inputs larger than L2, no flush"}
     finally:
         for op in ops:
@@ -566,18 +694,25 @@ def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with
 
 
 def run_reference(args, rank):
+    """The reference arm: the FP64 oracle (the reference is a paper; the oracle written from
+    it is the comparison program) on every host core, one process per core, each step one
+    product per process on the bounded sample; rank 0 only."""
     if rank != 0:
         return
-    res = None
-    res = cpu_baseline(steps=max(1, args.steps))
-    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "GB/s",
+    nrep = max(1, args.steps)
+    allc = oracle_all_cores(256, nrep)
+    ms_step = 1e3 * allc["wall_s"] / nrep
+    sample = (f"256x256 grid (N=65536) of the same kernel/rank/leaf/eta, FP64 blocks stored; {allc['cores']} oracle "
+              f"processes, {nrep} products each")
+    line = {"impl": "reference", "metric": METRIC, "value": allc["value"], "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": res["ms_per_product"], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "grid256_gauss (bounded sample of grid1024_gauss)", "n": 65536, "nv": 1,
                        "rank": 64, "leaf": 64, "eta": 0.7},
-            "cpu_baseline": {k: res[k] for k in ("kind", "cores", "sample", "value", "unit")},
-            "e2e": {"value": res["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"kind": "oracle", "cores": allc["cores"], "cores_available": host_cores(),
+                             "sample": sample, "value": allc["value"], "unit": "GB/s"},
+            "e2e": {"value": allc["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -587,8 +722,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 product beside the FP64 headline")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 counterparts of the batch and multi-vector measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the arithmetic-rate measurements and use nominal rates (profiler captures only)")
     ap.add_argument("--no-multi-rhs", action="store_true",
                     help="skip the 32-vector measurement on the 2^21-point 3D cloud")
     ap.add_argument("--cloud-n", type=int, default=2 ** 21,
@@ -675,62 +814,96 @@ def main():
         return {"prec": prec, "esize": es, "step_ms": step_ms, "phase_ms": phase_ms / max(prods, 1),
                 "phase_launches": phase_launches, "products": prods, "upload_s": upload_s, "X": X, "Y": Y}
 
-    res_fp64 = None
-    if not args.no_fp64:
-        res_fp64 = time_products("fp64", max(3, args.steps // 2), max(3, args.warmup))
-        del res_fp64["X"], res_fp64["Y"]
+    if args.no_peaks:
+        peaks = {"dfma_tflops": FP64_PEAK_TFLOPS, "dfma_tflops_sustained": FP64_PEAK_TFLOPS,
+                 "ffma_tflops": FFMA_PEAK_TFLOPS, "ex2_per_s": 152 * 32 * 2.07e9, "how": "nominal (not measured)"}
+    else:
+        peaks = measure_device_peaks(h2, local)
+    dfma_peak = max(peaks["dfma_tflops"], peaks["dfma_tflops_sustained"])
+    ffma_peak = peaks["ffma_tflops"]
+    rate_kind = "nominal (not measured)" if args.no_peaks else "measured (h2_measure_peak, {} FMA chains)"
+    cpl_entries, dns_entries = bottom_stream_entries(info)
+    # the dominant kernel (phase 1, the streaming product of the lower levels' coupling rows
+    # and of all dense rows): its blocks, one read of each input segment tree and one write of
+    # each output segment; 2 flops per block entry
+    seg_elems = 2 * ((info.n_nodes + 1) * info.rank + n)
+    stream_flops = 2 * (cpl_entries + dns_entries)
 
+    def e2e(X, Y, es):
+        """End to end through the public API: pinned host X -> device, product, Y -> host."""
+        dt = torch.float64 if es == 8 else torch.float32
+        xh = torch.from_numpy(x_host.astype(np.float64 if es == 8 else np.float32)).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        for _ in range(3):
+            X.copy_(xh, non_blocking=True)
+            op.matvec(X, Y)
+            yh.copy_(Y, non_blocking=True)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            X.copy_(xh, non_blocking=True)
+            op.matvec(X, Y)
+            yh.copy_(Y, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / args.steps
+        assert X.dtype == dt
+        return {"value": job_gbs(world, es * (mat_entries + vec_elems), max_over_ranks(e2e_ms, dist, "cuda")),
+                "unit": "GB/s", "h2d_bytes_per_step": es * n, "d2h_bytes_per_step": es * n}
+
+    # ---- headline: FP64
     with ClockSampler(local) as clk:
-        res = time_products("fp32", args.steps, max(3, args.warmup))
+        res = time_products("fp64", args.steps, max(3, args.warmup))
     clocks = clk.summary()
     ms_local = float(np.sum(res["step_ms"]))
     ms_total = max_over_ranks(ms_local, dist, "cuda")
     ms_step = ms_total / args.steps
-    bytes_step = 4 * (mat_entries + vec_elems)
+    bytes_step = 8 * (mat_entries + vec_elems)
     value = job_gbs(world, bytes_step, ms_step)
+    roof64 = stream_roofline("k_stream<double,1> (coupling rows of the lower levels + dense rows, Alg 4 + A_de x)",
+                             8 * (cpl_entries + dns_entries + seg_elems), stream_flops, float(res["phase_ms"][1]),
+                             dfma_peak, rate_kind.format("FP64"), peak_hbm, peak_kind,
+                             kernel_traffic(args.grid, "fp64"))
+    e2e64 = e2e(res["X"], res["Y"], 8)
+    launches_per_product = int(np.sum(res["phase_launches"])) // max(res["products"], 1)
+    Y64 = res["Y"].cpu().numpy()
+    del res["X"], res["Y"]
 
-    # roofline of the dominant kernel: the streaming product of coupling rows (levels below
-    # the top) and dense rows (phase 1); its algorithmic bytes are the blocks it streams plus
-    # one read of each input segment tree and one write of each output segment
-    cpl_bytes = 4 * (info.coupling_entries + info.dense_entries + 2 * (info.n_nodes + 1) * info.rank + 2 * n)
-    cpl_ms = float(res["phase_ms"][1])
-    cpl_gbs = cpl_bytes / (cpl_ms * 1e-3) / 1e9
-    traffic = kernel_traffic(args.grid)
-
-    # end to end through the public API: pinned host X -> device, product, Y -> host
-    X = res["X"]
-    Y = res["Y"]
-    xh = torch.from_numpy(x_host.astype(np.float32)).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    for _ in range(3):
-        X.copy_(xh, non_blocking=True)
-        op.matvec(X, Y)
-        yh.copy_(Y, non_blocking=True)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        X.copy_(xh, non_blocking=True)
-        op.matvec(X, Y)
-        yh.copy_(Y, non_blocking=True)
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    e2e_value = job_gbs(world, bytes_step, max_over_ranks(e2e_ms, dist, "cuda"))
+    # ---- the same product in FP32 (HBM-bound)
+    fp32 = None
+    if not args.no_fp32:
+        with ClockSampler(local) as clk32:
+            r32 = time_products("fp32", args.steps, max(3, args.warmup))
+        ms32 = max_over_ranks(float(np.sum(r32["step_ms"])), dist, "cuda") / args.steps
+        b32 = 4 * (mat_entries + vec_elems)
+        fp32 = {"value": job_gbs(world, b32, ms32), "unit": "GB/s", "ms_per_step": ms32,
+                "ms_median": float(np.median(r32["step_ms"])), "gflops": world * flops / (ms32 * 1e-3) / 1e9,
+                "bytes_per_step": b32, "frac_of_hbm": (b32 / (ms32 * 1e-3) / 1e9) / peak_hbm,
+                "phases_ms": dict(zip(h2.PHASES, [float(v) for v in r32["phase_ms"]])),
+                "roofline": stream_roofline("k_stream<float,1> (coupling rows of the lower levels + dense rows)",
+                                            4 * (cpl_entries + dns_entries + seg_elems), stream_flops,
+                                            float(r32["phase_ms"][1]), ffma_peak,
+                                            rate_kind.format("FP32"), peak_hbm, peak_kind,
+                                            kernel_traffic(args.grid, "fp32")),
+                "e2e": e2e(r32["X"], r32["Y"], 4), "clocks": clk32.summary(), "upload_s": r32["upload_s"],
+                "relerr_vs_fp64": float(np.linalg.norm(r32["Y"].double().cpu().numpy() - Y64) / np.linalg.norm(Y64))}
+        res32_Y = r32["Y"]
+        del r32["X"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             cpu = cpu_baseline()
-            cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            cpu = {k: cpu[k] for k in ("value", "unit", "cores", "cores_available", "kind", "sample", "one_core",
+                                       "all_cores") if k in cpu}
         except Exception as exc:  # the baseline is context; its failure must not hide the GPU line
             cpu = {"value": None, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
 
-    launches_per_product = int(np.sum(res["phase_launches"])) // max(res["products"], 1)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": n, "nv": 1, "rank": info.rank, "leaf": info.leaf_size, "eta": w.eta,
                    "kernel": "exp(-r^2/0.01)", "depth": info.depth, "coupling_blocks": info.n_coupling,
                    "dense_blocks": info.n_dense, "parallelism": f"replicas x{world}",
@@ -741,21 +914,28 @@ def main():
         "ms_trimmed_mean": float(np.mean(sorted(res["step_ms"])[1:-1])) if len(res["step_ms"]) > 2 else ms_step,
         "ms_median": float(np.median(res["step_ms"])),
         "bytes_per_step": bytes_step,
+        "flops_per_step": flops,
         "frac_of_hbm": (bytes_step / (ms_step * 1e-3) / 1e9) / peak_hbm,
+        # the whole product against its bound: every flop at the measured FP64 FMA rate or
+        # every byte at the measured copy bandwidth, whichever takes longer
+        "product_bound_ms": 1e3 * max(flops / (dfma_peak * 1e12), bytes_step / (peak_hbm * 1e9)),
         "phases_ms": dict(zip(h2.PHASES, [float(v) for v in res["phase_ms"]])),
-        "roofline": {"kernel": "k_stream (coupling rows + dense rows, Alg 4 + A_de x)", "bound": "hbm",
-                     "achieved": cpl_gbs, "peak": peak_hbm, "unit": "GB/s", "frac": cpl_gbs / peak_hbm,
-                     "peak_kind": peak_kind, "traffic": traffic, "algorithmic_bytes": cpl_bytes},
-        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n},
+        "roofline": roof64,
+        "e2e": e2e64,
         "gpu_launches": launches_per_product * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "peaks": peaks,
         "build_s": build_s, "upload_s": res["upload_s"],
     }
-    if not args.no_matrix_free:
+    line["product_bound_frac"] = line["product_bound_ms"] / ms_step
+    if fp32 is not None:
+        line["fp32"] = fp32
+    if not args.no_matrix_free and fp32 is not None:
         try:
             line["matrix_free"] = matrix_free(h2, torch, op, x_host, flush, stream, max(20, args.steps // 4),
-                                              max(3, args.warmup), ms_step, res["Y"])
+                                              max(3, args.warmup), fp32["ms_per_step"], res32_Y,
+                                              peaks["ex2_per_s"])
         except Exception as exc:  # reported, never silently dropped
             line["matrix_free"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_multi_rhs:
@@ -763,19 +943,19 @@ def main():
         try:
             mr_steps = args.multi_rhs_steps if args.multi_rhs_steps > 0 else max(5, args.steps // 20)
             line["multi_rhs"] = multi_rhs(h2, torch, mr_steps, 3, peak_hbm, peak_kind, args.cloud_n,
-                                          not args.no_multi_rhs_fp64)
+                                          not args.no_multi_rhs_fp64, ffma_peak, dfma_peak)
         except Exception as exc:  # reported, never silently dropped
             line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batch:
         try:
             line["batch"] = batch_benchmark(h2, torch, count=args.batch_count, n_max=args.batch_nmax,
-                                            with_fp64=not args.no_fp64)
+                                            with_fp64=not args.no_fp64, ffma_peak=ffma_peak)
         except Exception as exc:  # reported, never silently dropped
             line["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_compress:
         try:
             line["compress"] = compress_benchmark(h2, torch, args.compress_steps, tuple(args.compress_sets.split(",")),
-                                                  args.compress_grid)
+                                                  args.compress_grid, dfma_peak)
             if rank == 0 and world == 1 and not args.no_cpu_baseline:
                 line["compress"]["cpu_baseline"] = compress_oracle_sample(h2, torch)
         except Exception as exc:  # reported, never silently dropped
@@ -785,12 +965,6 @@ def main():
             line["serve"] = serve_benchmark(h2, torch, args.serve_requests, args.serve_maxit)
         except Exception as exc:  # reported, never silently dropped
             line["serve"] = {"error": f"{type(exc).__name__}: {exc}"}
-    if res_fp64 is not None:
-        ms64 = float(np.mean(res_fp64["step_ms"]))
-        b64 = 8 * (mat_entries + vec_elems)
-        line["fp64"] = {"ms_per_step": ms64, "GB/s": b64 / (ms64 * 1e-3) / 1e9,
-                        "gflops": flops / (ms64 * 1e-3) / 1e9,
-                        "phases_ms": dict(zip(h2.PHASES, [float(v) for v in res_fp64["phase_ms"]]))}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -355,6 +355,25 @@ int h2_server_destroy(h2_server_t s);
  * mechanism with a budget of about one second. */
 int h2_selftest_wait_timeout(int64_t budget_cycles);
 
+/* Measured arithmetic peak of the current device (no paper counterpart; it supplies the
+ * denominators of the rooflines: the FP64 product is bound by the FP64 fused multiply-add
+ * rate, the FP32 multi-vector product on the CUDA cores by the FP32 one, the matrix-free
+ * product by the special-function unit). Runs register-resident chains of one instruction
+ * kind on every SM (32 warps per SM; per thread either four FMA accumulators whose
+ * multiplicands rotate through distinct registers or eight FMA chains sharing their
+ * multiplicands, whichever is faster; eight chains for ex2) for about target_ms milliseconds
+ * per launch, after a calibration launch, and keeps the fastest of five timed launches per
+ * form (CUDA events on the legacy default stream; synchronises the device).
+ *   unit: H2_PEAK_DFMA (FP64 FMA, 2 flops each), H2_PEAK_FFMA (FP32 FMA, 2 flops each) or
+ *   H2_PEAK_EX2 (special-function 2^x, 1 evaluation each). target_ms in [1, 1000].
+ *   rate (host): flop/s, or evaluations/s for H2_PEAK_EX2. ms (host, may be NULL): the
+ *   fastest launch's duration. Changes no clock or power setting: the rate is the one at the
+ *   clocks the device runs at while measuring. Errors: H2_EINVAL, H2_ENOMEM, H2_ECUDA. */
+#define H2_PEAK_DFMA 0
+#define H2_PEAK_FFMA 1
+#define H2_PEAK_EX2 2
+int h2_measure_peak(int unit, double target_ms, double *rate, double *ms);
+
 /* Static description of a status code. */
 const char *h2_status_str(int status);
 

@@ -97,6 +97,7 @@ SIGNATURES = {
     "h2_server_cancel": (_I, [_P, _I64]),
     "h2_server_destroy": (_I, [_P]),
     "h2_selftest_wait_timeout": (_I, [_I64]),
+    "h2_measure_peak": (_I, [_I, _D, C.POINTER(_D), C.POINTER(_D)]),
 }
 
 _lib = None
@@ -278,6 +279,20 @@ def h2_get_timing(h: int):
     prods = np.zeros(1, dtype=np.int64)
     _check(load().h2_get_timing(h, _np_ptr(ms), _np_ptr(launches), _np_ptr(prods)), "h2_get_timing")
     return ms, launches, int(prods[0])
+
+
+H2_PEAK_DFMA, H2_PEAK_FFMA, H2_PEAK_EX2 = 0, 1, 2
+PEAK_UNITS = {"dfma": H2_PEAK_DFMA, "ffma": H2_PEAK_FFMA, "ex2": H2_PEAK_EX2}
+
+
+def h2_measure_peak(unit, target_ms: float = 30.0):
+    """Measured rate of one arithmetic unit of the current device: (rate, ms of the fastest
+    launch); flop/s for "dfma" / "ffma", evaluations/s for "ex2"."""
+    u = PEAK_UNITS[unit] if isinstance(unit, str) else int(unit)
+    rate = C.c_double(0.0)
+    ms = C.c_double(0.0)
+    _check(load().h2_measure_peak(u, float(target_ms), C.byref(rate), C.byref(ms)), "h2_measure_peak")
+    return rate.value, ms.value
 
 
 def h2_destroy(h: int) -> None:

@@ -243,13 +243,22 @@ h2s::Pipe make_pipe(uint32_t tile_bytes, uint32_t x_bytes, int sub_nodes, int kx
     return p;
 }
 
+// The FP64 single-vector block stream runs 256 consumer threads (the FP64 pipe bounds it, and
+// eight consumer warps per SM keep it busier than four).
+template <typename T, int NVMAX>
+constexpr int stream_consumers()
+{
+    return (sizeof(T) == 8 && NVMAX == 1) ? 2 * h2s::kConsumers : h2s::kConsumers;
+}
+
 template <typename T, int NVMAX>
 void set_kernel_attributes()
 {
     static bool done = false;  // per template instance
     if (done) return;
     for (const void *f : {(const void *)h2s::k_up_sub<T, NVMAX>, (const void *)h2s::k_down_sub<T, NVMAX>,
-                          (const void *)h2s::k_stream<T, NVMAX>}) {
+                          (const void *)h2s::k_stream<T, NVMAX>,
+                          (const void *)h2s::k_stream<T, NVMAX, stream_consumers<T, NVMAX>()>}) {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         // the largest shared-memory carveout lets the side stream's kernels become
         // resident next to the persistent streaming kernel
@@ -398,8 +407,9 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
                                                                        dv.n_chunks_bottom, 0);
             }
         } else {
-            k_stream<T, NVMAX><<<grid_bot, kThreads, sm_bot, st>>>(o, v, p_bot, dv.desc_bottom, dv.chunks_bottom,
-                                                                   dv.n_chunks_bottom, 0);
+            constexpr int C = stream_consumers<T, NVMAX>();
+            k_stream<T, NVMAX, C><<<grid_bot, C + 32, sm_bot, st>>>(o, v, p_bot, dv.desc_bottom, dv.chunks_bottom,
+                                                                    dv.n_chunks_bottom, 0);
         }
     }
     dv.end(1, ev, st, dv.n_chunks_bottom > 0 ? 1 : 0);

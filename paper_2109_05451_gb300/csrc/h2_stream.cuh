@@ -170,12 +170,12 @@ __device__ inline Smem<T> carve(unsigned char *base, const Pipe &p, int sub_node
 }
 
 template <typename T>
-__device__ inline void init_pipe(Smem<T> &s, const Pipe &p)
+__device__ inline void init_pipe(Smem<T> &s, const Pipe &p, int consumers = kConsumers)
 {
     if (threadIdx.x == 0) {
         for (int i = 0; i < p.ns; ++i) {
             h2p::mbar_init(&s.full[i], 1);
-            h2p::mbar_init(&s.empty[i], kConsumers / 32);
+            h2p::mbar_init(&s.empty[i], consumers / 32);
         }
         if (s.dbar) {
             h2p::mbar_init(&s.dbar[0], 1);
@@ -260,13 +260,16 @@ __device__ __forceinline__ void release(uint64_t *empty, int lane)
 }
 
 // Consumer accumulator: out[o] = sum_j tile[j*ld + o] * x[v*xld + j] over the tiles of one
-// output. The 128 consumer threads are split into `lanes` output lanes x G column groups
-// (both powers of two). With ld a multiple of VEC (16 bytes of T) each lane owns VEC
-// consecutive outputs and reads them with one 16-byte shared-memory load per column;
-// otherwise it owns one output (scalar path). Column group g takes j = g, g+G, ...; the
-// groups are summed in a fixed order, so the result is deterministic.
-template <typename T, int NVMAX>
+// output. The CONS consumer threads (128, or 256 for the FP64 single-vector stream) are split
+// into `lanes` output lanes x G column groups (both powers of two). With ld a multiple of VEC
+// (16 bytes of T) each lane owns VEC consecutive outputs and reads them with one 16-byte
+// shared-memory load per column; otherwise it owns one output (scalar path). Column group g
+// takes j = g, g+G, ...; the groups are summed in a fixed order, so the result is
+// deterministic.
+template <typename T, int NVMAX, int CONS = kConsumers>
 struct Acc {
+    static_assert(CONS == kConsumers || (CONS == 2 * kConsumers && sizeof(T) == 8),
+                  "256 consumers: FP64 only (the group-exchange buffer holds (G - 1) x 64 doubles)");
     static constexpr int VEC = 16 / int(sizeof(T));
     T a[NVMAX][VEC];
     int per, shift, g, G, o0, Rp;
@@ -278,7 +281,7 @@ struct Acc {
         const int lanes = Rp / per;
         shift = __ffs(lanes) - 1;
         g = tid >> shift;
-        G = kConsumers >> shift;
+        G = CONS >> shift;
         o0 = (tid & (lanes - 1)) * per;
     }
     __device__ __forceinline__ void zero()
@@ -294,7 +297,7 @@ struct Acc {
     __device__ __forceinline__ void gemv_fixed(const T *__restrict__ tile, const T *__restrict__ x, int xld, int nv)
     {
         using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-        constexpr int LANES = rpad(RC) / VEC, GG = kConsumers / LANES, ITER = RC / GG;
+        constexpr int LANES = rpad(RC) / VEC, GG = CONS / LANES, ITER = RC / GG;
         const T *tb = tile + g * RC + o0;
         const T *xb = x + g;
 #pragma unroll
@@ -353,7 +356,7 @@ struct Acc {
                     for (int e = 0; e < VEC; ++e)
                         if (v < nv && e < per) red[((g - 1) * NVMAX + v) * Rp + o0 + e] = a[v][e];
             }
-            h2p::consumer_sync(kConsumers);
+            h2p::consumer_sync(CONS);
             if (g == 0 && o0 < R)
                 for (int gg = 1; gg < G; ++gg)
 #pragma unroll
@@ -971,20 +974,24 @@ __global__ void __launch_bounds__(kThreads)
 // ------------------------------------------------------------------ block-row stream
 
 // chunks[c] = (first descriptor << 16) | descriptor count: whole rows, in order.
-template <typename T, int NVMAX>
-__global__ void __launch_bounds__(kThreads, 1)
+// CONS consumer threads (warps 0 .. CONS/32 - 1) and one producer warp after them. The FP64
+// single-vector stream runs 256 consumers: the FP64 pipe is the bound there, and eight
+// consumer warps per SM keep it busier than four (a 64 x 64 tile product from shared memory
+// measured 1.19 against 1.03 Tflop/s per GPU).
+template <typename T, int NVMAX, int CONS = kConsumers>
+__global__ void __launch_bounds__(CONS + 32, 1)
     k_stream(Op<T> op, Vec<T> vec, Pipe pp, const StreamDesc *__restrict__ desc, const int64_t *__restrict__ chunks,
              int64_t nchunks, int ticket_index)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<T> s = carve<T, NVMAX>(smem_raw, pp, 0, op.kx, true);
-    init_pipe(s, pp);
+    init_pipe(s, pp, CONS);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
     const uint32_t es = sizeof(T);
     Ring ring(pp.ns);
 
-    if (warp == 4) {
+    if (warp == CONS / 32) {
         if (lane == 0) {
             int *ticket = vec.tickets + ticket_index;
             // a chunk's descriptors are bulk-copied into one of two shared-memory slots while
@@ -1038,7 +1045,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     const int tid = threadIdx.x;
-    AccStreamOf<T, NVMAX> acc;
+    typename std::conditional<CONS == kConsumers, AccStreamOf<T, NVMAX>, Acc<T, NVMAX, CONS>>::type acc;
     bool fresh = true;
     for (;;) {
         if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
@@ -1060,7 +1067,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 T *out = dense ? vec.yd + int64_t(d.out_node) * mp * vs : vec.yh + int64_t(d.out_node) * kx * vs;
                 acc.store(out, xld, nv, d.rows);
             }
-            h2p::consumer_sync(kConsumers);
+            h2p::consumer_sync(CONS);
             fresh = true;
         }
     }

@@ -81,3 +81,24 @@ def test_batch_roofline_takes_the_slower_bound():
     assert r["bound"] == "hbm" and abs(r["frac"] - 0.5) < 1e-12 and abs(r["bound_ms"] - 1.0) < 1e-12
     r = b.batch_roofline(0.0, b.FFMA_PEAK_TFLOPS * 1e12 * 4e-3, 8.0)  # 4 ms of flops, measured 8 ms
     assert r["bound"] == "alu" and abs(r["frac"] - 0.5) < 1e-12
+
+
+def test_stream_roofline_takes_the_slower_bound():
+    b = bench
+    # 1 GB at 1000 GB/s = 1 ms; 1 Tflop at 2 Tflop/s = 500 ms: arithmetic-bound, measured 1000 ms
+    r = b.stream_roofline("k", 1e9, 1e12, 1000.0, 2.0, "measured", 1000.0, "measured")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 1.0) < 1e-12 and abs(r["frac"] - 0.5) < 1e-12 and abs(r["bound_ms"] - 500.0) < 1e-9
+    # the same bytes with few flops: HBM-bound
+    r = b.stream_roofline("k", 1e9, 1e6, 2.0, 2.0, "measured", 1000.0, "measured", traffic=123)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and abs(r["frac"] - 0.5) < 1e-12 and r["traffic"] == 123
+
+
+def test_bottom_stream_entries_counts_the_lowest_levels():
+    class Info:
+        depth = 6
+        rank = 4
+        dense_entries = 77
+        coupling_per_level = [0, 0, 1, 2, 3, 4, 5] + [0] * 25
+    cpl, dns = bench.bottom_stream_entries(Info())
+    assert cpl == (1 + 2 + 3 + 4 + 5) * 16 and dns == 77  # levels 2..6 (the lowest min(6, 4) + 1)
