@@ -34,9 +34,14 @@
  *     order. Element type: double for H2_FP64, float for H2_FP32, H2_BF16X2 and H2_FP32_MF.
  *   - Inputs are copied at h2_build; device X, Y, b, x stay owned by the caller; the
  *     handle owns its host operator and its device copy until h2_destroy.
- *   - One handle may be used by one stream at a time through h2_matvec (its internal
- *     workspace is shared); use h2_matvec_ws with separate workspaces for concurrent
- *     products on one handle.
+ *   - Products on one handle may be issued concurrently from several host threads and on
+ *     several streams: h2_matvec keeps one workspace per stream (products on one stream are
+ *     ordered by it), h2_matvec_ws runs on the workspace it is given (distinct workspaces
+ *     for products that may overlap), and every product borrows its own fork/join context
+ *     (side stream and events) while its launches are enqueued. h2_upload, h2_destroy,
+ *     h2_set_timing and h2_get_timing must not overlap other calls on the same handle.
+ *   - Device calls run on the current CUDA device, which must be the one the operator was
+ *     uploaded to (H2_EINVAL otherwise).
  */
 #ifndef H2_H
 #define H2_H
@@ -130,15 +135,19 @@ size_t h2_workspace_bytes(h2_handle h, int nv);
 /* Y = alpha * A_H2 * X + beta * Y (Sec. 3: upsweep, tree multiply, downsweep, dense).
  *   X, Y: device, n x nv column-major, ld = n, caller's point order; element type double
  *   for H2_FP64, float otherwise. X and Y must not overlap. When beta == 0, Y is not
- *   read (NaN in Y is ignored). nv >= 1. Uses a workspace owned by the handle, allocated
- *   (synchronously) on first use or when nv grows. Errors: H2_EINVAL, H2_ESTATE (no
+ *   read (NaN in Y is ignored). nv >= 1. Uses a workspace that the handle keeps for this
+ *   stream (by its cudaStream_t value), allocated on the stream's first product and grown
+ *   when nv grows (a growth waits for that workspace's last product and frees it); each
+ *   product on it is ordered after the previous one, also when a destroyed stream's handle
+ *   value is reused. Errors: H2_EINVAL (also: another device is current), H2_ESTATE (no
  *   device copy), H2_ENOMEM, H2_ECUDA. */
 int h2_matvec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta,
               void *cuda_stream);
 
 /* As h2_matvec, with a caller-owned device workspace of ws_bytes >= h2_workspace_bytes
- * (h, nv), 256-byte aligned. Products on one handle with distinct workspaces may run
- * concurrently on different streams. Allocates nothing. */
+ * (h, nv), 256-byte aligned, on the operator's device. Products on one handle with distinct
+ * workspaces may run concurrently on different streams, issued from any host threads.
+ * Allocates no device memory. */
 int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta,
                  void *workspace, size_t ws_bytes, void *cuda_stream);
 
@@ -155,14 +164,16 @@ int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, doub
  *     larger operators are rejected with H2_EINVAL before anything is launched.
  *   - The first call on a device looks up the scratch area's device address for that
  *     device (cudaGetSymbolAddress, with the device current); make that first call before
- *     any stream capture on the device. Call it with the device current that holds the
- *     operator's device copy.
+ *     any stream capture on the device. With CUDA's lazy module loading that first lookup
+ *     is also when the device reserves the scratch area, so it can fail with H2_ENOMEM.
+ *   - The current device must be the one holding the operator's device copy (H2_EINVAL
+ *     otherwise, before anything is launched).
  *   - All calls on one device share the one scratch area, whichever handle they use, and
  *     it keeps the previous call's contents (each product resets what it needs). Calls
  *     whose execution overlaps on the GPU (different streams, no ordering between them)
  *     race on it: order them on one stream or with events.
- * Errors: H2_EINVAL (bad argument or operator too large), H2_ESTATE (no device copy),
- * H2_ECUDA. */
+ * Errors: H2_EINVAL (bad argument, operator too large, another device current), H2_ESTATE
+ * (no device copy), H2_ENOMEM (first call only, see above), H2_ECUDA. */
 #define H2_NOALLOC_SCRATCH_BYTES (64u << 20)
 int h2_matvec_noalloc(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta,
                       void *cuda_stream);

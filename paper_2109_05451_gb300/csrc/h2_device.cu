@@ -35,6 +35,7 @@
 #include <chrono>
 #include <cstdlib>
 #include <fstream>
+#include <memory>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -78,15 +79,27 @@ struct h2_device {
     // matrix-free FP32 (H2_FP32_MF): coordinates instead of blocks
     bool mf = false;
     h2s::MfArgs mfa{};
-    // execution resources
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_up = nullptr, ev_top = nullptr, ev_topup = nullptr;
-    // handle-owned workspace for h2_matvec
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-    // instrumentation: the launch and product counters are atomic; the event timing is for
-    // one host thread at a time (leave it off while products run from several threads)
+    // fork/join contexts (side stream + events) of products in flight on the host: a product
+    // takes an idle one for its launch sequence and gives it back (calls from several host
+    // threads never share one); the first is created at upload
+    std::mutex exec_mutex;
+    std::vector<h2_exec> exec_idle, exec_all;
+    // h2_matvec's workspaces, one per CUDA stream it has been called with; `done` is recorded
+    // after each product, and the next product on that workspace waits for it
+    struct StreamWs {
+        void *stream = nullptr;
+        void *ws = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t done = nullptr;
+        std::mutex m;  // held while a product is enqueued on this workspace
+    };
+    std::mutex ws_mutex;
+    std::vector<std::unique_ptr<StreamWs>> stream_ws;
+    size_t ws_total = 0;  // bytes of all stream workspaces
+    // instrumentation: the launch and product counters are atomic; the event records of the
+    // phase timing are guarded by timing_mutex
     bool timing = false;
+    std::mutex timing_mutex;
     struct PhaseRec {
         int phase;
         cudaEvent_t a, b;
@@ -111,6 +124,7 @@ struct h2_device {
     cudaEvent_t begin(cudaStream_t st)
     {
         if (!timing) return nullptr;
+        std::lock_guard<std::mutex> lock(timing_mutex);
         cudaEvent_t a = event();
         cudaEventRecord(a, st);
         return a;
@@ -119,12 +133,14 @@ struct h2_device {
     {
         phase_launches[phase] += launches;
         if (!a) return;
+        std::lock_guard<std::mutex> lock(timing_mutex);
         cudaEvent_t b = event();
         cudaEventRecord(b, st);
         pending.push_back({phase, a, b});
     }
     void drain()
     {
+        std::lock_guard<std::mutex> lock(timing_mutex);
         for (auto &r : pending) {
             float ms = 0.f;
             cudaEventSynchronize(r.b);
@@ -139,10 +155,11 @@ struct h2_device {
     {
         drain();
         for (auto e : event_pool) cudaEventDestroy(e);
-        if (ev_up) cudaEventDestroy(ev_up);
-        if (ev_top) cudaEventDestroy(ev_top);
-        if (ev_topup) cudaEventDestroy(ev_topup);
-        if (side) cudaStreamDestroy(side);
+        for (auto &x : exec_all) h2_exec_destroy(&x);
+        for (auto &w : stream_ws) {
+            if (w->ws) cudaFree(w->ws);
+            if (w->done) cudaEventDestroy(w->done);
+        }
     }
 };
 
@@ -1177,8 +1194,7 @@ void h2_device_free(h2_op *op)
     cudaGetDevice(&prev);
     if (op->dev->device >= 0) cudaSetDevice(op->dev->device);
     if (op->dev->arena) cudaFree(op->dev->arena);
-    if (op->dev->ws) cudaFree(op->dev->ws);
-    delete op->dev;
+    delete op->dev;  // its destructor frees the stream workspaces and fork/join contexts
     op->dev = nullptr;
     if (prev >= 0) cudaSetDevice(prev);
 }
@@ -1253,6 +1269,49 @@ void h2_exec_destroy(h2_exec *ex)
     *ex = h2_exec{};
 }
 
+int h2_device_check(h2_handle h)
+{
+    if (!h) return H2_EINVAL;
+    if (!h->dev) return H2_ESTATE;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return H2_ECUDA;
+    }
+    return cur == h->dev->device ? H2_OK : H2_EINVAL;
+}
+
+namespace {
+
+// Take an idle fork/join context of the handle (creating one if every context is in use by
+// another host thread's launch sequence); give it back with exec_release.
+int exec_acquire(h2_device &dv, h2_exec *out)
+{
+    {
+        std::lock_guard<std::mutex> lock(dv.exec_mutex);
+        if (!dv.exec_idle.empty()) {
+            *out = dv.exec_idle.back();
+            dv.exec_idle.pop_back();
+            return H2_OK;
+        }
+    }
+    h2_exec ex;
+    const int rc = h2_exec_create(&ex);
+    if (rc != H2_OK) return rc;
+    std::lock_guard<std::mutex> lock(dv.exec_mutex);
+    dv.exec_all.push_back(ex);
+    *out = ex;
+    return H2_OK;
+}
+
+void exec_release(h2_device &dv, const h2_exec &ex)
+{
+    std::lock_guard<std::mutex> lock(dv.exec_mutex);
+    dv.exec_idle.push_back(ex);
+}
+
+}  // namespace
+
 int h2_matvec_exec(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta, void *workspace,
                    size_t ws_bytes, void *cuda_stream, const h2_exec *exp)
 {
@@ -1262,23 +1321,33 @@ int h2_matvec_exec(h2_handle h, const void *X, void *Y, int nv, double alpha, do
     h2_device &dv = *h->dev;
     if (ws_bytes < ws_layout(*h, dv, nv, nullptr, nullptr)) return H2_EINVAL;
     if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return H2_EINVAL;
-    h2_exec own;
-    own.side = dv.side;
-    own.ev_up = dv.ev_up;
-    own.ev_top = dv.ev_top;
-    own.ev_topup = dv.ev_topup;
+    // the kernels must run on the GPU that holds the operator (and, for a scratch or pooled
+    // workspace, the workspace)
+    const int dc = h2_device_check(h);
+    if (dc != H2_OK) return dc;
+    // a product without its own fork/join context borrows one of the handle's for the time its
+    // launches are enqueued; the stream and event orderings it records stay valid after that
+    h2_exec own{};
+    if (!exp) {
+        const int rc = exec_acquire(dv, &own);
+        if (rc != H2_OK) return rc;
+    }
     const h2_exec &ex = exp ? *exp : own;
     Workspace w;
     ws_layout(*h, dv, nv, &w, workspace);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     dv.products += 1;
+    int rc;
     if (dv.tc)
-        return launch_tc(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w, st);
-    if (dv.esize == 8)
-        return launch_product<double>(*h, dv, static_cast<const double *>(X), static_cast<double *>(Y), nv, alpha,
-                                      beta, w, st, ex);
-    return launch_product<float>(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w,
-                                 st, ex);
+        rc = launch_tc(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w, st);
+    else if (dv.esize == 8)
+        rc = launch_product<double>(*h, dv, static_cast<const double *>(X), static_cast<double *>(Y), nv, alpha, beta,
+                                    w, st, ex);
+    else
+        rc = launch_product<float>(*h, dv, static_cast<const float *>(X), static_cast<float *>(Y), nv, alpha, beta, w,
+                                   st, ex);
+    if (!exp) exec_release(dv, own);
+    return rc;
 }
 
 extern "C" {
@@ -1562,15 +1631,13 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
                                     ncpl_top, 0);
     if (rc == H2_OK) rc = cuda_status(cudaStreamSynchronize(st));
     cudaFree(tmp);
-    if (rc == H2_OK) {
-        int lo_prio = 0, hi_prio = 0;
-        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (rc == H2_OK) {  // the first fork/join context
         h2_exec ex;
         rc = h2_exec_create(&ex);
-        dv->side = static_cast<cudaStream_t>(ex.side);
-        dv->ev_up = static_cast<cudaEvent_t>(ex.ev_up);
-        dv->ev_top = static_cast<cudaEvent_t>(ex.ev_top);
-        dv->ev_topup = static_cast<cudaEvent_t>(ex.ev_topup);
+        if (rc == H2_OK) {
+            dv->exec_all.push_back(ex);
+            dv->exec_idle.push_back(ex);
+        }
     }
     if (rc != H2_OK) h2_device_free(&op);
     return rc;
@@ -1592,23 +1659,53 @@ int h2_matvec(h2_handle h, const void *X, void *Y, int nv, double alpha, double 
 {
     if (!h || !X || !Y || nv < 1) return H2_EINVAL;
     if (!h->dev) return H2_ESTATE;
+    const int dc = h2_device_check(h);
+    if (dc != H2_OK) return dc;
     h2_device &dv = *h->dev;
     const size_t need = ws_layout(*h, dv, nv, nullptr, nullptr);
-    if (dv.ws_bytes < need) {
-        if (dv.ws) {
-            cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
-            cudaFree(dv.ws);
-            dv.ws = nullptr;
-            dv.ws_bytes = 0;
+    // this stream's workspace (created on its first product)
+    h2_device::StreamWs *e = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(dv.ws_mutex);
+        for (auto &w : dv.stream_ws)
+            if (w->stream == cuda_stream) e = w.get();
+        if (!e) {
+            auto w = std::make_unique<h2_device::StreamWs>();
+            w->stream = cuda_stream;
+            if (cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return H2_ECUDA;
+            }
+            e = w.get();
+            dv.stream_ws.push_back(std::move(w));
         }
-        if (cudaMalloc(&dv.ws, need) != cudaSuccess) {
+    }
+    std::lock_guard<std::mutex> lock(e->m);
+    if (e->bytes < need) {
+        if (e->ws) {
+            cudaEventSynchronize(e->done);  // the last product on it has finished
+            cudaFree(e->ws);
+            std::lock_guard<std::mutex> l2(dv.ws_mutex);
+            dv.ws_total -= e->bytes;
+            e->ws = nullptr;
+            e->bytes = 0;
+        }
+        if (cudaMalloc(&e->ws, need) != cudaSuccess) {
             cudaGetLastError();
-            dv.ws = nullptr;
+            e->ws = nullptr;
             return H2_ENOMEM;
         }
-        dv.ws_bytes = need;
+        e->bytes = need;
+        std::lock_guard<std::mutex> l2(dv.ws_mutex);
+        dv.ws_total += need;
     }
-    return h2_matvec_ws(h, X, Y, nv, alpha, beta, dv.ws, dv.ws_bytes, cuda_stream);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // a stream handle can be reused after cudaStreamDestroy while the old stream's product is
+    // still running: order this product after the previous one on this workspace
+    cudaStreamWaitEvent(st, e->done, 0);
+    const int rc = h2_matvec_exec(h, X, Y, nv, alpha, beta, e->ws, e->bytes, cuda_stream, nullptr);
+    cudaEventRecord(e->done, st);
+    return rc;
 }
 
 int h2_set_timing(h2_handle h, int enable)
@@ -1704,7 +1801,7 @@ int h2_get_info(h2_handle h, h2_info *info)
     info->basis_entries = op.n * op.k;
     info->transfer_entries = (op.nnodes - 1) * op.k * op.k;
     info->uploaded_prec = op.dev ? int(op.dev->prec) : -1;
-    info->device_bytes = op.dev ? op.dev->arena_bytes + op.dev->ws_bytes : 0;
+    info->device_bytes = op.dev ? op.dev->arena_bytes + op.dev->ws_total : 0;
     return H2_OK;
 }
 

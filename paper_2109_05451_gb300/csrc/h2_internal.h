@@ -47,9 +47,10 @@ struct h2_op {
 };
 
 // Fork/join context of one product: the high-priority side stream that runs the upper tree
-// levels next to the main stream, and the two events that order them (cudaStream_t /
-// cudaEvent_t, kept opaque here). Each handle owns one for h2_matvec / h2_matvec_ws; callers
-// that run products of one handle concurrently on several streams give each its own.
+// levels next to the main stream, and the events that order them (cudaStream_t /
+// cudaEvent_t, kept opaque here). Each handle keeps a pool of them for h2_matvec /
+// h2_matvec_ws (a product borrows one while its launches are enqueued); the serving loop
+// gives each of its slots its own.
 struct h2_exec {
     void *side = nullptr;
     void *ev_up = nullptr;
@@ -58,6 +59,9 @@ struct h2_exec {
 };
 
 // h2_device.cu
+// H2_OK if the current CUDA device holds h's device copy; H2_ESTATE without a device copy,
+// H2_EINVAL if another device is current.
+int h2_device_check(h2_handle h);
 int h2_exec_create(h2_exec *ex);
 void h2_exec_destroy(h2_exec *ex);
 // h2_matvec_ws with an explicit fork/join context (nullptr: the handle's own).

@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "../../include/h2.h"
+#include "h2_internal.h"
 
 static __device__ __align__(256) unsigned char h2_noalloc_scratch[H2_NOALLOC_SCRATCH_BYTES];
 
@@ -32,10 +33,12 @@ int scratch_address(int device, void **out)
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_addr[device]) {
         void *p = nullptr;
+        // with lazy module loading this first lookup is what loads the module on this device
+        // and reserves the scratch area, so it can fail for lack of device memory
         const cudaError_t e = cudaGetSymbolAddress(&p, h2_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
-            return H2_ECUDA;
+            return e == cudaErrorMemoryAllocation ? H2_ENOMEM : H2_ECUDA;
         }
         g_scratch_addr[device] = p;
     }
@@ -49,9 +52,9 @@ extern "C" int h2_matvec_noalloc(h2_handle h, const void *X, void *Y, int nv, do
                                  void *cuda_stream)
 {
     if (!h || !X || !Y || nv < 1) return H2_EINVAL;
-    h2_info info;
-    if (h2_get_info(h, &info) != H2_OK) return H2_EINVAL;
-    if (info.uploaded_prec < 0) return H2_ESTATE;
+    // the current device must hold the operator: its scratch area is the one the kernels get
+    const int dc = h2_device_check(h);
+    if (dc != H2_OK) return dc;
     const size_t need = h2_workspace_bytes(h, nv);
     if (need == 0) return H2_ESTATE;
     if (need > size_t(H2_NOALLOC_SCRATCH_BYTES)) return H2_EINVAL;  // operator too large for the scratch area

@@ -7,8 +7,9 @@
 // upload, vectors per product), so a 1-D bulk copy lands the exact shared-memory image that
 // the MMA reads.
 //
-// Accumulators live in tensor memory (TMEM). For M = 64 with one CTA, row 16w + i of D is in
-// TMEM lane 32w + i (w = 0..3, i = 0..15): warp w reads rows 16w .. 16w+15 with its lanes 0-15.
+// Accumulators live in tensor memory (TMEM). The streams issue M = 128 with one CTA: row r of D
+// is in TMEM lane r, so warp w (w = 0..3) reads rows 32w .. 32w+31 with its 32 lanes, one
+// 32-bit column per register.
 #pragma once
 
 #include <cstdint>
