@@ -163,3 +163,48 @@ def test_compress_rejects_bad_arguments_before_cuda():
             assert e.value.status == h2.H2_EINVAL
     finally:
         h2.h2_destroy(h)
+
+
+FULL_SIZE = {
+    # the nv = 1 product workload: 2^20-point Gaussian grid, rank 64, eta 0.7
+    "grid1024_gauss": lambda: si.GRID1024_GAUSS,
+    # the 32-vector workload: 2^21 uniform points in [0,1]^3, tri-cubic rank 64, eta 0.7
+    "cloud3d_exp": lambda: si.CLOUD3D_EXP,
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(FULL_SIZE))
+def test_full_size_partition_matches_oracle(name):
+    """The benchmarked partitions, block by block: the host build's tree and coupling and
+    dense lists equal the oracle's (Sec. 6.1 admissibility, same-level pairs), at full size.
+
+    The counts are stated too, so that a change of either side's rule shows as a number:
+    2^20 grid 483,456 coupling + 145,924 dense blocks; 2^21 cloud 4,721,738 + 1,948,838."""
+    w = FULL_SIZE[name]()
+    pts = w.make_points()
+    orc = oracle.OracleH2(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    h = h2.h2_build(pts, w.kernel, w.leaf_size, w.cheb_order, w.eta)
+    try:
+        info = h2.h2_get_info(h)
+        assert (info.depth, info.rank, info.n_nodes) == (orc.depth, orc.rank, orc.nnodes)
+        assert np.array_equal(h2.h2_get_perm(h), orc.perm)
+        lvl, t, s, dt, ds = orc.blocks()
+        expect = {"grid1024_gauss": (483456, 145924), "cloud3d_exp": (4721738, 1948838)}[name]
+        assert (len(t), len(dt)) == expect == (info.n_coupling, info.n_dense)
+        for l in range(orc.depth + 1):
+            assert info.coupling_per_level[l] == np.sum(lvl == l)
+        rowptr, col = h2.h2_get_coupling_csr(h)
+        rows = np.repeat(np.arange(len(rowptr) - 1, dtype=np.int64), np.diff(rowptr))
+        o = np.lexsort((s, t))
+        g = np.lexsort((col, rows))
+        assert np.array_equal(rows[g], t[o]) and np.array_equal(col[g].astype(np.int64), s[o])
+        drowptr, dcol = h2.h2_get_dense_csr(h)
+        first = 2 ** orc.depth
+        drows = np.repeat(np.arange(len(drowptr) - 1, dtype=np.int64), np.diff(drowptr)) + first
+        dcol = dcol.astype(np.int64) + first
+        o = np.lexsort((ds, dt))
+        g = np.lexsort((dcol, drows))
+        assert np.array_equal(drows[g], dt[o]) and np.array_equal(dcol[g], ds[o])
+    finally:
+        h2.h2_destroy(h)
