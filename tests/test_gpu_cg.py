@@ -73,3 +73,39 @@ def test_cg_is_bitwise_repeatable(system):
     r1 = solve(op, b, 1e-5, 5000)
     r2 = solve(op, b, 1e-5, 5000)
     assert r1[1] == r2[1] and np.array_equal(r1[3], r2[3])
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def oracle_cg(orc, b, tol, maxit, sigma2=SIGMA2):
+    from oracle.cg import cg_solve
+    return cg_solve(lambda v: orc.matvec(v.reshape(-1, 1))[:, 0], b, sigma2=sigma2, tol=tol, maxit=maxit)
+
+
+@pytest.mark.parametrize("steps", [1, 3, 10])
+def test_cg_iterates_equal_the_oracle_cg(system, steps):
+    """FP64 products: the j-th GPU iterate is the oracle CG's j-th iterate (the same
+    Hestenes-Stiefel steps on the same operator), to rounding. Short runs only: CG loses
+    orthogonality in finite precision, and a 2e-16 relative perturbation of each product
+    already moves the 40th iterate of this system by 1e-5."""
+    orc, op, b = system
+    op.upload("fp64")
+    ref = oracle_cg(orc, b, 0.0, steps)
+    status, iters, relres, x = solve(op, b, 0.0, steps)
+    assert status == h2.H2_ENOTCONV and iters == ref["iters"] == steps
+    assert relerr(x, ref["x"]) <= 1e-12
+    assert abs(relres - ref["true_relres"]) <= 1e-12 * max(1.0, ref["true_relres"]) + 1e-14
+
+
+def test_cg_iteration_count_equals_the_oracle_cg(system):
+    orc, op, b = system
+    op.upload("fp64")
+    ref = oracle_cg(orc, b, 1e-10, 5000)
+    status, iters, relres, x = solve(op, b, 1e-10, 5000)
+    assert ref["converged"] and status == h2.H2_OK
+    # product rounding (GPU and oracle sum in different orders) delays or advances the step at
+    # which the recursive residual crosses tol by a few steps out of ~235 here
+    assert abs(iters - ref["iters"]) <= max(2, int(0.03 * ref["iters"]))
+    assert relerr(x, ref["x"]) <= 1e-8

@@ -154,3 +154,57 @@ def test_converged_residual_checked_with_the_oracle(ops):
     x = r["x"]
     res = b - (orc.matvec(x[:, None])[:, 0] + SIGMA2 * x)
     assert np.linalg.norm(res) / np.linalg.norm(b) <= 1e-9
+
+
+# ------------------------------------------------ the served operator family, at a small N
+#
+# (r^2 + 1e-4)^(-1.5) on uniform random points in [0,1]^2, leaf 64, 8 x 8 Chebyshev (rank 64),
+# eta 0.7, FP32 products: the family the serving benchmark runs at N = 2^14 ... 2^20, here at
+# N = 2^12 where the oracle's CG runs in seconds. sigma2 = 1e-2 is the literal shift (the
+# system's condition number is 1.3e4 here and grows ~200x per 4x in N); sigma2 = 1e4 is the
+# same 1e-2 relative to the kernel's diagonal value kappa(0) = 1e6.
+
+IMQ = ("imq", 1e-4, 1.5, 0)
+
+
+@pytest.fixture(scope="module")
+def imq_family():
+    pts = si.uniform_cloud(4096, 2, 50)
+    orc = oracle.OracleH2(pts, IMQ, 64, 8, 0.7, assemble=True)
+    op = h2.H2Operator(pts, IMQ, 64, 8, 0.7).upload("fp32")
+    yield orc, op, si.gaussian_vectors(4096, 1, 7)[:, 0].copy()
+    op.close()
+
+
+def oracle_product_relres(orc, x, b, sigma2):
+    r = b - (orc.matvec(x.reshape(-1, 1))[:, 0] + sigma2 * x)
+    return float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("sigma2,maxit", [(1e-2, 100), (1e4, 1000)])
+def test_served_imq_family_against_the_oracle(imq_family, sigma2, maxit):
+    from oracle.cg import cg_solve
+    orc, op, b = imq_family
+    server = h2.H2Server(4 * h2.H2Server.request_bytes(op), 2, op.n)
+    try:
+        rid = server.submit(op, b, 1e-6, maxit, sigma2)
+        assert server.wait(300.0) == h2.H2_OK
+        (r,) = server.poll()
+    finally:
+        server.close()
+    assert r["id"] == rid
+    # the reported true residual is the residual of the served x under the oracle's FP64 operator,
+    # up to the FP32 product's error (within the FP32 parity tolerance 1e-5 of ||(A + sigma2 I) x||)
+    orc_res = oracle_product_relres(orc, r["x"], b, sigma2)
+    Ax = orc.matvec(r["x"].reshape(-1, 1))[:, 0] + sigma2 * r["x"]
+    assert abs(r["true_relres"] - orc_res) <= 0.02 * orc_res + 1e-5 * np.linalg.norm(Ax) / np.linalg.norm(b)
+    ref = cg_solve(lambda v: orc.matvec(v.reshape(-1, 1))[:, 0], b, sigma2=sigma2, tol=1e-6, maxit=maxit)
+    if sigma2 < 1.0:
+        # the literal shift: neither the oracle's FP64 CG nor the served FP32 CG converges in 100
+        # steps; the served residual is the method's (CG's residual is not monotone), within 2x
+        assert r["status"] == h2.H2_ENOTCONV and r["iters"] == maxit and not ref["converged"]
+        assert 0.5 * ref["true_relres"] <= r["true_relres"] <= 2.0 * ref["true_relres"]
+    else:
+        assert r["status"] == h2.H2_OK and ref["converged"]
+        assert abs(r["iters"] - ref["iters"]) <= 0.15 * ref["iters"]
+        assert orc_res <= 5e-6
