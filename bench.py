@@ -296,7 +296,8 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with
               ffma_peak=FFMA_PEAK_TFLOPS, dfma_peak=None):
     """The multi-vector workload: N = 2^21 uniform random points in [0,1]^3, exp(-r/0.2),
     leaf 64, 4 x 4 x 4 Chebyshev grid (rank 64), eta 0.7, 32 vectors, in split-BF16 on the
-    tensor cores and in FP32. Its ~113 GB of stored blocks exceed L2 by far, so no flush is
+    tensor cores, in FP32 on the tensor cores (3xTF32; the default for FP32 passes of more
+    than 8 vectors) and in FP32 on the CUDA cores (FMA), and in FP64. Its ~113 GB of stored blocks exceed L2 by far, so no flush is
     needed between products. Bytes and flops are algorithmic: every stored entry once per
     product (bases and transfers twice), X read and Y written; 2 flops per entry per vector."""
     w = si.CLOUD3D_EXP if not n_points or n_points == 2 ** 21 else si.cloud3d(n_points)
@@ -314,11 +315,14 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with
            "l2": f"inputs larger than L2 ({4 * mat_entries / 1e9:.1f} GB of blocks per product), no flush"}
     stream = torch.cuda.current_stream()
     results = {}
-    precs = ("bf16x2", "fp32", "fp64") if with_fp64 else ("bf16x2", "fp32")
+    precs = ("bf16x2", "fp32", "fp32_cuda_cores", "fp64") if with_fp64 else ("bf16x2", "fp32", "fp32_cuda_cores")
     for prec in precs:
         t0 = time.perf_counter()
-        op.upload(prec)
+        if prec != "fp32_cuda_cores":  # the CUDA-core FP32 pass reuses the FP32 upload
+            op.upload(prec)
         upload_s = time.perf_counter() - t0
+        if prec.startswith("fp32"):
+            h2.h2_set_fp32_tensor(op.handle, prec == "fp32")
         X = torch.from_numpy(Xh).cuda().t()
         if prec == "fp64":
             X = X.double()
@@ -352,6 +356,12 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with
             roof = {"kernel": "k_stream_tc (split-BF16 tcgen05, 128x64x16 MMAs, FP32 accumulation in TMEM)",
                     "bound": "hbm", "achieved": blk_gbs, "peak": peak_hbm, "unit": "GB/s",
                     "frac": blk_gbs / peak_hbm, "peak_kind": peak_kind, "algorithmic_bytes": blk_bytes}
+        elif prec == "fp32":
+            roof = {"kernel": "k_stream_tf32 (3xTF32 tcgen05, A = [S_hi; S_lo] in TMEM, 128x64x8 MMAs, FP32 "
+                              "accumulation in TMEM)",
+                    "bound": "hbm", "achieved": blk_gbs, "peak": peak_hbm, "unit": "GB/s",
+                    "frac": blk_gbs / peak_hbm, "peak_kind": peak_kind, "algorithmic_bytes": blk_bytes,
+                    "block_tflops": blk_tflops}
         else:
             # 16 flop per byte at 32 vectors: the FP32 stream is bound by the CUDA-core FMA rate
             roof = {"kernel": "k_stream (FP32, register-blocked wide accumulator)", "bound": "alu",
@@ -374,7 +384,7 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with
     if "fp64" in results:
         ref = results["fp64"]
         nref = float(np.linalg.norm(ref))
-        for prec in ("bf16x2", "fp32"):
+        for prec in ("bf16x2", "fp32", "fp32_cuda_cores"):
             out[prec]["relerr_vs_fp64"] = float(np.linalg.norm(results[prec] - ref)) / nref
     op.close()
     return out

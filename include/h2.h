@@ -178,6 +178,19 @@ int h2_matvec_ws(h2_handle h, const void *X, void *Y, int nv, double alpha, doub
 int h2_matvec_noalloc(h2_handle h, const void *X, void *Y, int nv, double alpha, double beta,
                       void *cuda_stream);
 
+/* Multi-vector FP32 products on the tensor cores (Sec. 3.2, Alg 4: with nv vectors the
+ * per-level products are small GEMMs). For an H2_FP32 device copy with rank and leaf size
+ * of at most 64, passes of more than 8 vectors stream the stored FP32 blocks through
+ * tcgen05 MMAs in 3xTF32 form: each block value a and each vector value x is split into
+ * hi = tf32(a) and lo = tf32(a - hi), and the four products hi*hi, hi*lo, lo*hi, lo*lo
+ * accumulate in FP32 in tensor memory (22 of FP32's 24 significant bits per operand; the
+ * result meets the FP32 accuracy of the CUDA-core path). enable = 0 sends those passes to
+ * the CUDA-core FMA path instead; enable = 1 (the default after h2_upload) restores the
+ * tensor cores. No effect on other precisions, shapes or vector counts. Host only; must
+ * not overlap a product on the same handle. Errors: H2_EINVAL (h NULL), H2_ESTATE (no
+ * device copy). */
+int h2_set_fp32_tensor(h2_handle h, int enable);
+
 /* Unpreconditioned conjugate gradients for (A_H2 + sigma2 I) x = b (the Krylov solve of
  * Sec. 6.4, without its multigrid preconditioner). The products run in the uploaded
  * precision; Krylov vectors, dot products and updates are FP64 on the device.

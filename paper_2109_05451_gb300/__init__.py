@@ -76,6 +76,7 @@ SIGNATURES = {
     "h2_get_dense_csr": (_I, [_P, _P, _P]),
     "h2_get_bases": (_I, [_P, _P, _P]),
     "h2_set_timing": (_I, [_P, _I]),
+    "h2_set_fp32_tensor": (_I, [_P, _I]),
     "h2_get_timing": (_I, [_P, _P, _P, _P]),
     "h2_destroy": (_I, [_P]),
     "h2_status_str": (C.c_char_p, [_I]),
@@ -266,6 +267,11 @@ def h2_get_bases(h: int):
 
 H2_NPHASES = 4
 PHASES = ("upsweep", "stream", "top", "downsweep")
+
+
+def h2_set_fp32_tensor(h: int, enable: bool) -> None:
+    """FP32 passes of more than 8 vectors on the tensor cores (3xTF32; default) or on the CUDA cores."""
+    _check(load().h2_set_fp32_tensor(h, int(bool(enable))), "h2_set_fp32_tensor")
 
 
 def h2_set_timing(h: int, enable: bool) -> None:

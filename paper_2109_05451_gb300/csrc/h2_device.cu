@@ -26,6 +26,7 @@
 #include "h2_kernels.cuh"
 #include "h2_stream.cuh"
 #include "h2_tcstream.cuh"
+#include "h2_tf32stream.cuh"
 #include "h2_batch.cuh"
 #include "h2_mf.cuh"
 #include "h2_nvtx.h"
@@ -65,6 +66,9 @@ struct h2_device {
     int max_leaf_rows = 0;
     bool root_row = false;  // the root has coupling blocks
     bool tc = false;        // split-BF16 blocks for the tensor-core stream (H2_BF16X2)
+    // FP32 operators with ranks and leaves of at most 64: passes of more than 8 vectors run on
+    // the tensor cores (3xTF32, k_stream_tf32) unless switched off by h2_set_fp32_tensor
+    bool tf32_ok = false, tf32_on = true;
     // views into the arena
     int32_t *perm = nullptr, *leaf_lo = nullptr;
     int64_t *cpl_rowptr = nullptr;
@@ -176,12 +180,16 @@ struct Workspace {
 };
 
 constexpr int kTcSmemBudget = 224 * 1024;  // dynamic shared memory of the tensor-core stream
+constexpr int kTfSmemBudget = 227 * 1024;  // of the 3xTF32 stream: the most one CTA may have
 constexpr int kWidePass = 32;  // vectors per pass of the wide kernels and of the tensor-core stream
 
 inline int pad16(int x) { return (x + 15) / 16 * 16; }
 
 // The wide accumulator holds tiles of at most 64 outputs.
 inline bool wide_ok(const h2_device &dv) { return dv.kx <= 64 && dv.mp <= 64; }
+
+// FP32 passes of this many vectors run on the tensor cores (3xTF32).
+inline bool tf32_pass(const h2_device &dv, int vp) { return dv.tf32_ok && dv.tf32_on && vp > 8; }
 
 // Vectors per pass: up to kWidePass on the tensor-core path and, for more than kChunk
 // vectors, on the wide kernels; otherwise kChunk.
@@ -199,11 +207,13 @@ size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, voi
 {
     const int vp = pass_vectors(dv, nv), np = pad16(vp);
     const bool wide = vp > kChunk || dv.tc;
+    const bool tiles = dv.tc;
+    const size_t tile_bytes = h2s::vec_tile_bytes(np);
     const size_t es = dv.esize;
     const size_t vec = align_up(size_t(op.nleaves()) * vp * dv.mp * es);
     const size_t tree = align_up(size_t(op.nnodes + 1) * vp * dv.kx * es);
-    const size_t xb = dv.tc ? align_up(size_t(op.nnodes + 1) * 2 * np * 128) : 0;
-    const size_t xtb = dv.tc ? align_up(size_t(op.nleaves()) * 2 * np * 128) : 0;
+    const size_t xb = tiles ? align_up(size_t(op.nnodes + 1) * tile_bytes) : 0;
+    const size_t xtb = tiles ? align_up(size_t(op.nleaves()) * tile_bytes) : 0;
     const size_t rows = wide ? align_up(size_t(op.n) * round4(vp) * es) : 0;
     if (w) {
         char *p = static_cast<char *>(base);
@@ -211,8 +221,8 @@ size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, voi
         w->yd = p + vec;
         w->xh = p + 2 * vec;
         w->yh = p + 2 * vec + tree;
-        w->xb = dv.tc ? reinterpret_cast<unsigned char *>(p + 2 * vec + 2 * tree) : nullptr;
-        w->xtb = dv.tc ? w->xb + xb : nullptr;
+        w->xb = tiles ? reinterpret_cast<unsigned char *>(p + 2 * vec + 2 * tree) : nullptr;
+        w->xtb = tiles ? w->xb + xb : nullptr;
         w->rows = wide ? p + 2 * vec + 2 * tree + xb + xtb : nullptr;
         w->tickets = reinterpret_cast<int *>(p + 2 * vec + 2 * tree + xb + xtb + rows);
     }
@@ -705,6 +715,77 @@ int launch_tc(const h2_op &op, h2_device &dv, const float *X, float *Y, int nv, 
     return H2_OK;
 }
 
+// Tensor-core stream over one descriptor list of the FP32 operator (3xTF32): NP = vectors
+// padded to 16 or 32.
+template <int NP>
+int launch_tf32_stream(h2_device &dv, const Workspace &w, int npass, const h2s::StreamDesc *desc,
+                       const int64_t *chunks, int64_t nchunks, int *ticket, cudaStream_t st)
+{
+    using namespace h2s;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_stream_tf32<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTfSmemBudget);
+        cudaFuncSetAttribute(k_stream_tf32<NP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr_done = true;
+    }
+    if (nchunks <= 0) return H2_OK;
+    int ns = 16;
+    while (ns > 2 && tf_smem_bytes(NP, ns) > kTfSmemBudget) --ns;
+    TfArgs a;
+    a.vals = dv.vals;
+    a.desc = desc;
+    a.chunks = chunks;
+    a.nchunks = nchunks;
+    a.xh = static_cast<const float *>(w.xh);
+    a.xt = static_cast<const float *>(w.xt);
+    a.yh = static_cast<float *>(w.yh);
+    a.yd = static_cast<float *>(w.yd);
+    a.nv = npass;
+    a.kx = dv.kx;
+    a.mp = dv.mp;
+    a.ticket = ticket;
+    a.err = dv.err;
+    a.ns = ns;
+    const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(dv.num_sms, nchunks)));
+    k_stream_tf32<NP><<<grid, kTfThreads, tf_smem_bytes(NP, ns), st>>>(a);
+    return cuda_status(cudaGetLastError());
+}
+
+// FP32 pass of 8 < nv <= NVMAX vectors with the block rows on the tensor cores (3xTF32): FP32
+// upsweep on the wide subtree kernels, the coupling and dense rows of every level (bottom,
+// then top descriptor list) on k_stream_tf32 (which splits blocks and vectors on chip), FP32
+// downsweep with the leaf expansion and the epilogue; one stream.
+template <int NVMAX>
+int launch_tf32_pass(const h2_op &op, h2_device &dv, const float *X, float *Y, int npass, double alpha, double beta,
+                     const Workspace &w, cudaStream_t st)
+{
+    using namespace h2s;
+    using T = float;
+    static_assert(NVMAX % 16 == 0, "tensor-core passes are padded to 16 vectors");
+    const Op<T> o = make_op<T>(op, dv);
+    Vec<T> v{X, Y, npass, npass, T(alpha), T(beta), static_cast<T *>(w.xt), static_cast<T *>(w.yd),
+             static_cast<T *>(w.xh), static_cast<T *>(w.yh), w.tickets, dv.err};
+    v.xr = v.yr = static_cast<T *>(w.rows);
+    v.ldr = round4(npass);
+    const SweepPlan<T, NVMAX> sp = make_sweep_plan<T, NVMAX>(op, dv);
+    set_kernel_attributes<T, NVMAX>();
+    cudaEvent_t ev = dv.begin(st);
+    const int lu = up_all(op, dv, o, v, sp, st);
+    dv.end(0, ev, st, lu);
+    ev = dv.begin(st);
+    int rc = launch_tf32_stream<NVMAX>(dv, w, npass, dv.desc_bottom, dv.chunks_bottom, dv.n_chunks_bottom,
+                                       w.tickets + 0, st);
+    if (rc == H2_OK)
+        rc = launch_tf32_stream<NVMAX>(dv, w, npass, dv.desc_top, dv.chunks_top, dv.n_chunks_top, w.tickets + 1, st);
+    dv.end(1, ev, st, int(dv.n_chunks_bottom > 0) + int(dv.n_chunks_top > 0));
+    if (rc != H2_OK) return rc;
+    ev = dv.begin(st);
+    const int ld = down_all(op, dv, o, v, sp, st);
+    dv.end(3, ev, st, ld);
+    return cuda_status(cudaGetLastError());
+}
+
 template <typename T>
 int launch_product(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
                    const Workspace &w, cudaStream_t st, const h2_exec &ex)
@@ -713,6 +794,14 @@ int launch_product(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, dou
     for (int v0 = 0; v0 < nv; v0 += vp) {
         const int c = std::min(vp, nv - v0);
         const size_t o = size_t(v0) * op.n;
+        if constexpr (sizeof(T) == 4) {
+            if (tf32_pass(dv, c)) {
+                const int rc = c <= 16 ? launch_tf32_pass<16>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
+                                       : launch_tf32_pass<32>(op, dv, X + o, Y + o, c, alpha, beta, w, st);
+                if (rc != H2_OK) return rc;
+                continue;
+            }
+        }
         const int rc = c == 1       ? launch_chunk<T, 1>(op, dv, X + o, Y + o, c, alpha, beta, w, st, ex)
                      : c <= kChunk  ? launch_chunk<T, kChunk>(op, dv, X + o, Y + o, c, alpha, beta, w, st, ex)
                      : c <= 8       ? launch_wide<T, 8>(op, dv, X + o, Y + o, c, alpha, beta, w, st)
@@ -1395,6 +1484,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     dv->kx = round4(k);
     dv->mp = round4(dv->max_leaf_rows);
     dv->kkp = int64_t(k) * round4(k);  // entries per stored coupling tile (ld kx)
+    dv->tf32_ok = prec == H2_FP32 && k <= 64 && dv->max_leaf_rows <= 64;
     dv->L = std::min(op.q, 4);
     dv->Lb = op.q - dv->L;
     dv->root_row = op.cpl_rowptr[2] > op.cpl_rowptr[1];
@@ -1706,6 +1796,14 @@ int h2_matvec(h2_handle h, const void *X, void *Y, int nv, double alpha, double 
     const int rc = h2_matvec_exec(h, X, Y, nv, alpha, beta, e->ws, e->bytes, cuda_stream, nullptr);
     cudaEventRecord(e->done, st);
     return rc;
+}
+
+int h2_set_fp32_tensor(h2_handle h, int enable)
+{
+    if (!h) return H2_EINVAL;
+    if (!h->dev) return H2_ESTATE;
+    h->dev->tf32_on = enable != 0;
+    return H2_OK;
 }
 
 int h2_set_timing(h2_handle h, int enable)

@@ -95,6 +95,23 @@ __host__ __device__ inline uint32_t sw128(int r, int k)
     return o ^ (((o >> 7) & 7u) << 4);
 }
 
+// Byte offset of element (row r, column k < 64) in a K-major tf32 tile of `rows` rows: two
+// K-blocks of 32 columns (128 bytes per row), each `rows` x 128 bytes with the 128-byte swizzle.
+__host__ __device__ inline uint32_t sw128_tf32(int r, int k, int rows)
+{
+    const uint32_t o = uint32_t(r) * 128u + uint32_t(k & 31) * 4u;
+    return uint32_t(k >> 5) * uint32_t(rows) * 128u + (o ^ (((o >> 7) & 7u) << 4));
+}
+
+// The split-TF32 pair of x: hi = x with its 13 low mantissa bits cleared (exact as a TF32
+// operand), lo = x - hi (exact in FP32, |lo| < 2^-10 |x|; the tensor core keeps it to TF32
+// precision).
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
+{
+    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    lo = x - hi;
+}
+
 struct Pipe {
     int ns;               // stages
     uint32_t tile_bytes;  // bytes of one tile slot

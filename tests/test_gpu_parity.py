@@ -180,6 +180,9 @@ def test_full_size_grid1024_sampled_leaves(grid1024, prec):
     w, op, X, rows, ref, orc = grid1024
     info = h2.h2_get_info(op.handle)
     assert info.depth == orc.depth == 14 and info.rank == 64
+    lvl, _, _, dt, _ = orc.blocks()
+    assert info.n_coupling == len(lvl) == 483456 and info.n_dense == len(dt) == 145924
+    assert [info.coupling_per_level[l] for l in range(15)] == np.bincount(lvl, minlength=15).tolist()
     op.upload(prec)
     got = gpu_matvec(op, X, prec)
     assert np.all(np.isfinite(got))
@@ -250,3 +253,27 @@ def test_loaded_operator_gives_the_same_product(built, prec, tmp_path):
         assert relerr(Y, orc.matvec(X)) <= TOL[prec]
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("nv", [9, 16, 32])
+@pytest.mark.parametrize("name", ["cloud3d_k64", "grid37_gauss_k25", "cloud3d_k27_ragged", "all_dense"])
+def test_fp32_tensor_and_cuda_core_passes_agree(built, name, nv):
+    """FP32 passes of more than 8 vectors: the 3xTF32 tensor-core stream (default) and the
+    CUDA-core FMA stream each meet the FP32 tolerance against the oracle; the two differ by
+    FP32 rounding only."""
+    pts, ker, orc, op = built(name)
+    op.upload("fp32")
+    X = si.gaussian_vectors(len(pts), nv, 31)
+    Y0 = si.gaussian_vectors(len(pts), nv, 32)
+    ref = orc.matvec(X, 0.75, 0.5, Y0)
+    h2.h2_set_fp32_tensor(op.handle, False)
+    try:
+        cuda_cores = gpu_matvec(op, X, "fp32", 0.75, 0.5, Y0)
+    finally:
+        h2.h2_set_fp32_tensor(op.handle, True)
+    tensor = gpu_matvec(op, X, "fp32", 0.75, 0.5, Y0)
+    assert np.all(np.isfinite(tensor))
+    assert relerr(cuda_cores, ref) <= TOL["fp32"]
+    assert relerr(tensor, ref) <= TOL["fp32"]
+    assert relerr(tensor, cuda_cores) <= TOL["fp32"]
+    assert np.array_equal(gpu_matvec(op, X, "fp32", 0.75, 0.5, Y0), tensor)  # no atomics on data
