@@ -644,12 +644,15 @@ def batch_roofline(total_bytes, total_flops, ms, ffma_peak=None):
             "peak_kind": f"{kind} HBM / {'measured' if ffma_peak else 'derived'} FP32 FMA"}
 
 
-def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with_fp64=True, ffma_peak=None):
+def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with_fp64=True, ffma_peak=None,
+                    plain=False):
     """Batched products of 64 uneven operators (synthetic_inputs.uneven_batch: N log-uniform
     in [2^12, 2^18], even members 2D grids with orders 4-8, odd members 3D clouds with orders
     3-4, exp(-r/l) with l in [0.05, 0.3], leaf 64, eta 0.7, nv in 1..16), FP32, as one
     graph-replayed batch (h2_batch_run, autotuned) against the same products issued one after
-    another (h2_matvec). The batch streams more than L2 holds, so no flush is needed."""
+    another (h2_matvec) and against the batch with each member's sweeps as its own launches.
+    The batch streams more than L2 holds, so no flush is needed. plain: the batched product
+    alone, default configuration (for profiler launch lists)."""
     members = si.uneven_batch(count=count, n_max=n_max)
     ops, Xs, Ys = [], [], []
     total_bytes = 0
@@ -665,7 +668,7 @@ def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with
     stream = torch.cuda.current_stream()
     try:
         t0 = time.perf_counter()
-        batch = h2.H2Batch(ops, Xs, Ys, autotune=True)
+        batch = h2.H2Batch(ops, Xs, Ys, autotune=not plain)
         create_s = time.perf_counter() - t0
         desc = batch.describe()
 
@@ -686,6 +689,13 @@ def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with
         batch.run()
         torch.cuda.synchronize()
         y32 = [Y.double().cpu().numpy() for Y in Ys]
+        if plain:
+            batch.close()
+            return {"batched_ms": float(np.median(ms_batch)), "configuration": desc}
+        # the earlier schedule: the same batch with every member's sweeps as its own launches
+        own = h2.H2Batch(ops, Xs, Ys, member_sweeps=True)
+        ms_own = float(np.median(timed(own.run)))
+        own.close()
         ms_seq = timed(lambda: [op.matvec(X, Y) for op, X, Y in zip(ops, Xs, Ys)])
         batch.close()
         mb, msq = float(np.median(ms_batch)), float(np.median(ms_seq))
@@ -712,7 +722,8 @@ def batch_benchmark(h2, torch, steps=10, warmup=3, count=64, n_max=2 ** 18, with
                 "batched_ms": mb, "batched_GB/s": total_bytes / (mb * 1e-3) / 1e9,
                 "batched_gflops": total_flops / (mb * 1e-3) / 1e9,
                 "sequential_ms": msq, "sequential_GB/s": total_bytes / (msq * 1e-3) / 1e9,
-                "speedup_vs_sequential": msq / mb, "create_s": create_s, "configuration": desc,
+                "speedup_vs_sequential": msq / mb, "member_sweeps_ms": ms_own,
+                "create_s": create_s, "configuration": desc,
                 "roofline": batch_roofline(total_bytes, total_flops, mb, ffma_peak),
                 "fp64": fp64, "l2": "inputs larger than L2, no flush"}
     finally:
@@ -771,6 +782,9 @@ def main():
     ap.add_argument("--compress-grid", type=int, default=1024, help="grid side of the 2D compression set")
     ap.add_argument("--compress-steps", type=int, default=3, help="timed compressions per set")
     ap.add_argument("--batch-count", type=int, default=64, help="operators of the batched measurement")
+    ap.add_argument("--batch-steps", type=int, default=10, help="timed replays of the batched measurement")
+    ap.add_argument("--batch-plain", action="store_true",
+                    help="time the batched product alone in its default configuration (profiler launch lists)")
     ap.add_argument("--batch-nmax", type=int, default=2 ** 18,
                     help="largest N of the batched measurement (smaller values are for profiler captures)")
     ap.add_argument("--serve-maxit", type=int, default=100, help="CG iteration cap of each served solve")
@@ -978,8 +992,9 @@ def main():
             line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batch:
         try:
-            line["batch"] = batch_benchmark(h2, torch, count=args.batch_count, n_max=args.batch_nmax,
-                                            with_fp64=not args.no_fp64, ffma_peak=ffma_peak)
+            line["batch"] = batch_benchmark(h2, torch, steps=args.batch_steps, count=args.batch_count,
+                                            n_max=args.batch_nmax, with_fp64=not args.no_fp64, ffma_peak=ffma_peak,
+                                            plain=args.batch_plain)
         except Exception as exc:  # reported, never silently dropped
             line["batch"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_compress:

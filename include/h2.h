@@ -299,8 +299,10 @@ int h2_destroy(h2_handle h);
  * member i: Y_i = alpha A_i X_i + beta Y_i with nv[i] vectors (device, column-major, ld = n_i,
  * element type of the uploads). The members' coupling and dense block rows of every level
  * form one work list that a persistent launch streams (one launch per width class of nv:
- * 1, 2-4, 5-8, 9-16, 17-32); the members' upsweeps and downsweeps run on parallel branches
- * before and after it. The whole product is captured once as a CUDA graph and replayed by
+ * 1, 2-4, 5-8, 9-16, 17-32 and tile-size class); the members' upsweeps and downsweeps run
+ * as merged launches too, one per sweep step and width class over a table of the members'
+ * subtrees (Sec. 3.1 and 3.3 per member), so a replay takes a few dozen launches whatever
+ * the member count. The whole product is captured once as a CUDA graph and replayed by
  * h2_batch_run, always with the X, Y, alpha and beta given here (update the contents of X
  * and Y between runs, not the pointers). All members share one precision, FP64 or FP32 (not
  * H2_BF16X2), and take one pass each (nv <= 4, or nv <= 32 when k <= 64 and leaves hold <= 64
@@ -308,9 +310,12 @@ int h2_destroy(h2_handle h);
  * flags: H2_BATCH_AUTOTUNE times candidate launch configurations of each merged stream (CTAs
  * per SM, pipeline stages, scheduling chunk size) and appends the best to the autotuning
  * cache (the file named by the environment variable H2_TUNE_CACHE, else h2_autotune.txt next
- * to the library); without it a cached choice is used when present, else a default. */
+ * to the library); without it a cached choice is used when present, else a default.
+ * H2_BATCH_MEMBER_SWEEPS runs each member's sweeps as its own launches instead of the merged
+ * ones (the earlier schedule, kept for comparison). */
 typedef struct h2_batch *h2_batch_t;
 #define H2_BATCH_AUTOTUNE 1
+#define H2_BATCH_MEMBER_SWEEPS 2
 int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void *const *Y, const int *nv, double alpha,
                     double beta, int flags, h2_batch_t *out);
 /* Replay the batched product on the stream (asynchronous). */

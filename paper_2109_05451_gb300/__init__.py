@@ -451,6 +451,7 @@ class H2Server:
 
 
 H2_BATCH_AUTOTUNE = 1
+H2_BATCH_MEMBER_SWEEPS = 2
 
 
 class H2Batch:
@@ -458,7 +459,8 @@ class H2Batch:
     every member, captured once as a CUDA graph and replayed by run(). Xs, Ys: CUDA tensors
     (n_i, nv_i), column-major, of the members' element type; kept alive by the batch."""
 
-    def __init__(self, ops, Xs, Ys, alpha: float = 1.0, beta: float = 0.0, autotune: bool = False):
+    def __init__(self, ops, Xs, Ys, alpha: float = 1.0, beta: float = 0.0, autotune: bool = False,
+                 member_sweeps: bool = False):
         if not (len(ops) == len(Xs) == len(Ys)) or not ops:
             raise ValueError("ops, Xs and Ys must have the same nonzero length")
         nvs = []
@@ -474,7 +476,9 @@ class H2Batch:
         nv_arr = (C.c_int * n)(*nvs)
         h = C.c_void_p()
         _check(load().h2_batch_create(hs, n, xs, ys, nv_arr, float(alpha), float(beta),
-                                      H2_BATCH_AUTOTUNE if autotune else 0, C.byref(h)), "h2_batch_create")
+                                      (H2_BATCH_AUTOTUNE if autotune else 0)
+                                      | (H2_BATCH_MEMBER_SWEEPS if member_sweeps else 0), C.byref(h)),
+               "h2_batch_create")
         self.handle = h.value
         self._keep = (list(ops), list(Xs), list(Ys))
 

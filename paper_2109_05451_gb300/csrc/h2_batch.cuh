@@ -120,4 +120,98 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ------------------------------------------------------------------ merged sweeps
+//
+// The members' up- and downsweeps run as merged launches too: one launch per sweep step and
+// accumulator width over a task table (one SweepTask per member, its items numbered after
+// the previous member's), so a batch takes a few launches per width instead of a dozen per
+// member. The subtree steps are k_up_batch / k_down_batch (h2_stream.cuh); the gathers and
+// the row-major staging of wide passes are below, one item per leaf or per 32-point tile.
+
+// Members' gathers: xt[leaf][v][i] = X[v n + perm[..]] (narrow passes, as k_gather) or from
+// the row-major staging copy (wide passes, as k_gather_rows). Resets each member's tickets.
+template <typename T>
+__global__ void k_gather_batch(const SweepTask<T> *__restrict__ tasks, int ntasks, int64_t total, int rows)
+{
+    __shared__ T buf[64 * 33];
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const SweepTask<T> &t = tasks[sweep_task_of(tasks, ntasks, g)];
+        const Op<T> &op = t.op;
+        const Vec<T> &vec = t.vec;
+        const int64_t leaf = g - t.first;
+        if (leaf == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
+        const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
+        if (!rows) {
+            for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+                const int i = e % R, v = e / R;
+                vec.xt[(leaf * vec.vs + v) * op.mp + i] = vec.X[int64_t(v) * op.n + op.perm[r0 + i]];
+            }
+        } else {
+            for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+                const int i = e / vec.nv, v = e % vec.nv;
+                buf[i * 33 + v] = vec.xr[int64_t(op.perm[r0 + i]) * vec.ldr + v];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {
+                const int v = e / R, i = e % R;
+                vec.xt[(leaf * vec.vs + v) * op.mp + i] = buf[i * 33 + v];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Members' row-major staging of X (as k_rows_in; nv <= 32): one 32-point tile per item.
+// Block 32 x 8.
+template <typename T>
+__global__ void k_rows_in_batch(const SweepTask<T> *__restrict__ tasks, int ntasks, int64_t total)
+{
+    __shared__ T tt[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const SweepTask<T> &t = tasks[sweep_task_of(tasks, ntasks, g)];
+        const int64_t n = t.op.n, u0 = (g - t.first) * 32;
+        const int nv = t.vec.nv, ldr = t.vec.ldr;
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t u = u0 + tx;
+            if (u < n && j < nv) tt[j][tx] = t.vec.X[int64_t(j) * n + u];
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t u = u0 + j;
+            if (u < n && tx < nv) t.vec.xr[u * ldr + tx] = tt[tx][j];
+        }
+        __syncthreads();
+    }
+}
+
+// Members' epilogue of wide passes (as k_rows_out): Y[v n + u] = alpha yr[u ldr + v] + beta
+// Y[v n + u], Y not read when beta = 0. Block 32 x 8.
+template <typename T>
+__global__ void k_rows_out_batch(const SweepTask<T> *__restrict__ tasks, int ntasks, int64_t total)
+{
+    __shared__ T tt[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const SweepTask<T> &t = tasks[sweep_task_of(tasks, ntasks, g)];
+        const int64_t n = t.op.n, u0 = (g - t.first) * 32;
+        const int nv = t.vec.nv, ldr = t.vec.ldr;
+        const T alpha = t.vec.alpha, beta = t.vec.beta;
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t u = u0 + j;
+            if (u < n && tx < nv) tt[j][tx] = t.vec.yr[u * ldr + tx];
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t u = u0 + tx;
+            if (u < n && j < nv) {
+                T *dst = t.vec.Y + int64_t(j) * n + u;
+                const T y = tt[tx][j];
+                *dst = (beta == T(0)) ? alpha * y : alpha * y + beta * *dst;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace h2s

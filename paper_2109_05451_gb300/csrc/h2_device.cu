@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -958,6 +959,7 @@ struct h2_batch {
         void *Y;
         int nv;
         Workspace w;
+        bool merged = false;  // its sweeps run inside the merged launches of its width
     };
     struct Group {
         int width = 0;
@@ -974,11 +976,30 @@ struct h2_batch {
         StreamCfg cfg;
         bool tuned = false;
     };
+    // merged sweeps: per accumulator width, one launch per sweep step over all members of
+    // that width (a task table per launch, all tables of a width in one device allocation)
+    struct SweepLaunch {
+        int kind = 0;           // kRowsIn, kGather, kUp, kDown, kRowsOut
+        size_t task_off = 0;    // first task of this launch in the width's table
+        int ntasks = 0;
+        int64_t total = 0;      // work items: 32-point tiles, leaves or subtrees
+        h2s::Pipe pp{1, 0, 0};  // subtree steps: stages sized for the largest tiles
+        int sub_kx = 0;         // subtree steps: the largest subtree buffer (slots x kx)
+        int rows = 0;           // gather: from the row-major staging copy
+        size_t smem = 0;
+        unsigned grid = 1;
+    };
+    struct SweepClass {
+        int width = 0;
+        void *d_tasks = nullptr;
+        std::vector<SweepLaunch> up, down;
+    };
     int device = 0, num_sms = 0;
     size_t esize = 4;
     double alpha = 1, beta = 0;
     std::vector<Member> members;
     std::vector<Group> groups;
+    std::vector<SweepClass> sweeps;
     void *ws_mem = nullptr;
     int *d_flags = nullptr;                  // [0, kBatchGroups) tickets per group, [kBatchGroups] error flag
     std::vector<cudaStream_t> branches;
@@ -1093,47 +1114,298 @@ int batch_set_chunks(h2_batch::Group &g, uint64_t target)
     return H2_OK;
 }
 
-// The whole batched product on the capture stream: upsweeps on branch streams, the merged
-// streams after all of them, downsweeps on the branches, joined back. Without the
-// downsweeps (with_down false) nothing of the members' X and Y is written.
+constexpr int kRowsIn = 0, kGather = 1, kUp = 2, kDown = 3, kRowsOut = 4;  // merged sweep steps
+
+// The merged sweeps of the members `mem` (all of accumulator width W): one launch per step --
+// [row-major staging], gather, bottom subtrees and each run of upper levels (up), the upper
+// levels, bottom subtrees with the leaf epilogue, [staging back] (down) -- each over a task
+// table with one task per member, the member with the most work items first. The steps are
+// the ones up_all / down_all launch for one operator, in the same order. Returns false when
+// a subtree step cannot be staged in 200 KB (the width then keeps per-member sweeps).
+template <typename T, int W>
+bool batch_build_sweeps(h2_batch &b, const std::vector<int> &mem, h2_batch::SweepClass &sc)
+{
+    using namespace h2s;
+    const size_t es = sizeof(T);
+    struct Info {
+        SweepTask<T> base;
+        SweepPlan<T, W> sp;
+        int q;
+        uint32_t tile, xseg;
+        std::vector<std::array<int, 2>> up_top, down_top;  // (Lr, L) of each run of upper levels
+    };
+    std::vector<Info> inf;
+    for (int i : mem) {
+        h2_batch::Member &m = b.members[size_t(i)];
+        const h2_op &op = *m.op;
+        h2_device &dv = *op.dev;
+        Info f;
+        f.base.op = make_op<T>(op, dv);
+        f.base.vec = Vec<T>{static_cast<const T *>(m.X), static_cast<T *>(m.Y), m.nv, m.nv, T(b.alpha), T(b.beta),
+                            static_cast<T *>(m.w.xt), static_cast<T *>(m.w.yd), static_cast<T *>(m.w.xh),
+                            static_cast<T *>(m.w.yh), m.w.tickets, dv.err};
+        if (W >= kWideMin) {
+            f.base.vec.xr = f.base.vec.yr = static_cast<T *>(m.w.rows);
+            f.base.vec.ldr = round4(m.nv);
+        }
+        f.sp = make_sweep_plan<T, W>(op, dv);
+        f.q = op.q;
+        const int k = op.k, kx = dv.kx, mp = dv.mp;
+        f.tile = uint32_t(std::max({size_t(mp) * kx, size_t(k) * kx, size_t(k) * mp}) * es);
+        f.xseg = uint32_t(2 * std::max(mp, kx) * W * es);
+        for (int lin = op.q - f.sp.Lw; lin > 0;) {
+            const int L = std::min(f.sp.Ltop, lin), lr = lin - L;
+            f.up_top.push_back({lr, L});
+            lin = lr;
+        }
+        const int Lr0 = op.q - f.sp.Lw;
+        for (int lr = 0; lr <= Lr0 - 1;) {
+            const int L = std::min(f.sp.Ltop, Lr0 - 1 - lr);
+            f.down_top.push_back({lr, L});
+            lr += L + 1;
+        }
+        inf.push_back(f);
+    }
+    std::vector<SweepTask<T>> all;
+    bool ok = true;
+    auto push = [&](std::vector<h2_batch::SweepLaunch> &list, int kind, std::vector<SweepTask<T>> tk,
+                    uint32_t tile, uint32_t xseg, int sub_kx, int rows) {
+        if (!ok || tk.empty()) return;
+        std::stable_sort(tk.begin(), tk.end(), [](const SweepTask<T> &x, const SweepTask<T> &y) { return x.nsub > y.nsub; });
+        int64_t first = 0;
+        for (auto &t : tk) {
+            t.first = first;
+            first += t.nsub;
+        }
+        h2_batch::SweepLaunch L;
+        L.kind = kind;
+        L.task_off = all.size();
+        L.ntasks = int(tk.size());
+        L.total = first;
+        L.rows = rows;
+        L.sub_kx = sub_kx;
+        if (kind == kUp || kind == kDown) {
+            int per_sm = 2;
+            L.pp = make_pipe<T, W>(tile, xseg, 1, sub_kx, false, 100 * 1024, 8);
+            L.smem = smem_bytes<T, W>(L.pp, 1, sub_kx, false);
+            if (L.pp.ns < 2 || L.smem > 100 * 1024) {
+                per_sm = 1;
+                L.pp = make_pipe<T, W>(tile, xseg, 1, sub_kx, false, 200 * 1024, 8);
+                L.smem = smem_bytes<T, W>(L.pp, 1, sub_kx, false);
+            }
+            if (L.pp.ns < 2 || L.smem > 200 * 1024) {
+                ok = false;
+                return;
+            }
+            L.grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(first, int64_t(b.num_sms) * per_sm)));
+        } else {
+            L.grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(first, 65535)));
+        }
+        all.insert(all.end(), tk.begin(), tk.end());
+        list.push_back(L);
+    };
+    auto task = [](const Info &f, int Lr, int L, int flag, int64_t nsub) {
+        SweepTask<T> t = f.base;
+        t.Lr = Lr;
+        t.L = L;
+        t.flag = flag;
+        t.nsub = nsub;
+        return t;
+    };
+    // a subtree step over the given (member, Lr, L, flag) tasks: stages for the largest tiles
+    auto subtree_step = [&](std::vector<h2_batch::SweepLaunch> &list, int kind, const std::vector<SweepTask<T>> &tk,
+                            const std::vector<const Info *> &who) {
+        uint32_t tile = 0, xseg = 0;
+        int sub_kx = 0;
+        for (size_t j = 0; j < tk.size(); ++j) {
+            tile = std::max(tile, who[j]->tile);
+            xseg = std::max(xseg, who[j]->xseg);
+            sub_kx = std::max(sub_kx, (2 << tk[j].L) * tk[j].op.kx);
+        }
+        push(list, kind, tk, tile, xseg, sub_kx, 0);
+    };
+    std::vector<SweepTask<T>> tk;
+    std::vector<const Info *> who;
+    // ---- up
+    if (W >= kWideMin) {
+        for (auto &f : inf) tk.push_back(task(f, 0, 0, 0, (f.base.op.n + 31) / 32));
+        push(sc.up, kRowsIn, tk, 0, 0, 0, 0);
+        tk.clear();
+    }
+    for (auto &f : inf) tk.push_back(task(f, 0, 0, 0, f.base.op.nleaves));
+    push(sc.up, kGather, tk, 0, 0, 0, W >= kWideMin ? 1 : 0);
+    tk.clear();
+    for (auto &f : inf) {
+        tk.push_back(task(f, f.q - f.sp.Lw, f.sp.Lw, 1, f.sp.nsub));
+        who.push_back(&f);
+    }
+    subtree_step(sc.up, kUp, tk, who);
+    size_t runs = 0;
+    for (auto &f : inf) runs = std::max(runs, f.up_top.size());
+    for (size_t j = 0; j < runs; ++j) {
+        tk.clear();
+        who.clear();
+        for (auto &f : inf)
+            if (j < f.up_top.size()) {
+                tk.push_back(task(f, f.up_top[j][0], f.up_top[j][1], 0, int64_t(1) << f.up_top[j][0]));
+                who.push_back(&f);
+            }
+        subtree_step(sc.up, kUp, tk, who);
+    }
+    // ---- down
+    runs = 0;
+    for (auto &f : inf) runs = std::max(runs, f.down_top.size());
+    for (size_t j = 0; j < runs; ++j) {
+        tk.clear();
+        who.clear();
+        for (auto &f : inf)
+            if (j < f.down_top.size()) {
+                tk.push_back(task(f, f.down_top[j][0], f.down_top[j][1], 0, int64_t(1) << f.down_top[j][0]));
+                who.push_back(&f);
+            }
+        subtree_step(sc.down, kDown, tk, who);
+    }
+    tk.clear();
+    who.clear();
+    for (auto &f : inf) {
+        tk.push_back(task(f, f.q - f.sp.Lw, f.sp.Lw, 1, f.sp.nsub));
+        who.push_back(&f);
+    }
+    subtree_step(sc.down, kDown, tk, who);
+    if (W >= kWideMin) {
+        tk.clear();
+        for (auto &f : inf) tk.push_back(task(f, 0, 0, 0, (f.base.op.n + 31) / 32));
+        push(sc.down, kRowsOut, tk, 0, 0, 0, 0);
+    }
+    if (!ok) {
+        sc.up.clear();
+        sc.down.clear();
+        return false;
+    }
+    if (cudaMalloc(&sc.d_tasks, std::max<size_t>(1, all.size()) * sizeof(SweepTask<T>)) != cudaSuccess) {
+        cudaGetLastError();
+        sc.d_tasks = nullptr;
+        sc.up.clear();
+        sc.down.clear();
+        return false;
+    }
+    if (cudaMemcpy(sc.d_tasks, all.data(), all.size() * sizeof(SweepTask<T>), cudaMemcpyHostToDevice) != cudaSuccess) {
+        sc.up.clear();
+        sc.down.clear();
+        return false;
+    }
+    static bool attr = false;
+    if (!attr) {
+        for (const void *fn : {(const void *)k_up_batch<T, W>, (const void *)k_down_batch<T, W>}) {
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        }
+        attr = true;
+    }
+    return true;
+}
+
+template <typename T, int W>
+void batch_sweep_launch(const h2_batch::SweepClass &sc, const h2_batch::SweepLaunch &L, cudaStream_t st)
+{
+    using namespace h2s;
+    const SweepTask<T> *t = static_cast<const SweepTask<T> *>(sc.d_tasks) + L.task_off;
+    switch (L.kind) {
+    case kRowsIn: k_rows_in_batch<T><<<L.grid, dim3(32, 8), 0, st>>>(t, L.ntasks, L.total); break;
+    case kGather: k_gather_batch<T><<<L.grid, 128, 0, st>>>(t, L.ntasks, L.total, L.rows); break;
+    case kUp: k_up_batch<T, W><<<L.grid, kThreads, L.smem, st>>>(t, L.ntasks, L.total, L.pp, L.sub_kx); break;
+    case kDown: k_down_batch<T, W><<<L.grid, kThreads, L.smem, st>>>(t, L.ntasks, L.total, L.pp, L.sub_kx); break;
+    default: k_rows_out_batch<T><<<L.grid, dim3(32, 8), 0, st>>>(t, L.ntasks, L.total); break;
+    }
+}
+
+// One width's merged up- (up = true) or downsweep launches, in order, on one stream.
+template <typename T>
+void batch_sweeps_enqueue(const h2_batch::SweepClass &sc, bool up, cudaStream_t st)
+{
+    for (const auto &L : up ? sc.up : sc.down) {
+        switch (sc.width) {
+        case 1: batch_sweep_launch<T, 1>(sc, L, st); break;
+        case kChunk: batch_sweep_launch<T, kChunk>(sc, L, st); break;
+        case 8: batch_sweep_launch<T, 8>(sc, L, st); break;
+        case 16: batch_sweep_launch<T, 16>(sc, L, st); break;
+        default: batch_sweep_launch<T, 32>(sc, L, st); break;
+        }
+    }
+}
+
+// Builds the merged sweeps of every width present in the batch.
+template <typename T>
+int batch_build_all_sweeps(h2_batch &b)
+{
+    for (int w : {1, kChunk, 8, 16, 32}) {
+        std::vector<int> mem;
+        for (size_t i = 0; i < b.members.size(); ++i)
+            if (width_class(b.members[i].nv) == w) mem.push_back(int(i));
+        if (mem.empty()) continue;
+        h2_batch::SweepClass sc;
+        sc.width = w;
+        bool built = false;
+        switch (w) {
+        case 1: built = batch_build_sweeps<T, 1>(b, mem, sc); break;
+        case kChunk: built = batch_build_sweeps<T, kChunk>(b, mem, sc); break;
+        case 8: built = batch_build_sweeps<T, 8>(b, mem, sc); break;
+        case 16: built = batch_build_sweeps<T, 16>(b, mem, sc); break;
+        default: built = batch_build_sweeps<T, 32>(b, mem, sc); break;
+        }
+        if (!built) {
+            if (sc.d_tasks) cudaFree(sc.d_tasks);
+            continue;  // this width keeps per-member sweeps
+        }
+        for (int i : mem) b.members[size_t(i)].merged = true;
+        b.sweeps.push_back(sc);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+// The whole batched product on the capture stream, in three phases on the branch streams:
+// upsweeps (each width's merged sweep launches on a branch of its own; members of a width
+// without merged sweeps one by one on the other branches), the merged block streams (one per
+// group, concurrently: they write disjoint rows, so one group's tail overlaps the others'
+// work), downsweeps. Every phase forks all branches from the capture stream and joins them
+// back. Without the downsweeps (with_down false) nothing of the members' Y is written.
 template <typename T>
 int batch_enqueue(h2_batch &b, cudaStream_t st, bool with_down = true)
 {
-    int rc = cuda_status(cudaEventRecord(b.ev_fork, st));
     const size_t nb = b.branches.size();
-    for (size_t i = 0; rc == H2_OK && i < b.members.size(); ++i) {
-        cudaStream_t br = b.branches[i % nb];
-        if (i < nb) cudaStreamWaitEvent(br, b.ev_fork, 0);
-        batch_member_sweep<T>(b, b.members[i], br, true);
-    }
-    if (rc == H2_OK) rc = cuda_status(cudaGetLastError());
-    for (size_t j = 0; rc == H2_OK && j < std::min(nb, b.members.size()); ++j) {
-        cudaEventRecord(b.ev_branch[j], b.branches[j]);
-        cudaStreamWaitEvent(st, b.ev_branch[j], 0);
-    }
+    auto fork = [&](cudaEvent_t ev) {
+        int rc = cuda_status(cudaEventRecord(ev, st));
+        for (size_t j = 0; rc == H2_OK && j < nb; ++j) rc = cuda_status(cudaStreamWaitEvent(b.branches[j], ev, 0));
+        return rc;
+    };
+    auto join = [&]() {
+        int rc = H2_OK;
+        for (size_t j = 0; rc == H2_OK && j < nb; ++j) {
+            rc = cuda_status(cudaEventRecord(b.ev_branch[j], b.branches[j]));
+            if (rc == H2_OK) rc = cuda_status(cudaStreamWaitEvent(st, b.ev_branch[j], 0));
+        }
+        return rc;
+    };
+    auto sweeps = [&](bool up) {
+        const size_t nc = b.sweeps.size();
+        for (size_t c = 0; c < nc; ++c) batch_sweeps_enqueue<T>(b.sweeps[c], up, b.branches[c % nb]);
+        size_t k = 0;
+        for (size_t i = 0; i < b.members.size(); ++i)
+            if (!b.members[i].merged) batch_member_sweep<T>(b, b.members[i], b.branches[(nc + k++) % nb], up);
+        return cuda_status(cudaGetLastError());
+    };
+    int rc = fork(b.ev_fork);
+    if (rc == H2_OK) rc = sweeps(true);
+    if (rc == H2_OK) rc = join();
     if (rc == H2_OK) rc = cuda_status(cudaMemsetAsync(b.d_flags, 0, kBatchGroups * sizeof(int), st));
-    // the merged streams write disjoint rows: they run concurrently on the branches, so one
-    // group's tail overlaps the others' work
-    if (rc == H2_OK) rc = cuda_status(cudaEventRecord(b.ev_mid, st));
-    const size_t ng = std::min(nb, b.groups.size());
-    for (size_t gi = 0; rc == H2_OK && gi < b.groups.size(); ++gi) {
-        cudaStream_t br = b.branches[gi % nb];
-        if (gi < ng) cudaStreamWaitEvent(br, b.ev_mid, 0);
-        rc = batch_group_stream_any<T>(b, b.groups[gi], int(gi), br);
-    }
-    for (size_t j = 0; rc == H2_OK && j < ng; ++j) {
-        cudaEventRecord(b.ev_branch[j], b.branches[j]);
-        cudaStreamWaitEvent(st, b.ev_branch[j], 0);
-    }
-    if (rc == H2_OK) rc = cuda_status(cudaEventRecord(b.ev_mid, st));
-    for (size_t i = 0; rc == H2_OK && with_down && i < b.members.size(); ++i) {
-        cudaStream_t br = b.branches[i % nb];
-        if (i < nb) cudaStreamWaitEvent(br, b.ev_mid, 0);
-        batch_member_sweep<T>(b, b.members[i], br, false);
-    }
-    for (size_t j = 0; rc == H2_OK && with_down && j < std::min(nb, b.members.size()); ++j) {
-        cudaEventRecord(b.ev_branch[j], b.branches[j]);
-        cudaStreamWaitEvent(st, b.ev_branch[j], 0);
+    if (rc == H2_OK) rc = fork(b.ev_mid);
+    for (size_t gi = 0; rc == H2_OK && gi < b.groups.size(); ++gi)
+        rc = batch_group_stream_any<T>(b, b.groups[gi], int(gi), b.branches[gi % nb]);
+    if (rc == H2_OK) rc = join();
+    if (rc == H2_OK && with_down) {
+        rc = fork(b.ev_mid);
+        if (rc == H2_OK) rc = sweeps(false);
+        if (rc == H2_OK) rc = join();
     }
     if (rc == H2_OK) rc = cuda_status(cudaGetLastError());
     return rc;
@@ -1264,6 +1536,8 @@ void batch_free(h2_batch *b)
         if (g.d_chunks) cudaFree(g.d_chunks);
         if (g.d_ops) cudaFree(g.d_ops);
     }
+    for (auto &c : b->sweeps)
+        if (c.d_tasks) cudaFree(c.d_tasks);
     for (cudaStream_t s : b->branches) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->ev_branch) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
@@ -2070,6 +2344,8 @@ int h2_batch_create(const h2_handle *ops, int count, const void *const *X, void 
         if (rc == H2_OK) rc = cuda_status(cudaMalloc(&g.d_chunks, g.chunk_cap * 8));
     }
     if (rc == H2_OK) rc = esize == 8 ? batch_build_group_tables<double>(*b) : batch_build_group_tables<float>(*b);
+    if (rc == H2_OK && !(flags & H2_BATCH_MEMBER_SWEEPS))
+        rc = esize == 8 ? batch_build_all_sweeps<double>(*b) : batch_build_all_sweeps<float>(*b);
     if (rc == H2_OK && b->groups.size() > size_t(kBatchGroups)) rc = H2_EINVAL;
     if (rc == H2_OK) rc = cuda_status(cudaMalloc(&b->d_flags, (kBatchGroups + 1) * sizeof(int)));
     if (rc == H2_OK) rc = cuda_status(cudaMemset(b->d_flags, 0, (kBatchGroups + 1) * sizeof(int)));
@@ -2147,6 +2423,11 @@ int h2_batch_describe(h2_batch_t b, char *buf, size_t len)
         o << "; width " << g.width << ": members " << g.members.size() << " blocks " << g.desc.size() << " chunks "
           << g.nchunks << " ctas/sm " << g.cfg.per_sm << " stages " << g.cfg.ns << " chunk " << g.cfg.chunk_target
           << (g.tuned ? " (tuned)" : " (default)") << " tiles<=" << g.tile_class;
+    size_t own = 0;
+    for (const auto &m : b->members) own += m.merged ? 0 : 1;
+    for (const auto &c : b->sweeps)
+        o << "; sweeps width " << c.width << ": " << c.up.size() << " up + " << c.down.size() << " down launches";
+    o << "; members with their own sweeps " << own;
     const std::string str = o.str();
     const size_t n = std::min(len - 1, str.size());
     std::memcpy(buf, str.data(), n);

@@ -892,99 +892,176 @@ __global__ void k_rows_out(const T *__restrict__ yr, int ldr, T *__restrict__ Y,
 // input (Lr+L = q) the inputs are the leaf projections xhat^q_t = U_t^T x_t; otherwise they
 // are the coefficient vectors of level Lr+L computed by an earlier launch. Writes xhat for
 // levels Lr .. Lr+L (the input level only with leaf input).
+//
+// The work of one subtree st is split into its producer part (the tiles in the order the
+// consumers use them) and its consumer part, so that one kernel (k_up_sub) walks the
+// subtrees of one operator and another (k_up_batch) a merged list over many operators.
+
+// One subtree's tiles into the ring; false once the pipeline aborted.
+template <typename T, int NVMAX>
+__device__ bool up_sub_produce(const Op<T> &op, const Vec<T> &vec, Smem<T> &s, const Pipe &pp, Ring &ring, int Lr,
+                               int L, int64_t st, int leaf_input)
+{
+    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
+    const int Lin = Lr + L;
+    const uint32_t es = sizeof(T);
+    bool ok = true;
+    if (leaf_input) {
+        const int64_t leaf0 = st << L;
+        for (int j = 0; ok && j < (1 << L); ++j) {
+            const int64_t leaf = leaf0 + j;
+            ok = produce(s, pp, ring, op.U + leaf * mp * kx, mp * kx * es, vec.xt + leaf * mp * vs, mp * nv * es,
+                         nullptr, 0, nullptr, vec.err);
+        }
+    }
+    for (int lev = Lin; ok && lev > Lr; --lev) {
+        const int64_t cnt = int64_t(1) << (lev - Lr);
+        const int64_t c0 = (int64_t(1) << lev) + st * cnt;
+        // an input level from an earlier launch travels with its transfer tiles
+        const bool with_x = !leaf_input && lev == Lin;
+        for (int64_t c = c0; ok && c < c0 + cnt; ++c)
+            ok = produce(s, pp, ring, op.E + c * k * kx, k * kx * es, with_x ? vec.xh + c * kx * vs : nullptr,
+                         with_x ? kx * nv * es : 0, nullptr, 0, nullptr, vec.err);
+    }
+    return ok;
+}
+
+// One subtree's products (consumer warps); false once the pipeline aborted.
+template <typename T, int NVMAX>
+__device__ bool up_sub_consume(const Op<T> &op, const Vec<T> &vec, Smem<T> &s, const Pipe &pp, Ring &ring,
+                               AccOf<T, NVMAX> &acc, int Lr, int L, int64_t st, int leaf_input)
+{
+    const int lane = threadIdx.x % 32;
+    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
+    const int Lin = Lr + L;
+    const int wstride = kx * NVMAX;
+    if (leaf_input) {
+        // leaf projections into local slots 2^L + j
+        const int64_t leaf0 = st << L;
+        for (int j = 0; j < (1 << L); ++j) {
+            const int64_t leaf = leaf0 + j;
+            const int R = op.leaf_lo[leaf + 1] - op.leaf_lo[leaf];
+            acc.zero();
+            if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return false;
+            acc.gemv(stage_tile(s, pp, ring.stage), kx, k, R, stage_x(s, pp, ring.stage), mp, nv);
+            release(&s.empty[ring.stage], lane);
+            ring.next();
+            if (acc.reduce(k, nv, s.red)) {
+                acc.store(s.sub + ((1 << L) + j) * wstride, kx, nv, k);
+                acc.store(vec.xh + (op.first_leaf + leaf) * kx * vs, kx, nv, k);
+            }
+            if constexpr (NVMAX >= kWideMin)
+                if (vec.xb) acc.store_tile(vec.xb + (op.first_leaf + leaf) * vec_tile_bytes(vec.np), vec.np, nv, k);
+            h2p::consumer_sync(kConsumers);
+        }
+    }
+    // transfers, level by level (the input level of a launch without leaf input arrives in
+    // the stages, next to its transfer tiles)
+    for (int lev = Lin; lev > Lr; --lev) {
+        const int rel = lev - Lr;
+        const int64_t cnt = int64_t(1) << rel;
+        const bool staged_x = !leaf_input && lev == Lin;
+        for (int64_t pi = 0; pi < cnt / 2; ++pi) {
+            acc.zero();
+            for (int c = 0; c < 2; ++c) {
+                const int child_slot = (1 << rel) + int(2 * pi + c);
+                if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return false;
+                const T *xc = staged_x ? stage_x(s, pp, ring.stage) : s.sub + child_slot * wstride;
+                acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, xc, kx, nv);
+                release(&s.empty[ring.stage], lane);
+                ring.next();
+            }
+            const int64_t par = (int64_t(1) << (lev - 1)) + st * (cnt / 2) + pi;
+            if (acc.reduce(k, nv, s.red)) {
+                const int pslot = (1 << (rel - 1)) + int(pi);
+                acc.store(s.sub + pslot * wstride, kx, nv, k);
+                acc.store(vec.xh + par * kx * vs, kx, nv, k);
+            }
+            if constexpr (NVMAX >= kWideMin)
+                if (vec.xb) acc.store_tile(vec.xb + par * vec_tile_bytes(vec.np), vec.np, nv, k);
+            h2p::consumer_sync(kConsumers);
+        }
+    }
+    return true;
+}
+
 template <typename T, int NVMAX>
 __global__ void __launch_bounds__(kThreads)
     k_up_sub(Op<T> op, Vec<T> vec, Pipe pp, int Lr, int L, int64_t nsub, int leaf_input)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int sub_nodes = 2 << L;
-    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, sub_nodes, op.kx, false);
+    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, 2 << L, op.kx, false);
     init_pipe(s, pp);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
-    const int Lin = Lr + L;
-    const uint32_t es = sizeof(T);
     Ring ring(pp.ns);
-
     if (warp == 4) {  // producer: fixed-size tiles, so no per-leaf metadata is needed
         if (lane == 0) {
             bool ok = true;
-            for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x) {
-                if (leaf_input) {
-                    const int64_t leaf0 = st << L;
-                    for (int j = 0; ok && j < (1 << L); ++j) {
-                        const int64_t leaf = leaf0 + j;
-                        ok = produce(s, pp, ring, op.U + leaf * mp * kx, mp * kx * es, vec.xt + leaf * mp * vs,
-                                     mp * nv * es, nullptr, 0, nullptr, vec.err);
-                    }
-                }
-                for (int lev = Lin; ok && lev > Lr; --lev) {
-                    const int64_t cnt = int64_t(1) << (lev - Lr);
-                    const int64_t c0 = (int64_t(1) << lev) + st * cnt;
-                    // an input level from an earlier launch travels with its transfer tiles
-                    const bool with_x = !leaf_input && lev == Lin;
-                    for (int64_t c = c0; ok && c < c0 + cnt; ++c)
-                        ok = produce(s, pp, ring, op.E + c * k * kx, k * kx * es, with_x ? vec.xh + c * kx * vs : nullptr,
-                                     with_x ? kx * nv * es : 0, nullptr, 0, nullptr, vec.err);
-                }
+            for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x)
+                ok = up_sub_produce<T, NVMAX>(op, vec, s, pp, ring, Lr, L, st, leaf_input);
+            drain_on_abort(s, ring);
+        }
+        return;
+    }
+    AccOf<T, NVMAX> acc;
+    acc.setup(op.k, op.kx, threadIdx.x);
+    for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x)
+        if (!up_sub_consume<T, NVMAX>(op, vec, s, pp, ring, acc, Lr, L, st, leaf_input)) return;
+}
+
+// A sweep step of one operator inside a merged launch: its subtrees are the global work
+// items first .. first + nsub - 1.
+template <typename T>
+struct SweepTask {
+    Op<T> op;
+    Vec<T> vec;
+    int Lr, L, flag;  // flag: leaf input (upsweep) or leaf output (downsweep)
+    int64_t first, nsub;
+};
+
+// The task holding global item g (tasks ordered by first, every nsub >= 1).
+template <typename T>
+__device__ inline int sweep_task_of(const SweepTask<T> *__restrict__ tasks, int ntasks, int64_t g)
+{
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (tasks[mid].first <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Merged upsweep step: every task's subtrees in one persistent launch. Shared memory is
+// carved for the largest subtree buffer of the tasks (sub_kx = the most subtree slots x kx
+// over the tasks) and the pipe's slots for the largest tiles.
+template <typename T, int NVMAX>
+__global__ void __launch_bounds__(kThreads)
+    k_up_batch(const SweepTask<T> *__restrict__ tasks, int ntasks, int64_t total, Pipe pp, int sub_kx)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, 1, sub_kx, false);
+    init_pipe(s, pp);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    Ring ring(pp.ns);
+    if (warp == 4) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int64_t g = blockIdx.x; ok && g < total; g += gridDim.x) {
+                const SweepTask<T> &t = tasks[sweep_task_of(tasks, ntasks, g)];
+                ok = up_sub_produce<T, NVMAX>(t.op, t.vec, s, pp, ring, t.Lr, t.L, g - t.first, t.flag);
             }
             drain_on_abort(s, ring);
         }
         return;
     }
-
-    const int tid = threadIdx.x;
     AccOf<T, NVMAX> acc;
-    acc.setup(k, kx, tid);
-    const int wstride = kx * NVMAX;
-    for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x) {
-        if (leaf_input) {
-            // leaf projections into local slots 2^L + j
-            const int64_t leaf0 = st << L;
-            for (int j = 0; j < (1 << L); ++j) {
-                const int64_t leaf = leaf0 + j;
-                const int R = op.leaf_lo[leaf + 1] - op.leaf_lo[leaf];
-                acc.zero();
-                if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
-                acc.gemv(stage_tile(s, pp, ring.stage), kx, k, R, stage_x(s, pp, ring.stage), mp, nv);
-                release(&s.empty[ring.stage], lane);
-                ring.next();
-                if (acc.reduce(k, nv, s.red)) {
-                    acc.store(s.sub + ((1 << L) + j) * wstride, kx, nv, k);
-                    acc.store(vec.xh + (op.first_leaf + leaf) * kx * vs, kx, nv, k);
-                }
-                if constexpr (NVMAX >= kWideMin)
-                    if (vec.xb) acc.store_tile(vec.xb + (op.first_leaf + leaf) * vec_tile_bytes(vec.np), vec.np, nv, k);
-                h2p::consumer_sync(kConsumers);
-            }
-        }
-        // transfers, level by level (the input level of a launch without leaf input arrives in
-        // the stages, next to its transfer tiles)
-        for (int lev = Lin; lev > Lr; --lev) {
-            const int rel = lev - Lr;
-            const int64_t cnt = int64_t(1) << rel;
-            const bool staged_x = !leaf_input && lev == Lin;
-            for (int64_t pi = 0; pi < cnt / 2; ++pi) {
-                acc.zero();
-                for (int c = 0; c < 2; ++c) {
-                    const int child_slot = (1 << rel) + int(2 * pi + c);
-                    if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
-                    const T *xc = staged_x ? stage_x(s, pp, ring.stage) : s.sub + child_slot * wstride;
-                    acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, xc, kx, nv);
-                    release(&s.empty[ring.stage], lane);
-                    ring.next();
-                }
-                const int64_t par = (int64_t(1) << (lev - 1)) + st * (cnt / 2) + pi;
-                if (acc.reduce(k, nv, s.red)) {
-                    const int pslot = (1 << (rel - 1)) + int(pi);
-                    acc.store(s.sub + pslot * wstride, kx, nv, k);
-                    acc.store(vec.xh + par * kx * vs, kx, nv, k);
-                }
-                if constexpr (NVMAX >= kWideMin)
-                    if (vec.xb) acc.store_tile(vec.xb + par * vec_tile_bytes(vec.np), vec.np, nv, k);
-                h2p::consumer_sync(kConsumers);
-            }
-        }
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const SweepTask<T> &t = tasks[sweep_task_of(tasks, ntasks, g)];
+        acc.setup(t.op.k, t.op.kx, threadIdx.x);
+        if (!up_sub_consume<T, NVMAX>(t.op, t.vec, s, pp, ring, acc, t.Lr, t.L, g - t.first, t.flag)) return;
     }
 }
 
@@ -1097,119 +1174,164 @@ __global__ void __launch_bounds__(CONS + 32, 1)
 // rows were written as zeros) and the parent total of a root at level Lr >= 1 comes from
 // an earlier launch. With leaf output (Lr+L = q) it finishes with the leaf expansion
 // y_t = U_t yhat^q_t, the dense partial result and Y[perm] = alpha y + beta Y; otherwise it
-// writes the totals of level Lr+L over their coupling rows, for the next launch.
+// writes the totals of level Lr+L over their coupling rows, for the next launch. As for the
+// upsweep, one subtree's producer and consumer parts serve k_down_sub (one operator) and
+// k_down_batch (a merged list).
+//
+// Each node's own coupling vector travels with its transfer tile in the second half of the
+// stage's vector slot; the root's parent total in the first half.
 template <typename T, int NVMAX>
-__global__ void __launch_bounds__(kThreads)
-    k_down_sub(Op<T> op, Vec<T> vec, Pipe pp, int Lr, int L, int64_t nsub, int leaf_output)
+__device__ bool down_sub_produce(const Op<T> &op, const Vec<T> &vec, Smem<T> &s, const Pipe &pp, Ring &ring,
+                                 int Lr, int L, int64_t st, int leaf_output)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int sub_nodes = 2 << L;
-    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, sub_nodes, op.kx, false);
-    init_pipe(s, pp);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
     const int Lo = Lr + L;
     const uint32_t es = sizeof(T);
     const uint32_t vb = kx * nv * es;  // bytes of one node's coefficient vector
-    Ring ring(pp.ns);
-
-    // each node's own coupling vector travels with its transfer tile in the second half of
-    // the stage's vector slot; the root's parent total in the first half
-    if (warp == 4) {
-        if (lane == 0) {
-            bool ok = true;
-            for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x) {
-                const int64_t r = (int64_t(1) << Lr) + st;
-                if (Lr >= 1)
-                    ok = produce(s, pp, ring, op.Et + r * k * kx, k * kx * es, vec.yh + (r / 2) * kx * vs, vb,
-                                 vec.yh + r * kx * vs, vb, nullptr, vec.err);
-                else
-                    ok = produce(s, pp, ring, nullptr, 0, nullptr, 0, vec.yh + r * kx * vs, vb, nullptr, vec.err);
-                for (int lev = Lr + 1; ok && lev <= Lo; ++lev) {
-                    const int64_t cnt = int64_t(1) << (lev - Lr);
-                    const int64_t c0 = (int64_t(1) << lev) + st * cnt;
-                    for (int64_t c = c0; ok && c < c0 + cnt; ++c)
-                        ok = produce(s, pp, ring, op.Et + c * k * kx, k * kx * es, nullptr, 0, vec.yh + c * kx * vs,
-                                     vb, nullptr, vec.err);
-                }
-                if (leaf_output) {
-                    const int64_t leaf0 = st << L;
-                    for (int j = 0; ok && j < (1 << L); ++j) {
-                        const int64_t leaf = leaf0 + j;
-                        ok = produce(s, pp, ring, op.Ut + leaf * kx * mp, k * mp * es, vec.yd + leaf * mp * vs,
-                                     mp * nv * es, nullptr, 0, nullptr, vec.err);
-                    }
-                }
-            }
-            drain_on_abort(s, ring);
-        }
-        return;
+    bool ok = true;
+    const int64_t r = (int64_t(1) << Lr) + st;
+    if (Lr >= 1)
+        ok = produce(s, pp, ring, op.Et + r * k * kx, k * kx * es, vec.yh + (r / 2) * kx * vs, vb,
+                     vec.yh + r * kx * vs, vb, nullptr, vec.err);
+    else
+        ok = produce(s, pp, ring, nullptr, 0, nullptr, 0, vec.yh + r * kx * vs, vb, nullptr, vec.err);
+    for (int lev = Lr + 1; ok && lev <= Lo; ++lev) {
+        const int64_t cnt = int64_t(1) << (lev - Lr);
+        const int64_t c0 = (int64_t(1) << lev) + st * cnt;
+        for (int64_t c = c0; ok && c < c0 + cnt; ++c)
+            ok = produce(s, pp, ring, op.Et + c * k * kx, k * kx * es, nullptr, 0, vec.yh + c * kx * vs, vb, nullptr,
+                         vec.err);
     }
-
-    const int tid = threadIdx.x;
-    const int wstride = kx * NVMAX;
-    AccOf<T, NVMAX> acc;
-    for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x) {
-        // subtree root: E_r yhat_parent + own
-        acc.setup(k, kx, tid);
-        acc.zero();
-        if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
-        if (Lr >= 1) acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, stage_x(s, pp, ring.stage), kx, nv);
-        if (acc.reduce(k, nv, s.red)) {
-            acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
-            acc.store(s.sub + 1 * wstride, kx, nv, k);
-            if (L == 0 && !leaf_output) acc.store(vec.yh + ((int64_t(1) << Lr) + st) * kx * vs, kx, nv, k);
-        }
-        release(&s.empty[ring.stage], lane);
-        ring.next();
-        h2p::consumer_sync(kConsumers);
-        for (int lev = Lr + 1; lev <= Lo; ++lev) {
-            const int rel = lev - Lr;
-            const int64_t cnt = int64_t(1) << rel;
-            for (int64_t ci = 0; ci < cnt; ++ci) {
-                const int slot = (1 << rel) + int(ci);
-                acc.zero();
-                if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
-                acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, s.sub + (slot / 2) * wstride, kx, nv);
-                if (acc.reduce(k, nv, s.red)) {
-                    acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
-                    acc.store(s.sub + slot * wstride, kx, nv, k);
-                    if (lev == Lo && !leaf_output)
-                        acc.store(vec.yh + ((int64_t(1) << lev) + st * cnt + ci) * kx * vs, kx, nv, k);
-                }
-                release(&s.empty[ring.stage], lane);
-                ring.next();
-                h2p::consumer_sync(kConsumers);
-            }
-        }
-        if (!leaf_output) continue;
-        // leaves: y = U_t yhat_t + yd_t; Y[perm] = alpha y + beta Y
+    if (leaf_output) {
         const int64_t leaf0 = st << L;
-        for (int j = 0; j < (1 << L); ++j) {
+        for (int j = 0; ok && j < (1 << L); ++j) {
             const int64_t leaf = leaf0 + j;
-            const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
-            acc.setup(R, mp, tid);
+            ok = produce(s, pp, ring, op.Ut + leaf * kx * mp, k * mp * es, vec.yd + leaf * mp * vs, mp * nv * es,
+                         nullptr, 0, nullptr, vec.err);
+        }
+    }
+    return ok;
+}
+
+template <typename T, int NVMAX>
+__device__ bool down_sub_consume(const Op<T> &op, const Vec<T> &vec, Smem<T> &s, const Pipe &pp, Ring &ring,
+                                 AccOf<T, NVMAX> &acc, int Lr, int L, int64_t st, int leaf_output)
+{
+    const int lane = threadIdx.x % 32, tid = threadIdx.x;
+    const int k = op.k, kx = op.kx, mp = op.mp, nv = vec.nv, vs = vec.vs;
+    const int Lo = Lr + L;
+    const int wstride = kx * NVMAX;
+    // subtree root: E_r yhat_parent + own
+    acc.setup(k, kx, tid);
+    acc.zero();
+    if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return false;
+    if (Lr >= 1) acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, stage_x(s, pp, ring.stage), kx, nv);
+    if (acc.reduce(k, nv, s.red)) {
+        acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
+        acc.store(s.sub + 1 * wstride, kx, nv, k);
+        if (L == 0 && !leaf_output) acc.store(vec.yh + ((int64_t(1) << Lr) + st) * kx * vs, kx, nv, k);
+    }
+    release(&s.empty[ring.stage], lane);
+    ring.next();
+    h2p::consumer_sync(kConsumers);
+    for (int lev = Lr + 1; lev <= Lo; ++lev) {
+        const int rel = lev - Lr;
+        const int64_t cnt = int64_t(1) << rel;
+        for (int64_t ci = 0; ci < cnt; ++ci) {
+            const int slot = (1 << rel) + int(ci);
             acc.zero();
-            acc.fetch_rows(op.perm, r0, R);  // output rows, fetched while the tile is in flight
-            if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return;
-            acc.gemv(stage_tile(s, pp, ring.stage), mp, R, k, s.sub + ((1 << L) + j) * wstride, kx, nv);
-            if (acc.reduce(R, nv, s.red)) {
-                acc.add(stage_x(s, pp, ring.stage), mp, nv, R);
-                // narrow passes write Y directly (a runtime choice here slowed the nv = 1 leaf
-                // epilogue measurably); wide passes may stage rows for k_rows_out
-                if constexpr (NVMAX >= kWideMin) {
-                    if (vec.yr)
-                        acc.write_rows(vec.yr, vec.ldr, nv, R);
-                    else
-                        acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
-                } else {
-                    acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
-                }
+            if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return false;
+            acc.gemv(stage_tile(s, pp, ring.stage), kx, k, k, s.sub + (slot / 2) * wstride, kx, nv);
+            if (acc.reduce(k, nv, s.red)) {
+                acc.add(stage_x(s, pp, ring.stage, 1), kx, nv, k);
+                acc.store(s.sub + slot * wstride, kx, nv, k);
+                if (lev == Lo && !leaf_output)
+                    acc.store(vec.yh + ((int64_t(1) << lev) + st * cnt + ci) * kx * vs, kx, nv, k);
             }
             release(&s.empty[ring.stage], lane);
             ring.next();
             h2p::consumer_sync(kConsumers);
         }
+    }
+    if (!leaf_output) return true;
+    // leaves: y = U_t yhat_t + yd_t; Y[perm] = alpha y + beta Y
+    const int64_t leaf0 = st << L;
+    for (int j = 0; j < (1 << L); ++j) {
+        const int64_t leaf = leaf0 + j;
+        const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
+        acc.setup(R, mp, tid);
+        acc.zero();
+        acc.fetch_rows(op.perm, r0, R);  // output rows, fetched while the tile is in flight
+        if (!h2p::mbar_wait(&s.full[ring.stage], ring.phase, s.abort_flag, vec.err)) return false;
+        acc.gemv(stage_tile(s, pp, ring.stage), mp, R, k, s.sub + ((1 << L) + j) * wstride, kx, nv);
+        if (acc.reduce(R, nv, s.red)) {
+            acc.add(stage_x(s, pp, ring.stage), mp, nv, R);
+            // narrow passes write Y directly (a runtime choice here slowed the nv = 1 leaf
+            // epilogue measurably); wide passes may stage rows for k_rows_out
+            if constexpr (NVMAX >= kWideMin) {
+                if (vec.yr)
+                    acc.write_rows(vec.yr, vec.ldr, nv, R);
+                else
+                    acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
+            } else {
+                acc.write_out(vec.Y, op.n, vec.alpha, vec.beta, nv, R);
+            }
+        }
+        release(&s.empty[ring.stage], lane);
+        ring.next();
+        h2p::consumer_sync(kConsumers);
+    }
+    return true;
+}
+
+template <typename T, int NVMAX>
+__global__ void __launch_bounds__(kThreads)
+    k_down_sub(Op<T> op, Vec<T> vec, Pipe pp, int Lr, int L, int64_t nsub, int leaf_output)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, 2 << L, op.kx, false);
+    init_pipe(s, pp);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    Ring ring(pp.ns);
+    if (warp == 4) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int64_t st = blockIdx.x; ok && st < nsub; st += gridDim.x)
+                ok = down_sub_produce<T, NVMAX>(op, vec, s, pp, ring, Lr, L, st, leaf_output);
+            drain_on_abort(s, ring);
+        }
+        return;
+    }
+    AccOf<T, NVMAX> acc;
+    for (int64_t st = blockIdx.x; st < nsub; st += gridDim.x)
+        if (!down_sub_consume<T, NVMAX>(op, vec, s, pp, ring, acc, Lr, L, st, leaf_output)) return;
+}
+
+// Merged downsweep step over the tasks' subtrees (see k_up_batch).
+template <typename T, int NVMAX>
+__global__ void __launch_bounds__(kThreads)
+    k_down_batch(const SweepTask<T> *__restrict__ tasks, int ntasks, int64_t total, Pipe pp, int sub_kx)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<T> s = carve<T, NVMAX>(smem_raw, pp, 1, sub_kx, false);
+    init_pipe(s, pp);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    Ring ring(pp.ns);
+    if (warp == 4) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int64_t g = blockIdx.x; ok && g < total; g += gridDim.x) {
+                const SweepTask<T> &t = tasks[sweep_task_of(tasks, ntasks, g)];
+                ok = down_sub_produce<T, NVMAX>(t.op, t.vec, s, pp, ring, t.Lr, t.L, g - t.first, t.flag);
+            }
+            drain_on_abort(s, ring);
+        }
+        return;
+    }
+    AccOf<T, NVMAX> acc;
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        const SweepTask<T> &t = tasks[sweep_task_of(tasks, ntasks, g)];
+        if (!down_sub_consume<T, NVMAX>(t.op, t.vec, s, pp, ring, acc, t.Lr, t.L, g - t.first, t.flag)) return;
     }
 }
 

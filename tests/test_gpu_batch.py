@@ -68,7 +68,13 @@ def test_batch_matches_oracle_and_single_products(members, prec):
             got = to_host(Y)
             assert np.all(np.isfinite(got)), m.name
             assert relerr(got, ref) <= TOL[prec], m.name
-            single = to_host(op.matvec(to_dev(X, prec)))
+            # the batch streams FP32 blocks on the CUDA cores: compare with the single product
+            # on the same path (FP32 passes of more than 8 vectors otherwise take 3xTF32)
+            h2.h2_set_fp32_tensor(op.handle, False)
+            try:
+                single = to_host(op.matvec(to_dev(X, prec)))
+            finally:
+                h2.h2_set_fp32_tensor(op.handle, True)
             assert relerr(got, single) <= (1e-14 if prec == "fp64" else 1e-6), m.name
         first = [to_host(Y).copy() for Y in Ys]
         b.run()
@@ -153,3 +159,33 @@ def test_batch_rejects_what_it_cannot_run(members):
     Xw = to_dev(si.gaussian_vectors(op1.n, 40, 1), "fp32")
     with pytest.raises(h2.H2Error):  # more than one pass of vectors
         h2.H2Batch([op1], [Xw], [op1.new_vectors(40)])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_merged_sweeps_equal_member_sweeps(members, prec):
+    """The merged sweep launches (one per step and width over a table of the members'
+    subtrees) run each member's subtrees with the same arithmetic as its own launches: the
+    batched results are bitwise equal, and a replay takes a few launches per width."""
+    ops, Xs, Ys_a, Ys_b = [], [], [], []
+    for m, orc, op in members:
+        op.upload(prec)
+        ops.append(op)
+        Xs.append(to_dev(m.make_x(), prec))
+        Ys_a.append(op.new_vectors(m.nv, fill=float("nan")))
+        Ys_b.append(op.new_vectors(m.nv, fill=float("nan")))
+    merged = h2.H2Batch(ops, Xs, Ys_a)
+    own = h2.H2Batch(ops, Xs, Ys_b, member_sweeps=True)
+    try:
+        desc = merged.describe()
+        assert "members with their own sweeps 0" in desc, desc
+        assert "sweeps width" in desc and "sweeps width" not in own.describe()
+        merged.run()
+        own.run()
+        torch.cuda.synchronize()
+        merged.check()
+        own.check()
+        for (m, _, _), ya, yb in zip(members, Ys_a, Ys_b):
+            assert np.array_equal(to_host(ya), to_host(yb)), m.name
+    finally:
+        merged.close()
+        own.close()
