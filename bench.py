@@ -590,14 +590,22 @@ def compress_benchmark(h2, torch, steps=3, sets=("2d", "3d"), grid2d=1024, dfma_
             for _ in range(3):
                 o.matvec(X32, Y32)
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            h2.h2_get_timing(o.handle)
+            h2.h2_set_timing(o.handle, True)
             for a, b in evs:
                 flush.zero_()
                 a.record()
                 o.matvec(X32, Y32)
                 b.record()
             torch.cuda.synchronize()
+            h2.h2_set_timing(o.handle, False)
+            phase_ms, _, nprod = h2.h2_get_timing(o.handle)
             prod[name] = float(np.mean([a.elapsed_time(b) for a, b in evs]))
-            prod[name + "_device_GB"] = h2.h2_get_info(o.handle).device_bytes / 1e9
+            oinfo = h2.h2_get_info(o.handle)
+            prod[name + "_device_GB"] = oinfo.device_bytes / 1e9
+            mat, vec = entry_counts(oinfo, 1)
+            prod[name + "_GB/s"] = 4 * (mat + vec) / (prod[name] * 1e-3) / 1e9
+            prod[name + "_phases_ms"] = dict(zip(h2.PHASES, [float(v) / max(nprod, 1) for v in phase_ms]))
         prod["speedup"] = prod["uncompressed"] / prod["compressed"]
         del flush
         total_ms = float(ms.sum())

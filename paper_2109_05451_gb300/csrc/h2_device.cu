@@ -77,6 +77,15 @@ struct h2_device {
     unsigned char *vals = nullptr;  // coupling blocks, then dense blocks
     h2s::StreamDesc *desc_bottom = nullptr, *desc_top = nullptr;
     int64_t *chunks_bottom = nullptr, *chunks_top = nullptr;  // (first << 16) | count
+    // when dense tiles are at least twice the coupling tiles (small ranks, e.g. after
+    // recompression), the bottom list's dense rows get a stream of their own: each stream's
+    // stages are sized for its own tiles, so small coupling tiles get a deep pipeline.
+    // chunks_bottom then covers the coupling rows, chunks_dense the dense rows (descriptor
+    // indices into the same desc_bottom array); otherwise n_chunks_dense = 0
+    int64_t *chunks_dense = nullptr;
+    int64_t n_chunks_dense = 0;
+    int grid_dense = 0;
+    uint32_t tile_cpl = 0, tile_dns = 0;  // bytes of the largest coupling / dense tile
     int grid_bottom = 0, grid_top = 0;
     int64_t n_chunks_bottom = 0, n_chunks_top = 0;
     int64_t n_desc_bottom = 0, n_desc_top = 0;
@@ -375,13 +384,24 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     // (16 consumer warps) share each SM, leaving room for the side stream's kernels
     const bool mf = dv.mf && sizeof(T) == 4;
     const uint32_t x_mf = mf_seg_bytes(kx, mp, NVMAX) + 2 * mf_coord_bytes(k, mp);
-    const Pipe p_bot = mf ? make_pipe<T, NVMAX>(0, x_mf, 0, kx, true, 36 * 1024, 12)
-                          : make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
+    // With a separate dense stream each stream's stages fit its own tiles. A stream CTA's
+    // single producer thread starts about one block per 700 clocks, which is HBM speed for
+    // 16 KB tiles but not for small ones: small coupling tiles run 2 or 4 CTAs per SM (each
+    // with its own producer) within the same 160 KB.
+    const bool dsplit = dv.n_chunks_dense > 0;
+    const int cpl_per_sm = !dsplit ? 1 : dv.tile_cpl <= 4096 ? 4 : dv.tile_cpl <= 8192 ? 2 : 1;
+    const Pipe p_bot = mf       ? make_pipe<T, NVMAX>(0, x_mf, 0, kx, true, 36 * 1024, 12)
+                       : dsplit ? make_pipe<T, NVMAX>(dv.tile_cpl, uint32_t(kx * NVMAX * es), 0, kx, true,
+                                                      160 * 1024 / size_t(cpl_per_sm), 32)
+                                : make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
+    const Pipe p_dns = make_pipe<T, NVMAX>(dv.tile_dns, uint32_t(mp * NVMAX * es), 0, kx, true, 160 * 1024, 32);
+    const size_t sm_dns = smem_bytes<T, NVMAX>(p_dns, 0, kx, true);
     // (the upper levels' coupling blocks are stored for the matrix-free precision too)
     const Pipe p_top = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
     const size_t sm_bot = smem_bytes<T, NVMAX>(p_bot, 0, kx, true), sm_top = smem_bytes<T, NVMAX>(p_top, 0, kx, true);
-    const unsigned grid_bot = mf ? unsigned(std::max<int64_t>(1, std::min<int64_t>(4 * int64_t(dv.num_sms), dv.n_chunks_bottom)))
-                                 : unsigned(dv.grid_bottom);
+    const unsigned grid_bot =
+        mf ? unsigned(std::max<int64_t>(1, std::min<int64_t>(4 * int64_t(dv.num_sms), dv.n_chunks_bottom)))
+           : unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(cpl_per_sm) * dv.num_sms, dv.n_chunks_bottom)));
     set_kernel_attributes<T, NVMAX>();
     const int grid_bsub = int(std::min<int64_t>(nsub, int64_t(dv.num_sms) * 2));
 
@@ -440,7 +460,13 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
                                                                     dv.n_chunks_bottom, 0);
         }
     }
-    dv.end(1, ev, st, dv.n_chunks_bottom > 0 ? 1 : 0);
+    if (dsplit) {  // the dense rows, after the coupling rows on the same stream
+        h2n::Range r("dense product");
+        constexpr int C = (sizeof(T) == 4 && NVMAX <= kChunk) ? kConsumers : stream_consumers<T, NVMAX>();
+        k_stream<T, NVMAX, C><<<dv.grid_dense, C + 32, sm_dns, st>>>(o, v, p_dns, dv.desc_bottom, dv.chunks_dense,
+                                                                     dv.n_chunks_dense, 2);
+    }
+    dv.end(1, ev, st, (dv.n_chunks_bottom > 0 ? 1 : 0) + (dsplit ? 1 : 0));
     // ---- stream B, part 2: coupling rows of the upper levels, their downsweep
     if (top) {
         cudaStream_t sb = side;
@@ -621,6 +647,13 @@ int launch_wide(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double
                                                             dv.n_chunks_bottom, 0);
         ++ls;
     }
+    if (dv.n_chunks_dense > 0) {  // dense rows in a list of their own (small coupling tiles)
+        const unsigned g_dns =
+            unsigned(std::max<int64_t>(1, std::min<int64_t>(int64_t(dv.num_sms) * per_sm, dv.n_chunks_dense)));
+        k_stream<T, NVMAX><<<g_dns, kThreads, sm_str, st>>>(o, v, p_str, dv.desc_bottom, dv.chunks_dense,
+                                                            dv.n_chunks_dense, 2);
+        ++ls;
+    }
     if (dv.n_chunks_top > 0) {
         k_stream<T, NVMAX><<<g_top, kThreads, sm_str, st>>>(o, v, p_str, dv.desc_top, dv.chunks_top,
                                                          dv.n_chunks_top, 1);
@@ -777,9 +810,12 @@ int launch_tf32_pass(const h2_op &op, h2_device &dv, const float *X, float *Y, i
     ev = dv.begin(st);
     int rc = launch_tf32_stream<NVMAX>(dv, w, npass, dv.desc_bottom, dv.chunks_bottom, dv.n_chunks_bottom,
                                        w.tickets + 0, st);
+    if (rc == H2_OK && dv.n_chunks_dense > 0)
+        rc = launch_tf32_stream<NVMAX>(dv, w, npass, dv.desc_bottom, dv.chunks_dense, dv.n_chunks_dense,
+                                       w.tickets + 2, st);
     if (rc == H2_OK)
         rc = launch_tf32_stream<NVMAX>(dv, w, npass, dv.desc_top, dv.chunks_top, dv.n_chunks_top, w.tickets + 1, st);
-    dv.end(1, ev, st, int(dv.n_chunks_bottom > 0) + int(dv.n_chunks_top > 0));
+    dv.end(1, ev, st, int(dv.n_chunks_bottom > 0) + int(dv.n_chunks_top > 0) + int(dv.n_chunks_dense > 0));
     if (rc != H2_OK) return rc;
     ev = dv.begin(st);
     const int ld = down_all(op, dv, o, v, sp, st);
@@ -1836,11 +1872,32 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
             bb.push_back(dv->tc ? tcb : uint64_t(d.ld) * d.cols * es);
         }
     }
-    std::vector<int64_t> pb, pt;
-    if (!make_chunks(db, bb, 512 * 1024, pb) || !make_chunks(dt, bt, 128 * 1024, pt)) {
+    std::vector<int64_t> pb, pt, pd;
+    dv->tile_cpl = uint32_t((uint64_t(k) * round4(k) * es + 15) / 16 * 16);
+    dv->tile_dns = uint32_t((uint64_t(round4(dv->max_leaf_rows)) * dv->max_leaf_rows * es + 15) / 16 * 16);
+    const bool split = !dv->tc && !dv->mf && ndns > 0 && dv->tile_dns >= 2 * dv->tile_cpl;
+    if (split) {
+        // db holds the coupling rows, then the dense rows: chunk the two parts separately
+        size_t nc = 0;
+        while (nc < db.size() && !(db[nc].flags & h2s::kDense)) ++nc;
+        const std::vector<h2s::StreamDesc> dc(db.begin(), db.begin() + nc), dd(db.begin() + nc, db.end());
+        const std::vector<uint64_t> bc(bb.begin(), bb.begin() + nc), bd(bb.begin() + nc, bb.end());
+        // small tiles: smaller scheduling chunks, for the several CTAs per SM of their stream
+        if (!make_chunks(dc, bc, 128 * 1024, pb) || !make_chunks(dd, bd, 512 * 1024, pd)) {
+            h2_device_free(&op);
+            return H2_EINVAL;
+        }
+        for (auto &c : pd) c += int64_t(nc) << 16;  // descriptor indices of the whole array
+    } else if (!make_chunks(db, bb, 512 * 1024, pb)) {
         h2_device_free(&op);
         return H2_EINVAL;  // a block row longer than one scheduling chunk
     }
+    if (!make_chunks(dt, bt, 128 * 1024, pt)) {
+        h2_device_free(&op);
+        return H2_EINVAL;
+    }
+    dv->n_chunks_dense = int64_t(pd.size());
+    dv->grid_dense = int(std::max<int64_t>(1, std::min<int64_t>(dv->num_sms, dv->n_chunks_dense)));
     dv->n_chunks_bottom = int64_t(pb.size());
     dv->n_chunks_top = int64_t(pt.size());
     dv->n_desc_bottom = int64_t(db.size());
@@ -1862,7 +1919,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     const size_t o_npts = dv->mf ? take(size_t(op.nnodes + 1) * k * sizeof(float4)) : 0;
     const size_t o_lpts = dv->mf ? take(size_t(nleaves) * mp * sizeof(float4)) : 0;
     const size_t o_db = take(db.size() * sizeof(h2s::StreamDesc)), o_dt = take(dt.size() * sizeof(h2s::StreamDesc));
-    const size_t o_pb = take(pb.size() * 8), o_pt = take(pt.size() * 8), o_err = take(16);
+    const size_t o_pb = take(pb.size() * 8), o_pt = take(pt.size() * 8), o_pd = take(pd.size() * 8), o_err = take(16);
     const size_t persistent = off;
     // temporaries for generation
     const size_t t_cheb = align_up(op.cheb.size() * 8), t_pts = align_up(size_t(op.n) * op.dim * 8);
@@ -1895,6 +1952,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     dv->desc_top = reinterpret_cast<h2s::StreamDesc *>(arena + o_dt);
     dv->chunks_bottom = reinterpret_cast<int64_t *>(arena + o_pb);
     dv->chunks_top = reinterpret_cast<int64_t *>(arena + o_pt);
+    dv->chunks_dense = reinterpret_cast<int64_t *>(arena + o_pd);
     dv->err = reinterpret_cast<int *>(arena + o_err);
     if (dv->mf) {
         dv->mfa.node_pts = reinterpret_cast<const float4 *>(arena + o_npts);
@@ -1963,6 +2021,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     cp(dv->desc_top, dt.data(), dt.size() * sizeof(h2s::StreamDesc));
     cp(dv->chunks_bottom, pb.data(), pb.size() * 8);
     cp(dv->chunks_top, pt.data(), pt.size() * 8);
+    if (!pd.empty()) cp(dv->chunks_dense, pd.data(), pd.size() * 8);
     cp(d_cheb, op.cheb.data(), op.cheb.size() * 8);
     cp(d_pts, pts_tree.data(), pts_tree.size() * 8);
     cp(d_crow, cpl_row.data(), ncpl * 4);
