@@ -1892,7 +1892,10 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
         h2_device_free(&op);
         return H2_EINVAL;  // a block row longer than one scheduling chunk
     }
-    if (!make_chunks(dt, bt, 128 * 1024, pt)) {
+    // the upper levels' rows: about eight coupling tiles per chunk (at least 8 KB), so that
+    // small tiles spread over as many CTAs as large ones
+    const uint64_t top_target = std::max<uint64_t>(8 * 1024, std::min<uint64_t>(128 * 1024, 8 * uint64_t(dv->tile_cpl)));
+    if (!make_chunks(dt, bt, top_target, pt)) {
         h2_device_free(&op);
         return H2_EINVAL;
     }
