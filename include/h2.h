@@ -364,6 +364,20 @@ size_t h2_server_request_bytes(h2_handle h);
  * H2_ESTATE (operator not uploaded), H2_ENOMEM (the request can never fit the slot memory). */
 int h2_server_submit(h2_server_t s, h2_handle op, double sigma2, const double *b, double *x, double tol, int maxit,
                      int64_t *request_id);
+/* A solve by mixed-precision iterative refinement: products in op's precision (FP32 or
+ * split-BF16) inside, FP64 residuals outside. op64 is an FP64 device copy of the same
+ * operator (another handle of the same build, e.g. h2_load of its h2_save, uploaded in
+ * H2_FP64). From x = 0: an inner CG on (A_op + sigma2 I) d = r to the relative tolerance
+ * inner_tol (0 < inner_tol < 1), then x += d and r = b - (A_op64 + sigma2 I) x in FP64, until
+ * |r| / |b| < tol or maxit inner iterations in all. An FP32 product's error (about 1e-7 of
+ * |A| |x|) bounds what plain CG on op can reach; the refinement's bound is op64's. Result:
+ * iters = inner iterations in all, true_relres = the last FP64 residual, status H2_OK when it
+ * is below tol. Errors as h2_server_submit; H2_ESTATE if op64 is not uploaded in FP64. */
+int h2_server_submit_refined(h2_server_t s, h2_handle op, h2_handle op64, double sigma2, const double *b, double *x,
+                             double tol, double inner_tol, int maxit, int64_t *request_id);
+/* Device bytes one refined request occupies (0 unless op is uploaded and op64 is an FP64
+ * copy with the same n). */
+size_t h2_server_request_bytes_refined(h2_handle op, h2_handle op64);
 /* Move up to max_results completed requests into results (host array) and set *n_results;
  * never blocks. */
 int h2_server_poll(h2_server_t s, h2_request_result *results, int max_results, int *n_results);

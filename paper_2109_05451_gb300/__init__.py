@@ -93,6 +93,8 @@ SIGNATURES = {
     "h2_server_create": (_I, [_SZ, _I, _I64, C.POINTER(_P)]),
     "h2_server_request_bytes": (_SZ, [_P]),
     "h2_server_submit": (_I, [_P, _P, _D, _P, _P, _D, _I, C.POINTER(_I64)]),
+    "h2_server_submit_refined": (_I, [_P, _P, _P, _D, _P, _P, _D, _D, _I, C.POINTER(_I64)]),
+    "h2_server_request_bytes_refined": (_SZ, [_P, _P]),
     "h2_server_poll": (_I, [_P, C.POINTER(h2_request_result), _I, C.POINTER(_I)]),
     "h2_server_wait": (_I, [_P, _D]),
     "h2_server_cancel": (_I, [_P, _I64]),
@@ -406,14 +408,26 @@ class H2Server:
     def request_bytes(op: "H2Operator") -> int:
         return int(load().h2_server_request_bytes(op.handle))
 
-    def submit(self, op: "H2Operator", b: np.ndarray, tol: float, maxit: int, sigma2: float = 0.0) -> int:
+    @staticmethod
+    def request_bytes_refined(op: "H2Operator", op64: "H2Operator") -> int:
+        return int(load().h2_server_request_bytes_refined(op.handle, op64.handle))
+
+    def submit(self, op: "H2Operator", b: np.ndarray, tol: float, maxit: int, sigma2: float = 0.0,
+               op64: "H2Operator" = None, inner_tol: float = 1e-3) -> int:
+        """Queue a CG solve; with op64 (an FP64 upload of the same operator) a mixed-precision
+        refinement: inner CG on op to inner_tol, outer FP64 residuals on op64 until tol."""
         b = np.ascontiguousarray(b, dtype=np.float64)
         if b.shape != (op.n,):
             raise ValueError("b must have n entries")
         x = np.empty_like(b)
         rid = C.c_int64(0)
-        _check(load().h2_server_submit(self.handle, op.handle, float(sigma2), _np_ptr(b), _np_ptr(x), float(tol),
-                                       int(maxit), C.byref(rid)), "h2_server_submit")
+        if op64 is None:
+            _check(load().h2_server_submit(self.handle, op.handle, float(sigma2), _np_ptr(b), _np_ptr(x), float(tol),
+                                           int(maxit), C.byref(rid)), "h2_server_submit")
+        else:
+            _check(load().h2_server_submit_refined(self.handle, op.handle, op64.handle, float(sigma2), _np_ptr(b),
+                                                   _np_ptr(x), float(tol), float(inner_tol), int(maxit),
+                                                   C.byref(rid)), "h2_server_submit_refined")
         self._live[rid.value] = (b, x)
         return rid.value
 

@@ -12,6 +12,12 @@
 // flag leave x untouched. The result of a request therefore does not depend on the other
 // requests in flight, and equals h2_cg_solve's result bitwise.
 //
+// Refined requests (h2_server_submit_refined) run the same CG iterations as the inner solver
+// of a mixed-precision iterative refinement: when an inner solve stops, one outer step
+// (x_o += d, r = b - (A64 + sigma2 I) x_o with the FP64 operator) is enqueued, and the
+// scheduler either finishes the request (FP64 residual below tol) or restarts the inner CG on
+// r, with the same captured iteration graph.
+//
 // One scheduler thread per server drives all slots; the public calls only touch the
 // request queue and the result list under a mutex.
 #include <cuda_runtime.h>
@@ -42,7 +48,23 @@ struct Head {
     int flag;        // 0 running, 1 converged, 2 breakdown
     int iters;       // iterations applied
     double scal[8];  // see h2_cgk.cuh: [0] r.r [1] p.Ap [2] r.r new [3] b.b [4] true residual^2
+                     // refined solves: [3] the inner right-hand side's r.r, [5] b.b
 };
+
+// x += d (the outer update of a refined solve)
+__global__ void k_axpy(double *__restrict__ x, const double *__restrict__ d, int64_t n)
+{
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        x[i] += d[i];
+}
+
+// Restart of a refined solve's inner CG on the outer residual r (already in r and p):
+// r.r of the new right-hand side is both the inner r.r and its reference, the flag clears.
+__global__ void k_restart(Head *h)
+{
+    h->scal[3] = h->scal[0];
+    h->flag = 0;
+}
 
 // flag = 1 before the first iteration when b = 0 (x = 0 is the solution) or the initial
 // residual already meets the tolerance (the tests of h2_cg_solve, in the same order).
@@ -128,6 +150,8 @@ class Arena {
 struct Request {
     int64_t id = 0;
     h2_handle op = nullptr;
+    h2_handle op64 = nullptr;  // refined solves: FP64 copy of the operator for the outer residuals
+    double inner_tol = 0;      // refined solves: relative tolerance of each inner CG
     double sigma2 = 0, tol = 0;
     int maxit = 0;
     const double *b = nullptr;
@@ -144,6 +168,7 @@ struct Slot {
     Request req;
     double t_admit = 0;
     int enq = 0, done = 0;
+    int enq_cap = 0;  // iterations may be enqueued while enq < enq_cap
     cudaStream_t st = nullptr;
     h2_exec ex;
     cudaEvent_t ev[kRing] = {};
@@ -158,13 +183,19 @@ struct Slot {
     float *pf = nullptr, *Apf = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    // refined solves: outer iterate, FP64 product workspace, the pending outer step
+    double *xo = nullptr;
+    void *ws64 = nullptr;
+    size_t ws64_bytes = 0;
+    bool outer_pending = false;
+    cudaEvent_t ev_outer = nullptr;
 };
 
-size_t request_bytes(h2_handle h, bool fp64, int64_t n)
+size_t request_bytes(h2_handle h, bool fp64, int64_t n, h2_handle h64 = nullptr)
 {
     const size_t nd = al(size_t(n) * 8), nf = al(size_t(n) * 4);
     return al(sizeof(Head)) + al(kDotBlocks * sizeof(double)) + 5 * nd + (fp64 ? 0 : 2 * nf) +
-           al(h2_workspace_bytes(h, 1));
+           al(h2_workspace_bytes(h, 1)) + (h64 ? nd + al(h2_workspace_bytes(h64, 1)) : 0);
 }
 
 int status_of(cudaError_t e) { return e == cudaSuccess ? H2_OK : (e == cudaErrorMemoryAllocation ? H2_ENOMEM : H2_ECUDA); }
@@ -210,6 +241,19 @@ struct h2_server {
         return status_of(cudaGetLastError());
     }
 
+    // out = (A64 + sigma2 I) v with the refinement operator (FP64)
+    int apply64(Slot &s, const double *v, double *out)
+    {
+        const Request &q = s.req;
+        const int rc = h2_matvec_exec(q.op64, v, out, 1, 1.0, 0.0, s.ws64, s.ws64_bytes, s.st, &s.ex);
+        if (rc != H2_OK) return rc;
+        k_shift<double><<<grid_for(q.n), kThreads, 0, s.st>>>(out, v, q.sigma2, out, q.n);
+        return status_of(cudaGetLastError());
+    }
+
+    // the stopping tolerance of the CG iterations: the request's, or a refined solve's inner one
+    static double cg_tol(const Request &q) { return q.op64 ? q.inner_tol : q.tol; }
+
     int admit(Slot &s, const Request &q, char *mem)
     {
         h2n::Range range("h2_server: admit");
@@ -218,6 +262,8 @@ struct h2_server {
         s.cancel = false;
         s.req = q;
         s.enq = s.done = 0;
+        s.enq_cap = q.maxit;
+        s.outer_pending = false;
         s.t_admit = now();
         s.mem = mem;
         const size_t nd = al(size_t(q.n) * 8), nf = al(size_t(q.n) * 4);
@@ -240,6 +286,16 @@ struct h2_server {
         }
         s.ws = m;
         s.ws_bytes = h2_workspace_bytes(q.op, 1);
+        m += al(s.ws_bytes);
+        s.xo = nullptr;
+        s.ws64 = nullptr;
+        s.ws64_bytes = 0;
+        if (q.op64) {
+            s.xo = reinterpret_cast<double *>(m);
+            m += nd;
+            s.ws64 = m;
+            s.ws64_bytes = h2_workspace_bytes(q.op64, 1);
+        }
         const size_t bytes = size_t(q.n) * 8;
         std::memcpy(s.stage, q.b, bytes);
         cudaMemcpyAsync(s.b, s.stage, bytes, cudaMemcpyHostToDevice, s.st);
@@ -250,9 +306,13 @@ struct h2_server {
         cudaMemcpyAsync(s.p, s.b, bytes, cudaMemcpyDeviceToDevice, s.st);
         dot(s.r, s.r, q.n, s.partial, s.head->scal + 0, s.st);
         dot(s.b, s.b, q.n, s.partial, s.head->scal + 3, s.st);
-        h2srv::k_init<<<1, 1, 0, s.st>>>(s.head, q.tol);
+        if (q.op64) {  // refined: x0 = 0 is the outer iterate, the inner CG starts on r = b
+            cudaMemsetAsync(s.xo, 0, bytes, s.st);
+            k_copy_scalar<<<1, 1, 0, s.st>>>(s.head->scal, 5, 3);
+        }
+        h2srv::k_init<<<1, 1, 0, s.st>>>(s.head, cg_tol(q));
         const int rc = status_of(cudaGetLastError());
-        if (rc == H2_OK && q.maxit == 0) return finish(s);
+        if (rc == H2_OK && q.maxit == 0) return q.op64 ? outer_step(s) : finish(s);
         return rc;
     }
 
@@ -267,7 +327,7 @@ struct h2_server {
         dot(s.p, s.Ap, n, s.partial, scal + 1, s.st);
         k_update_xr_if<<<grid_for(n), kThreads, 0, s.st>>>(s.x, s.r, s.p, s.Ap, scal, &s.head->flag, n);
         dot(s.r, s.r, n, s.partial, scal + 2, s.st);
-        k_check<<<1, 1, 0, s.st>>>(scal, &s.head->flag, &s.head->iters, q.tol);
+        k_check<<<1, 1, 0, s.st>>>(scal, &s.head->flag, &s.head->iters, cg_tol(q));
         k_update_p_if<<<grid_for(n), kThreads, 0, s.st>>>(s.p, s.r, scal, &s.head->flag, n);
         k_roll_if<<<1, 1, 0, s.st>>>(scal, &s.head->flag);
         return status_of(cudaGetLastError());
@@ -309,6 +369,37 @@ struct h2_server {
         return status_of(cudaGetLastError());
     }
 
+    // Refined solve, after an inner CG: x_o += d, d = 0, r = p = b - (A64 + sigma2 I) x_o in
+    // FP64, its r.r (also the next inner solve's initial r.r); the state goes to the host.
+    int outer_step(Slot &s)
+    {
+        h2n::Range range("h2_server: refinement step");
+        const Request &q = s.req;
+        const size_t bytes = size_t(q.n) * 8;
+        h2srv::k_axpy<<<grid_for(q.n), kThreads, 0, s.st>>>(s.xo, s.x, q.n);
+        cudaMemsetAsync(s.x, 0, bytes, s.st);
+        int rc = apply64(s, s.xo, s.Ap);
+        if (rc != H2_OK) return rc;
+        k_residual<<<grid_for(q.n), kThreads, 0, s.st>>>(s.b, s.Ap, s.r, s.p, q.n);
+        dot(s.r, s.r, q.n, s.partial, s.head->scal + 4, s.st);
+        k_copy_scalar<<<1, 1, 0, s.st>>>(s.head->scal, 0, 4);
+        cudaMemcpyAsync(&s.ring[kRing], s.head, sizeof(Head), cudaMemcpyDeviceToHost, s.st);
+        cudaEventRecord(s.ev_outer, s.st);
+        s.outer_pending = true;
+        s.done = s.enq;  // iterations enqueued after the inner convergence changed nothing
+        return status_of(cudaGetLastError());
+    }
+
+    // Refined solve, done: the outer iterate to the host (its FP64 residual is in ring[kRing]).
+    int finish_refined(Slot &s)
+    {
+        h2n::Range range("h2_server: finish");
+        s.finishing = true;
+        cudaMemcpyAsync(s.stage, s.xo, size_t(s.req.n) * 8, cudaMemcpyDeviceToHost, s.st);
+        cudaEventRecord(s.ev_fin, s.st);
+        return status_of(cudaGetLastError());
+    }
+
     // true residual with one more product, then x and the final state to the host
     int finish(Slot &s)
     {
@@ -330,9 +421,10 @@ struct h2_server {
         h2_request_result r{};
         r.request_id = s.req.id;
         r.iters = rc == H2_OK ? h.iters : 0;
-        const double bb = h.scal[3];
+        const double bb = s.req.op64 ? h.scal[5] : h.scal[3];
         r.true_relres = (rc == H2_OK && bb > 0.0) ? std::sqrt(h.scal[4] / bb) : 0.0;
-        r.status = rc != H2_OK ? rc : s.cancel ? H2_ECANCELED : (h.flag == 1 ? H2_OK : H2_ENOTCONV);
+        const bool ok = s.req.op64 ? (bb == 0.0 || r.true_relres < s.req.tol) : h.flag == 1;
+        r.status = rc != H2_OK ? rc : s.cancel ? H2_ECANCELED : (ok ? H2_OK : H2_ENOTCONV);
         if (rc == H2_OK) std::memcpy(s.req.x, s.stage, size_t(s.req.n) * 8);
         r.t_submit = s.req.t_submit;
         r.t_admit = s.t_admit;
@@ -396,6 +488,31 @@ struct h2_server {
                 moved = true;
                 continue;
             }
+            if (s.outer_pending) {  // refined solve: the FP64 residual of the new outer iterate
+                const cudaError_t e = cudaEventQuery(s.ev_outer);
+                if (e == cudaErrorNotReady) continue;
+                moved = true;
+                s.outer_pending = false;
+                if (e != cudaSuccess) {
+                    complete(s, status_of(e));
+                    continue;
+                }
+                const Head h = s.ring[kRing];
+                const double bb = h.scal[5];
+                const bool conv = bb == 0.0 || std::sqrt(h.scal[4] / bb) < s.req.tol;
+                if (conv || h.flag == 2 || h.iters >= s.req.maxit || s.cancel) {
+                    const int rc = finish_refined(s);
+                    if (rc != H2_OK) complete(s, rc);
+                    continue;
+                }
+                h2srv::k_restart<<<1, 1, 0, s.st>>>(s.head);  // next inner CG on the outer residual
+                s.enq_cap = s.enq + (s.req.maxit - h.iters);
+                const int rc = status_of(cudaGetLastError());
+                if (rc != H2_OK) {
+                    complete(s, rc);
+                    continue;
+                }
+            }
             while (s.done < s.enq) {
                 const cudaError_t e = cudaEventQuery(s.ev[s.done % kRing]);
                 if (e == cudaErrorNotReady) break;
@@ -407,21 +524,21 @@ struct h2_server {
                 const Head h = s.ring[s.done % kRing];
                 ++s.done;
                 if (h.flag != 0 || h.iters >= s.req.maxit) {
-                    const int rc = finish(s);
+                    const int rc = s.req.op64 ? outer_step(s) : finish(s);
                     if (rc != H2_OK) complete(s, rc);
                     break;
                 }
             }
-            if (!s.busy || s.finishing) continue;
+            if (!s.busy || s.finishing || s.outer_pending) continue;
             if (s.cancel) {  // no new iterations; finish once the enqueued ones are done
                 if (s.done == s.enq) {
-                    const int rc = finish(s);
+                    const int rc = s.req.op64 ? outer_step(s) : finish(s);
                     if (rc != H2_OK) complete(s, rc);
                     moved = true;
                 }
                 continue;
             }
-            while (s.enq - s.done < kAhead && s.enq < s.req.maxit) {
+            while (s.enq - s.done < kAhead && s.enq < s.enq_cap) {
                 const int rc = enqueue_iteration(s);
                 moved = true;
                 if (rc != H2_OK) {
@@ -477,6 +594,7 @@ int h2_server_create(size_t slot_memory_bytes, int max_slots, int64_t max_points
         for (int j = 0; rc == H2_OK && j < kRing; ++j)
             rc = status_of(cudaEventCreateWithFlags(&sl.ev[j], cudaEventDisableTiming));
         if (rc == H2_OK) rc = status_of(cudaEventCreateWithFlags(&sl.ev_fin, cudaEventDisableTiming));
+        if (rc == H2_OK) rc = status_of(cudaEventCreateWithFlags(&sl.ev_outer, cudaEventDisableTiming));
         if (rc == H2_OK)
             rc = status_of(cudaMallocHost(reinterpret_cast<void **>(&sl.stage), size_t(max_points) * sizeof(double)));
     }
@@ -516,6 +634,48 @@ int h2_server_submit(h2_server_t s, h2_handle op, double sigma2, const double *b
     ++s->outstanding;
     if (request_id) *request_id = q.id;
     return H2_OK;
+}
+
+int h2_server_submit_refined(h2_server_t s, h2_handle op, h2_handle op64, double sigma2, const double *b, double *x,
+                             double tol, double inner_tol, int maxit, int64_t *request_id)
+{
+    if (request_id) *request_id = 0;
+    if (!s || !op || !op64 || !b || !x || maxit < 0 || !(tol >= 0) || !(sigma2 >= 0) ||
+        !(inner_tol > 0 && inner_tol < 1))
+        return H2_EINVAL;
+    h2_info info, info64;
+    if (h2_get_info(op, &info) != H2_OK || h2_get_info(op64, &info64) != H2_OK) return H2_EINVAL;
+    if (info.uploaded_prec < 0 || info64.uploaded_prec != H2_FP64) return H2_ESTATE;
+    if (info.n != info64.n || info.n > s->max_points) return H2_EINVAL;
+    Request q;
+    q.op = op;
+    q.op64 = op64;
+    q.inner_tol = inner_tol;
+    q.sigma2 = sigma2;
+    q.tol = tol;
+    q.maxit = maxit;
+    q.b = b;
+    q.x = x;
+    q.n = info.n;
+    q.fp64 = info.uploaded_prec == H2_FP64;
+    q.bytes = request_bytes(op, q.fp64, q.n, op64);
+    if (al(q.bytes) > s->arena.capacity()) return H2_ENOMEM;
+    q.t_submit = s->now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    q.id = s->next_id++;
+    s->queue.push_back(q);
+    ++s->outstanding;
+    if (request_id) *request_id = q.id;
+    return H2_OK;
+}
+
+size_t h2_server_request_bytes_refined(h2_handle op, h2_handle op64)
+{
+    if (!op || !op64) return 0;
+    h2_info info, info64;
+    if (h2_get_info(op, &info) != H2_OK || info.uploaded_prec < 0) return 0;
+    if (h2_get_info(op64, &info64) != H2_OK || info64.uploaded_prec != H2_FP64 || info64.n != info.n) return 0;
+    return request_bytes(op, info.uploaded_prec == H2_FP64, info.n, op64);
 }
 
 int h2_server_poll(h2_server_t s, h2_request_result *results, int max_results, int *n_results)
@@ -575,6 +735,7 @@ int h2_server_destroy(h2_server_t s)
         for (cudaEvent_t e : sl.ev)
             if (e) cudaEventDestroy(e);
         if (sl.ev_fin) cudaEventDestroy(sl.ev_fin);
+        if (sl.ev_outer) cudaEventDestroy(sl.ev_outer);
         h2_exec_destroy(&sl.ex);
         if (sl.st) cudaStreamDestroy(sl.st);
         if (sl.stage) cudaFreeHost(sl.stage);

@@ -208,3 +208,66 @@ def test_served_imq_family_against_the_oracle(imq_family, sigma2, maxit):
         assert r["status"] == h2.H2_OK and ref["converged"]
         assert abs(r["iters"] - ref["iters"]) <= 0.15 * ref["iters"]
         assert orc_res <= 5e-6
+
+
+@pytest.fixture(scope="module")
+def imq_refined():
+    pts = si.uniform_cloud(4096, 2, 50)
+    orc = oracle.OracleH2(pts, IMQ, 64, 8, 0.7, assemble=True)
+    op32 = h2.H2Operator(pts, IMQ, 64, 8, 0.7).upload("fp32")
+    op64 = h2.H2Operator(pts, IMQ, 64, 8, 0.7).upload("fp64")
+    yield orc, op32, op64, si.gaussian_vectors(4096, 1, 7)[:, 0].copy()
+    op32.close()
+    op64.close()
+
+
+def test_refined_solve_reaches_tol_in_fp64(imq_refined):
+    """Mixed-precision refinement (inner CG on the FP32 product, outer FP64 residuals): the
+    served x meets tol 1e-6 under the oracle's FP64 operator, which plain CG with FP32
+    products does not (its FP64 residual stalls just above tol here, ≈1.1e-6, and grows with
+    N); the result is the same alone and among other requests."""
+    orc, op32, op64, b = imq_refined
+    sigma2, tol = 1e4, 1e-6
+    server = h2.H2Server(6 * h2.H2Server.request_bytes_refined(op32, op64), 4, op32.n)
+    try:
+        rid = server.submit(op32, b, tol, 3000, sigma2, op64=op64, inner_tol=1e-3)
+        assert server.wait(300.0) == h2.H2_OK
+        (alone,) = server.poll()
+        # the same request among plain ones and another refined one
+        ids = [server.submit(op32, rhs(op32.n, 40 + j), 1e-5, 200, sigma2) for j in range(3)]
+        rid2 = server.submit(op32, b, tol, 3000, sigma2, op64=op64, inner_tol=1e-3)
+        ids.append(server.submit(op32, rhs(op32.n, 50), tol, 3000, sigma2, op64=op64, inner_tol=1e-2))
+        assert server.wait(300.0) == h2.H2_OK
+        mix = {r["id"]: r for r in server.poll(16)}
+    finally:
+        server.close()
+    assert alone["id"] == rid and alone["status"] == h2.H2_OK
+    assert alone["true_relres"] < tol
+    assert oracle_product_relres(orc, alone["x"], b, sigma2) < 1.5 * tol
+    assert np.array_equal(mix[rid2]["x"], alone["x"]) and mix[rid2]["iters"] == alone["iters"]
+    assert all(mix[i]["status"] == h2.H2_OK for i in ids)
+    # plain FP32 CG on the same system stalls above tol in the FP64 sense
+    server = h2.H2Server(4 * h2.H2Server.request_bytes(op32), 2, op32.n)
+    try:
+        server.submit(op32, b, tol, 3000, sigma2)
+        assert server.wait(300.0) == h2.H2_OK
+        (plain,) = server.poll()
+    finally:
+        server.close()
+    assert plain["status"] == h2.H2_OK  # its recursive residual met tol ...
+    assert oracle_product_relres(orc, plain["x"], b, sigma2) > oracle_product_relres(orc, alone["x"], b, sigma2)
+    assert alone["iters"] <= 2 * plain["iters"]
+
+
+def test_refined_submit_rejects_mismatched_operators(imq_refined):
+    orc, op32, op64, b = imq_refined
+    server = h2.H2Server(4 * h2.H2Server.request_bytes_refined(op32, op64), 2, op32.n)
+    try:
+        with pytest.raises(h2.H2Error) as e:
+            server.submit(op32, b, 1e-6, 10, 1.0, op64=op32)  # not an FP64 copy
+        assert e.value.status == h2.H2_ESTATE
+        with pytest.raises(h2.H2Error) as e:
+            server.submit(op32, b, 1e-6, 10, 1.0, op64=op64, inner_tol=1.5)
+        assert e.value.status == h2.H2_EINVAL
+    finally:
+        server.close()
