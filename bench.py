@@ -998,6 +998,10 @@ def main():
     line["product_bound_frac"] = line["product_bound_ms"] / ms_step
     if fp32 is not None:
         line["fp32"] = fp32
+    if world > 1:
+        # replicas: the side measurements below characterise one GPU; at N > 1 the line is the
+        # replicated headline product only, so the job holds its GPUs for no longer than that
+        args.no_matrix_free = args.no_multi_rhs = args.no_batch = args.no_compress = args.no_serve = True
     if not args.no_matrix_free and fp32 is not None:
         try:
             line["matrix_free"] = matrix_free(h2, torch, op, x_host, flush, stream, max(20, args.steps // 4),

@@ -277,3 +277,26 @@ def test_fp32_tensor_and_cuda_core_passes_agree(built, name, nv):
     assert relerr(tensor, ref) <= TOL["fp32"]
     assert relerr(tensor, cuda_cores) <= TOL["fp32"]
     assert np.array_equal(gpu_matvec(op, X, "fp32", 0.75, 0.5, Y0), tensor)  # no atomics on data
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_ranks_stream_dense_rows_apart(built, prec):
+    """Rank 16 with 64-point leaves: the dense tiles are 4x the coupling tiles, so the lower
+    levels' coupling rows and the dense rows run as two streams (the coupling rows with
+    several CTAs per SM); the product still matches the oracle, at 1 and at 4 vectors."""
+    pts, ker, orc, op = built("grid64_exp")
+    op.upload(prec)
+    for nv in (1, 4):
+        X = si.gaussian_vectors(len(pts), nv, 41)
+        h2.h2_get_timing(op.handle)
+        got = gpu_matvec(op, X, prec)
+        _, launches, products = h2.h2_get_timing(op.handle)
+        assert products == 1 and launches[1] == 2  # coupling stream + dense stream
+        assert relerr(got, orc.matvec(X)) <= TOL[prec]
+    # rank 64 with 64-point leaves: one stream for both
+    pts64, _, orc64, op64 = built("cloud3d_k64")
+    op64.upload(prec)
+    h2.h2_get_timing(op64.handle)
+    gpu_matvec(op64, si.gaussian_vectors(len(pts64), 1, 42), prec)
+    _, launches, _ = h2.h2_get_timing(op64.handle)
+    assert launches[1] == 1
