@@ -139,7 +139,7 @@ __global__ void k_gather_batch(const SweepTask<T> *__restrict__ tasks, int ntask
         const Op<T> &op = t.op;
         const Vec<T> &vec = t.vec;
         const int64_t leaf = g - t.first;
-        if (leaf == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
+        if (leaf == 0 && threadIdx.x < kTickets) vec.tickets[threadIdx.x] = 0;
         const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
         if (!rows) {
             for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {

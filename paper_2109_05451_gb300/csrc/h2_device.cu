@@ -30,6 +30,7 @@
 #include "h2_tf32stream.cuh"
 #include "h2_batch.cuh"
 #include "h2_mf.cuh"
+#include "h2_warpsweep.cuh"
 #include "h2_nvtx.h"
 
 #include <dlfcn.h>
@@ -70,6 +71,9 @@ struct h2_device {
     // FP32 operators with ranks and leaves of at most 64: passes of more than 8 vectors run on
     // the tensor cores (3xTF32, k_stream_tf32) unless switched off by h2_set_fp32_tensor
     bool tf32_ok = false, tf32_on = true;
+    // ranks of at most 32: single-vector products sweep the tree with one warp per node
+    // (h2_warpsweep.cuh) instead of the staged subtree kernels
+    bool warp_sweeps = false;
     // views into the arena
     int32_t *perm = nullptr, *leaf_lo = nullptr;
     int64_t *cpl_rowptr = nullptr;
@@ -182,6 +186,7 @@ namespace {
 struct Workspace {
     void *xt, *yd, *xh, *yh;
     int *tickets;
+    int *flags = nullptr;  // warp sweeps: 2 (nnodes + 1) node flags, upsweep then downsweep
     // tensor-core path (H2_BF16X2): split-BF16 vector tiles of the coefficient tree and of
     // the permuted input
     unsigned char *xb = nullptr, *xtb = nullptr;
@@ -225,6 +230,8 @@ size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, voi
     const size_t xb = tiles ? align_up(size_t(op.nnodes + 1) * tile_bytes) : 0;
     const size_t xtb = tiles ? align_up(size_t(op.nleaves()) * tile_bytes) : 0;
     const size_t rows = wide ? align_up(size_t(op.n) * round4(vp) * es) : 0;
+    const size_t flags = dv.warp_sweeps ? align_up(size_t(2) * (op.nnodes + 1) * sizeof(int)) : 0;
+    static_assert(h2s::kTickets * sizeof(int) <= kAlign, "scheduling words fit the ticket slot");
     if (w) {
         char *p = static_cast<char *>(base);
         w->xt = p;
@@ -235,8 +242,9 @@ size_t ws_layout(const h2_op &op, const h2_device &dv, int nv, Workspace *w, voi
         w->xtb = tiles ? w->xb + xb : nullptr;
         w->rows = wide ? p + 2 * vec + 2 * tree + xb + xtb : nullptr;
         w->tickets = reinterpret_cast<int *>(p + 2 * vec + 2 * tree + xb + xtb + rows);
+        w->flags = dv.warp_sweeps ? reinterpret_cast<int *>(p + 2 * vec + 2 * tree + xb + xtb + rows + kAlign) : nullptr;
     }
-    return 2 * vec + 2 * tree + xb + xtb + rows + kAlign;
+    return 2 * vec + 2 * tree + xb + xtb + rows + kAlign + flags;
 }
 
 int cuda_status(cudaError_t e)
@@ -349,6 +357,74 @@ void launch_mf(const h2_op &op, const h2s::Op<float> &o, const h2s::Vec<float> &
         launch_mf_dim<2, NVMAX>(op.ker.kind, o, v, ma, p, smem, grid, desc, chunks, nchunks, ticket, st);
 }
 
+template <typename T, int KM>
+void launch_warp_sweep_km(bool up, const h2_op &op, const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_device &dv,
+                          const Workspace &w, int lo, int hi, int edge, int ticket, cudaStream_t st)
+{
+    using namespace h2s;
+    static int occ = 0;  // resident CTAs per SM (per element type and partial width)
+    if (!occ) {
+        int a = 0, b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_up_warp<T, KM>, kWsThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_down_warp<T, KM>, kWsThreads, 0);
+        occ = std::max(1, std::min(a, b));
+    }
+    const int top = up ? (edge ? hi : hi - 1) : hi;
+    if (top < lo) return;
+    const int64_t items = (int64_t(2) << top) - (int64_t(1) << lo);
+    const int64_t warps = (items + kWsChunk - 1) / kWsChunk;
+    const int64_t ctas = std::min<int64_t>((warps + kWsWarps - 1) / kWsWarps, int64_t(dv.num_sms) * occ);
+    const WarpSweep ws{w.tickets + ticket, w.tickets + 8, w.flags + (up ? 0 : op.nnodes + 1), lo, hi, edge};
+    if (up)
+        k_up_warp<T, KM><<<unsigned(ctas), kWsThreads, 0, st>>>(o, v, ws);
+    else
+        k_down_warp<T, KM><<<unsigned(ctas), kWsThreads, 0, st>>>(o, v, ws);
+}
+
+// Coupling rows of small ranks, one vector: one warp per chunk of rows (k_rows_warp) on the
+// scheduling word `ticket`, at most the CTAs resident on the device.
+template <typename T, int KM>
+void launch_rows_warp_km(const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_device &dv,
+                         const h2s::StreamDesc *desc, const int64_t *chunks, int64_t nchunks, int ticket,
+                         cudaStream_t st)
+{
+    using namespace h2s;
+    static int occ = 0;
+    if (!occ) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_warp<T, KM>, kWsThreads, 0);
+        occ = std::max(1, occ);
+    }
+    const int64_t ctas = std::min<int64_t>((nchunks + kWsWarps - 1) / kWsWarps, int64_t(dv.num_sms) * occ);
+    k_rows_warp<T, KM><<<unsigned(std::max<int64_t>(1, ctas)), kWsThreads, 0, st>>>(o, v, desc, chunks, nchunks,
+                                                                                   ticket);
+}
+
+template <typename T>
+void launch_rows_warp(const h2_op &op, const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_device &dv,
+                      const h2s::StreamDesc *desc, const int64_t *chunks, int64_t nchunks, int ticket,
+                      cudaStream_t st)
+{
+    if (op.k <= 16)
+        launch_rows_warp_km<T, 16>(o, v, dv, desc, chunks, nchunks, ticket, st);
+    else
+        launch_rows_warp_km<T, 32>(o, v, dv, desc, chunks, nchunks, ticket, st);
+}
+
+// One launch of a warp-per-node sweep (ranks <= 32, one vector; h2_warpsweep.cuh): enough
+// warps for the launch's tickets, at most the CTAs resident on the device. Upsweep: levels
+// hi-1 .. lo from level hi (with edge, hi = q and the leaf projections); downsweep: levels
+// lo .. hi (with edge, hi = q and the leaf expansion and epilogue). `ticket` is the launch's
+// scheduling word.
+template <typename T>
+void launch_warp_sweep(bool up, const h2_op &op, const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_device &dv,
+                       const Workspace &w, int lo, int hi, int edge, int ticket, cudaStream_t st)
+{
+    if (op.k <= 16)
+        launch_warp_sweep_km<T, 16>(up, op, o, v, dv, w, lo, hi, edge, ticket, st);
+    else
+        launch_warp_sweep_km<T, 32>(up, op, o, v, dv, w, lo, hi, edge, ticket, st);
+}
+
 template <typename T, int NVMAX>
 int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, double alpha, double beta,
                  const Workspace &w, cudaStream_t st, const h2_exec &ex)
@@ -363,6 +439,12 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
              static_cast<T *>(w.yh), w.tickets, dv.err};
     const int Lbot = dv.L, Lb = dv.Lb;
     const int64_t nsub = int64_t(1) << Lb;
+    // ranks of at most 32, one vector: warp-per-node sweeps, one launch per part of the tree
+    const bool wsw = NVMAX == 1 && dv.warp_sweeps && w.flags;
+    if (wsw) {
+        v.flags = w.flags;
+        v.nflags = 2 * (op.nnodes + 1);
+    }
     // levels per launch above the bottom subtrees: as many as keep the subtree's vectors
     // within 16 KB of shared memory (at most 5)
     int Ltop = 1;
@@ -396,8 +478,10 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
                                 : make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 160 * 1024, 12);
     const Pipe p_dns = make_pipe<T, NVMAX>(dv.tile_dns, uint32_t(mp * NVMAX * es), 0, kx, true, 160 * 1024, 32);
     const size_t sm_dns = smem_bytes<T, NVMAX>(p_dns, 0, kx, true);
-    // (the upper levels' coupling blocks are stored for the matrix-free precision too)
-    const Pipe p_top = make_pipe<T, NVMAX>(tile_str, x_str, 0, kx, true, 64 * 1024, 4);
+    // (the upper levels' coupling blocks are stored for the matrix-free precision too). The
+    // upper rows hold coupling blocks only: stages sized for them keep this kernel small
+    // enough to become resident next to the bottom streams.
+    const Pipe p_top = make_pipe<T, NVMAX>(dv.tile_cpl, uint32_t(kx * NVMAX * es), 0, kx, true, 64 * 1024, 8);
     const size_t sm_bot = smem_bytes<T, NVMAX>(p_bot, 0, kx, true), sm_top = smem_bytes<T, NVMAX>(p_top, 0, kx, true);
     const unsigned grid_bot =
         mf ? unsigned(std::max<int64_t>(1, std::min<int64_t>(4 * int64_t(dv.num_sms), dv.n_chunks_bottom)))
@@ -410,7 +494,10 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     {
         h2n::Range r("upsweep: leaf subtrees");
         k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
-        k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
+        if (wsw)
+            launch_warp_sweep<T>(true, op, o, v, dv, w, Lb, op.q, 1, 4, st);
+        else
+            k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
     }
     dv.end(0, ev, st, 2);
     const bool top = Lb >= 1;
@@ -425,6 +512,11 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     auto top_up = [&]() {
         h2n::Range r("upsweep: upper levels");
         eb = dv.begin(side);
+        if (wsw) {
+            launch_warp_sweep<T>(true, op, o, v, dv, w, 0, Lb, 0, 5, side);
+            ++top_launches;
+            return;
+        }
         for (int lin = Lb; lin > 0;) {
             const int L = std::min(Ltop, lin), lr = lin - L;
             const int64_t ns = int64_t(1) << lr;
@@ -446,7 +538,9 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     ev = dv.begin(st);
     if (dv.n_chunks_bottom > 0) {
         h2n::Range r("tree multiply + dense: lower levels");
-        if constexpr (sizeof(T) == 4 && NVMAX <= kChunk) {
+        if (wsw && dsplit && !mf) {  // the bottom list holds coupling rows only
+            launch_rows_warp<T>(op, o, v, dv, dv.desc_bottom, dv.chunks_bottom, dv.n_chunks_bottom, 0, st);
+        } else if constexpr (sizeof(T) == 4 && NVMAX <= kChunk) {
             if (mf) {
                 launch_mf<NVMAX>(op, o, v, dv.mfa, p_bot, sm_bot, grid_bot, dv.desc_bottom, dv.chunks_bottom,
                                  dv.n_chunks_bottom, 0, st);
@@ -473,17 +567,25 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
         if (!mf) top_up();
         h2n::Range r("tree multiply + downsweep: upper levels");
         if (dv.n_chunks_top > 0) {
-            k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
-                                                                      dv.n_chunks_top, 1);
+            if (wsw)
+                launch_rows_warp<T>(op, o, v, dv, dv.desc_top, dv.chunks_top, dv.n_chunks_top, 1, sb);
+            else
+                k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
+                                                                          dv.n_chunks_top, 1);
             ++top_launches;
         }
-        for (int lr = 0; lr <= Lb - 1;) {
-            const int L = std::min(Ltop, Lb - 1 - lr);
-            const int64_t ns = int64_t(1) << lr;
-            k_down_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, sb>>>(
-                o, v, p_tsub, lr, L, ns, 0);
+        if (wsw) {
+            launch_warp_sweep<T>(false, op, o, v, dv, w, 0, Lb - 1, 0, 6, sb);
             ++top_launches;
-            lr += L + 1;
+        } else {
+            for (int lr = 0; lr <= Lb - 1;) {
+                const int L = std::min(Ltop, Lb - 1 - lr);
+                const int64_t ns = int64_t(1) << lr;
+                k_down_sub<T, NVMAX><<<unsigned(std::min<int64_t>(ns, dv.num_sms)), kThreads, sm_tsub, sb>>>(
+                    o, v, p_tsub, lr, L, ns, 0);
+                ++top_launches;
+                lr += L + 1;
+            }
         }
         dv.end(2, eb, sb, top_launches);
         cudaEventRecord(ev_top, sb);
@@ -493,7 +595,10 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     ev = dv.begin(st);
     {
         h2n::Range r("downsweep: leaf subtrees");
-        k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
+        if (wsw)
+            launch_warp_sweep<T>(false, op, o, v, dv, w, Lb, op.q, 1, 7, st);
+        else
+            k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
     }
     dv.end(3, ev, st, 1);
     return cuda_status(cudaGetLastError());
@@ -1795,6 +1900,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     dv->mp = round4(dv->max_leaf_rows);
     dv->kkp = int64_t(k) * round4(k);  // entries per stored coupling tile (ld kx)
     dv->tf32_ok = prec == H2_FP32 && k <= 64 && dv->max_leaf_rows <= 64;
+    dv->warp_sweeps = !dv->tc && k <= h2s::kWsMaxRank && dv->mp <= 128;
     dv->L = std::min(op.q, 4);
     dv->Lb = op.q - dv->L;
     dv->root_row = op.cpl_rowptr[2] > op.cpl_rowptr[1];
@@ -1882,8 +1988,12 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
         while (nc < db.size() && !(db[nc].flags & h2s::kDense)) ++nc;
         const std::vector<h2s::StreamDesc> dc(db.begin(), db.begin() + nc), dd(db.begin() + nc, db.end());
         const std::vector<uint64_t> bc(bb.begin(), bb.begin() + nc), bd(bb.begin() + nc, bb.end());
-        // small tiles: smaller scheduling chunks, for the several CTAs per SM of their stream
-        if (!make_chunks(dc, bc, 128 * 1024, pb) || !make_chunks(dd, bd, 512 * 1024, pd)) {
+        // small tiles: smaller scheduling chunks, for the several CTAs per SM of their stream;
+        // with warp sweeps (ranks <= 32) single-vector products take one warp per chunk: about
+        // 48 blocks each
+        const uint64_t cpl_target =
+            dv->warp_sweeps ? std::min<uint64_t>(128 * 1024, 48 * uint64_t(dv->tile_cpl)) : 128 * 1024;
+        if (!make_chunks(dc, bc, cpl_target, pb) || !make_chunks(dd, bd, 512 * 1024, pd)) {
             h2_device_free(&op);
             return H2_EINVAL;
         }

@@ -72,7 +72,7 @@ struct Vec {
     int vs;  // vectors per node in the tree layouts (>= nv)
     T alpha, beta;
     T *xt, *yd, *xh, *yh;
-    int *tickets;  // [0] bottom stream, [1] top stream (zeroed by k_gather)
+    int *tickets;  // kTickets scheduling words of this product (zeroed by k_gather)
     int *err;
     // tensor-core path only: split-BF16 B-operand tiles of every node's xhat (written by the
     // upsweep) and of every leaf's permuted input (written by the gather), np rows each
@@ -82,7 +82,14 @@ struct Vec {
     // so that the gather and the leaf epilogue move whole rows of nv values
     T *xr = nullptr, *yr = nullptr;
     int ldr = 0;
+    // warp-per-node sweeps (h2_warpsweep.cuh): the nodes' completion flags, zeroed by k_gather
+    int *flags = nullptr;
+    int64_t nflags = 0;
 };
+
+// Scheduling words of a product: [0] bottom block stream, [1] top block stream, [2] dense
+// stream, [4 .. 7] the warp sweeps' launches, [8] their abort word.
+constexpr int kTickets = 16;
 
 // Bytes of one node's split-BF16 vector tile: np rows (vectors) x 64 bf16, hi then lo.
 __host__ __device__ constexpr uint32_t vec_tile_bytes(int np) { return 2u * uint32_t(np) * 128u; }
@@ -766,12 +773,14 @@ using AccStreamOf =
 // ------------------------------------------------------------------ gather
 
 // xt[leaf][v][i] = X[v*n + perm[leaf_lo[leaf] + i]]: one CTA per leaf (grid-stride). Also
-// resets the scheduling tickets of this product. With vec.xtb (tensor-core passes) it also
-// writes each leaf's split-BF16 tile.
+// resets the scheduling tickets and the warp sweeps' node flags of this product. With
+// vec.xtb (tensor-core passes) it also writes each leaf's split-BF16 tile.
 template <typename T>
 __global__ void k_gather(Op<T> op, Vec<T> vec)
 {
-    if (blockIdx.x == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < kTickets) vec.tickets[threadIdx.x] = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < vec.nflags; i += int64_t(gridDim.x) * blockDim.x)
+        vec.flags[i] = 0;
     for (int64_t leaf = blockIdx.x; leaf < op.nleaves; leaf += gridDim.x) {
         const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
         if (vec.xtb == nullptr) {
@@ -806,7 +815,7 @@ template <typename T>
 __global__ void k_gather_rows(Op<T> op, Vec<T> vec)
 {
     __shared__ T rows[64 * 33];
-    if (blockIdx.x == 0 && threadIdx.x < 4) vec.tickets[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < kTickets) vec.tickets[threadIdx.x] = 0;
     for (int64_t leaf = blockIdx.x; leaf < op.nleaves; leaf += gridDim.x) {
         const int r0 = op.leaf_lo[leaf], R = op.leaf_lo[leaf + 1] - r0;
         for (int e = threadIdx.x; e < R * vec.nv; e += blockDim.x) {

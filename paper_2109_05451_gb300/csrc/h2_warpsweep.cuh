@@ -1,0 +1,388 @@
+// h2_warpsweep.cuh -- sweeps and coupling rows of operators of small rank (k <= 32), one
+// vector: one warp per tree node or per chunk of block rows.
+//
+// With k <= 32 a node's coefficient vector fits one warp and a transfer or leaf-basis tile is
+// a few hundred bytes to a few KB. The staged sweeps of h2_stream.cuh (one tile per pipeline
+// stage, reductions across four consumer warps) are then bound by their per-tile latency, not
+// by HBM. Here each warp takes tree nodes from a ticket counter in dependency order and reads
+// its tiles straight from global memory:
+//
+//   k_up_warp    xhat^q_t = U_t^T x_t at the leaves (Sec. 3.1), then
+//                xhat^{l-1}_p = sum_c E_c^T xhat^l_c (Alg 1), level by level upwards;
+//   k_down_warp  yhat^l_c = E_c yhat^{l-1}_p + yhat^l_c (the node's own coupling row), level
+//                by level downwards, and at the leaves y_t = U_t yhat^q_t + (A_de x)_t,
+//                Y[perm] = alpha y + beta Y (Sec. 3.3, Alg 6).
+//
+// Every product of a node is formed the same way: each lane accumulates a partial vector of
+// KM (16 or 32 >= k) outputs from the tile entries it loaded (lane j takes row j of a
+// transfer tile, lane i row i of the leaf basis), and one reduce-scatter over the warp (31
+// shuffles) leaves output o in lane o. A node issues all its tile loads before it waits for
+// the nodes it reads, so one memory latency, not one per tile row, lies on each dependency.
+// Tiles are read in the layouts of h2_stream.cuh: U_t^T as [nu][i] (ld mp), E_c and E_c^T
+// as [j][o] (ld kx), where j is the input and o the output coefficient.
+//
+// Ordering: a node's work item comes after the items of the nodes it reads (its children in
+// the upsweep, its parent in the downsweep), and a warp takes a ticket only while it runs, so
+// each wait is for a warp that is already running and that itself waits only on earlier
+// items; the waits end. Each one is still bounded (about a second): a wait that runs out
+// raises the launch's abort word and the operator's error flag, and every warp then returns.
+// A node publishes its vector by a release store of its flag after its lanes' stores and a
+// fence; a reader acquires the flag in every lane and reads the vector through L2.
+#pragma once
+
+#include <cstdint>
+
+#include "h2_pipe.cuh"
+#include "h2_stream.cuh"
+
+namespace h2s {
+
+// Two warps per CTA: small CTAs also become resident next to a persistent block stream (the
+// upper levels' sweeps run on a side stream while the lower levels' rows stream).
+constexpr int kWsThreads = 64;
+constexpr int kWsWarps = kWsThreads / 32;
+constexpr int kWsChunk = 2;      // consecutive work items per ticket
+constexpr int kWsMaxRank = 32;
+
+// One launch of a warp sweep.
+struct WarpSweep {
+    int *ticket;  // this launch's work counter (zeroed by the gather)
+    int *abort;   // raised by a wait that ran out (zeroed by the gather)
+    int *flag;    // per heap node: set once the node's vector is final (zeroed by the gather)
+    int lo, hi;   // upsweep: levels hi-1 .. lo from the inputs of level hi (with edge, level hi
+                  // = q is computed too, from the leaf projections); downsweep: levels lo .. hi
+    int edge;     // upsweep: leaf projections; downsweep: leaf expansion and epilogue
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits (lane 0, bounded) until *flag is set, then acquires it in every lane. False, in every
+// lane, once this launch aborted.
+__device__ __forceinline__ bool ws_wait(const int *flag, int *abort, int *err)
+{
+    const int lane = threadIdx.x & 31;
+    int ok = 1;
+    if (lane == 0 && !ld_acquire_gpu(flag)) {
+        const long long t0 = clock64();
+        for (;;) {
+            if (ld_acquire_gpu(flag)) break;
+            if (*reinterpret_cast<volatile int *>(abort)) {
+                ok = 0;
+                break;
+            }
+            if (clock64() - t0 > h2p::kWaitCycles) {
+                atomicExch(abort, 1);
+                if (err) atomicExch(err, 1);
+                ok = 0;
+                break;
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) (void)ld_acquire_gpu(flag);
+    return ok != 0;
+}
+
+// After the lanes' stores of a node's vector: every lane fences, then lane 0 sets the flag.
+__device__ __forceinline__ void ws_publish(int *flag)
+{
+    __threadfence();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) st_release_gpu(flag, 1);
+}
+
+// Next ticket of the warp (lane 0 draws, all lanes get it).
+__device__ __forceinline__ int64_t ws_ticket(int *ticket)
+{
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(ticket, 1);
+    return int64_t(__shfl_sync(0xffffffffu, t, 0));
+}
+
+// Sum over the warp of the lanes' partial vectors p[0 .. KM): afterwards p[0] of lane l holds
+// output l mod KM. Pairs of lanes halve the outputs they keep at each step (KM = 32) or first
+// add their whole vectors (the step of offset 16 with KM = 16).
+template <typename T, int KM>
+__device__ __forceinline__ T ws_reduce(T (&p)[KM])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        if (s >= KM) {
+#pragma unroll
+            for (int j = 0; j < KM; ++j) p[j] += __shfl_xor_sync(0xffffffffu, p[j], s);
+        } else {
+            const bool upper = (lane & s) != 0;
+#pragma unroll
+            for (int j = 0; j < s; ++j) {
+                const T send = upper ? p[j] : p[j + s];
+                const T keep = upper ? p[j + s] : p[j];
+                p[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+            }
+        }
+    }
+    return p[0];
+}
+
+// Row j = lane of a transfer tile ([j][o], ld kx): r[o] for o < KM, zero beyond kx and for
+// lanes j >= k. 16-byte loads (kx is a multiple of 4, tile rows start on 16 bytes).
+template <typename T, int KM>
+__device__ __forceinline__ void ws_load_row(const T *__restrict__ tile, int k, int kx, T (&r)[KM])
+{
+    const int lane = threadIdx.x & 31;
+    constexpr int V = 16 / sizeof(T);  // elements per 16-byte load
+    const T *__restrict__ row = tile + int64_t(lane) * kx;
+#pragma unroll
+    for (int q = 0; q < KM / V; ++q) {
+        if (lane < k && q * V < kx) {
+            if constexpr (V == 4) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(row) + q);
+                r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
+            } else {
+                const double2 v = __ldg(reinterpret_cast<const double2 *>(row) + q);
+                r[2 * q] = v.x, r[2 * q + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) r[V * q + e] = T(0);
+        }
+    }
+}
+
+// Upsweep: items bottom-up from level top = (edge ? hi : hi - 1) to level lo, item g of level
+// l being node 3 * 2^l + g - 2^(top+1).
+template <typename T, int KM>
+__global__ void __launch_bounds__(kWsThreads, 8) k_up_warp(Op<T> op, Vec<T> vec, WarpSweep ws)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = op.k, kx = op.kx, mp = op.mp, vs = vec.vs;
+    const int top = ws.edge ? ws.hi : ws.hi - 1;
+    if (top < ws.lo) return;
+    const int64_t span = int64_t(2) << top;  // 2^(top+1)
+    const int64_t total = span - (int64_t(1) << ws.lo);
+    for (;;) {
+        const int64_t g0 = ws_ticket(ws.ticket) * kWsChunk;
+        if (g0 >= total) return;
+        const int64_t g1 = g0 + kWsChunk < total ? g0 + kWsChunk : total;
+        for (int64_t g = g0; g < g1; ++g) {
+            const int l = 63 - __clzll(static_cast<unsigned long long>(span - g - 1));
+            const int64_t node = (int64_t(3) << l) + g - span;
+            T p[KM];
+            if (ws.edge && l == ws.hi) {
+                // leaf projection: lane i takes rows i, i + 32, ... of U_t (column i of U_t^T)
+                const int64_t t = node - op.first_leaf;
+                const int R = op.leaf_lo[t + 1] - op.leaf_lo[t];
+                const T *__restrict__ x = vec.xt + t * mp * vs;
+                const T *__restrict__ ut = op.Ut + t * kx * mp;
+#pragma unroll
+                for (int j = 0; j < KM; ++j) p[j] = T(0);
+                for (int rb = 0; rb < mp; rb += 64) {  // two row blocks per round of loads
+                    const int i0 = rb + lane, i1 = rb + 32 + lane;
+                    const T x0 = i0 < R ? x[i0] : T(0), x1 = i1 < R ? x[i1] : T(0);
+                    T u0[KM], u1[KM];
+#pragma unroll
+                    for (int j = 0; j < KM; ++j) {
+                        u0[j] = j < k && i0 < mp ? __ldg(ut + j * mp + i0) : T(0);
+                        u1[j] = j < k && i1 < mp ? __ldg(ut + j * mp + i1) : T(0);
+                    }
+#pragma unroll
+                    for (int j = 0; j < KM; ++j) p[j] = fma(u1[j], x1, fma(u0[j], x0, p[j]));
+                }
+            } else {
+                // transfers: xhat_p = sum over the two children of E_c^T xhat_c; lane j takes
+                // row j of each child's tile, loaded before the children are waited for
+                const int64_t c0 = 2 * node;
+                T e0[KM], e1[KM];
+                ws_load_row<T, KM>(op.E + c0 * k * kx, k, kx, e0);
+                ws_load_row<T, KM>(op.E + (c0 + 1) * k * kx, k, kx, e1);
+                const bool wait = l + 1 <= top;  // the children are items of this launch
+                if (wait && !ws_wait(ws.flag + c0, ws.abort, vec.err)) return;
+                if (wait && !ws_wait(ws.flag + c0 + 1, ws.abort, vec.err)) return;
+                const T x0 = lane < k ? __ldcg(vec.xh + c0 * kx * vs + lane) : T(0);
+                const T x1 = lane < k ? __ldcg(vec.xh + (c0 + 1) * kx * vs + lane) : T(0);
+#pragma unroll
+                for (int j = 0; j < KM; ++j) p[j] = fma(e1[j], x1, e0[j] * x0);
+            }
+            const T r = ws_reduce<T, KM>(p);
+            if (lane < k) vec.xh[node * kx * vs + lane] = r;
+            if (l > ws.lo) ws_publish(ws.flag + node);
+        }
+    }
+}
+
+// Downsweep: items top-down, item g being heap node 2^lo + g (level lo .. hi).
+template <typename T, int KM>
+__global__ void __launch_bounds__(kWsThreads, 8) k_down_warp(Op<T> op, Vec<T> vec, WarpSweep ws)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = op.k, kx = op.kx, mp = op.mp, vs = vec.vs;
+    if (ws.hi < ws.lo) return;
+    const int64_t first = int64_t(1) << ws.lo;
+    const int64_t total = (int64_t(2) << ws.hi) - first;
+    for (;;) {
+        const int64_t g0 = ws_ticket(ws.ticket) * kWsChunk;
+        if (g0 >= total) return;
+        const int64_t g1 = g0 + kWsChunk < total ? g0 + kWsChunk : total;
+        for (int64_t g = g0; g < g1; ++g) {
+            const int64_t node = first + g;
+            const int l = 63 - __clzll(static_cast<unsigned long long>(node));
+            const bool leaf = ws.edge && l == ws.hi;
+            // everything that does not depend on the parent is loaded first
+            const T own = lane < k ? vec.yh[node * kx * vs + lane] : T(0);  // the node's coupling row
+            T e[KM];
+            if (l >= 1) ws_load_row<T, KM>(op.Et + node * k * kx, k, kx, e);
+            int64_t t = 0;
+            int r0 = 0, R = 0;
+            T u0[KM], u1[KM], d0 = T(0), d1 = T(0);
+            int perm0 = 0, perm1 = 0;
+            if (leaf) {  // the leaf's basis rows, dense partial result and output rows
+                t = node - op.first_leaf;
+                r0 = op.leaf_lo[t];
+                R = op.leaf_lo[t + 1] - r0;
+                const T *__restrict__ ut = op.Ut + t * kx * mp;
+                const int i0 = lane, i1 = 32 + lane;
+#pragma unroll
+                for (int j = 0; j < KM; ++j) {
+                    u0[j] = j < k && i0 < mp ? __ldg(ut + j * mp + i0) : T(0);
+                    u1[j] = j < k && i1 < mp ? __ldg(ut + j * mp + i1) : T(0);
+                }
+                const T *__restrict__ yd = vec.yd + t * mp * vs;
+                if (i0 < R) d0 = yd[i0], perm0 = op.perm[r0 + i0];
+                if (i1 < R) d1 = yd[i1], perm1 = op.perm[r0 + i1];
+            }
+            T acc = T(0);
+            if (l >= 1) {
+                const int64_t p = node >> 1;
+                // a parent of level lo - 1 was completed by an earlier launch
+                if (l - 1 >= ws.lo && !ws_wait(ws.flag + p, ws.abort, vec.err)) return;
+                const T yp = lane < k ? __ldcg(vec.yh + p * kx * vs + lane) : T(0);
+                T q[KM];
+#pragma unroll
+                for (int j = 0; j < KM; ++j) q[j] = e[j] * yp;
+                acc = ws_reduce<T, KM>(q);
+            }
+            acc += own;
+            if (!leaf) {
+                if (lane < k) vec.yh[node * kx * vs + lane] = acc;
+                if (l < ws.hi) ws_publish(ws.flag + node);
+                continue;
+            }
+            // leaf: y_i = sum_nu U_t[i][nu] yhat_nu + (A_de x)_i for the rows i = lane, lane + 32,
+            // then the rows beyond 64 (leaves of up to 128 points) with loads of their own
+            T y0 = T(0), y1 = T(0);
+#pragma unroll
+            for (int j = 0; j < KM; ++j) {
+                const T a = __shfl_sync(0xffffffffu, acc, j);
+                y0 = fma(u0[j], a, y0);
+                y1 = fma(u1[j], a, y1);
+            }
+            if (lane < R) {
+                const T v = y0 + d0;
+                T *dst = vec.Y + perm0;
+                *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
+            }
+            if (32 + lane < R) {
+                const T v = y1 + d1;
+                T *dst = vec.Y + perm1;
+                *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
+            }
+            const T *__restrict__ ut = op.Ut + t * kx * mp;
+            const T *__restrict__ yd = vec.yd + t * mp * vs;
+            for (int ib = 64; ib < R; ib += 32) {  // uniform over the warp
+                const int i = ib + lane;
+                T y = T(0);
+                for (int j = 0; j < k; ++j) {
+                    const T a = __shfl_sync(0xffffffffu, acc, j);
+                    if (i < mp) y = fma(__ldg(ut + j * mp + i), a, y);
+                }
+                if (i < R) {
+                    const T v = y + yd[i];
+                    T *dst = vec.Y + op.perm[r0 + i];
+                    *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
+                }
+            }
+        }
+    }
+}
+
+// Block rows of small coupling blocks (k <= 32), one vector (Sec. 3.2, Alg 4): one warp per
+// scheduling chunk of whole rows (chunks[c] = (first descriptor << 16) | count), taken from
+// the ticket vec.tickets[ticket_index]; lane j takes row j of each block's tile S_ts^T ([j][o],
+// ld kx) and entry j of xhat_s, so a row's partial vectors need one reduce-scatter at its end.
+// The tiles of NB blocks are loaded at once (NB x KM values per lane), and the next chunk's
+// ticket is drawn while the current one is processed. An empty row (kZero) is stored as zeros.
+// Rows are independent: no warp waits for another.
+template <typename T, int KM>
+__global__ void __launch_bounds__(kWsThreads, 8)
+    k_rows_warp(Op<T> op, Vec<T> vec, const StreamDesc *__restrict__ desc, const int64_t *__restrict__ chunks,
+                int64_t nchunks, int ticket_index)
+{
+    constexpr int NB = (64 * 4 / int(sizeof(T))) / KM;  // blocks in flight: 64 registers of tiles
+    const int lane = threadIdx.x & 31;
+    const int k = op.k, kx = op.kx, vs = vec.vs;
+    int *ticket = vec.tickets + ticket_index;
+    int64_t c = ws_ticket(ticket);
+    T p[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) p[j] = T(0);
+    while (c < nchunks) {
+        int next = 0;
+        if (lane == 0) next = atomicAdd(ticket, 1);  // used after this chunk
+        const int64_t rec = chunks[c];
+        const int64_t b0 = rec >> 16;
+        const int cnt = int(rec & 0xffff);
+        for (int gb = 0; gb < cnt; gb += 32) {
+            const int n = cnt - gb < 32 ? cnt - gb : 32;
+            // lane i holds descriptor gb + i of the chunk
+            uint64_t src = 0;
+            int xn = 0, on = 0, fl = 0;
+            if (lane < n) {
+                const StreamDesc d = desc[b0 + gb + lane];
+                src = d.src;
+                xn = d.x_node;
+                on = d.out_node;
+                fl = d.flags;
+            }
+            for (int b = 0; b < n; b += NB) {
+                T t[NB][KM], xv[NB];
+                int fb[NB], ob[NB];
+#pragma unroll
+                for (int u = 0; u < NB; ++u) {
+                    const int bi = b + u < n ? b + u : n - 1;
+                    const uint64_t sb = __shfl_sync(0xffffffffu, src, bi);
+                    const int xb = __shfl_sync(0xffffffffu, xn, bi);
+                    fb[u] = __shfl_sync(0xffffffffu, fl, bi);
+                    ob[u] = __shfl_sync(0xffffffffu, on, bi);
+                    const bool live = b + u < n && !(fb[u] & kZero);
+                    ws_load_row<T, KM>(reinterpret_cast<const T *>(op.vals + sb), live ? k : 0, kx, t[u]);
+                    xv[u] = live && lane < k ? vec.xh[int64_t(xb) * kx * vs + lane] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < NB; ++u) {
+                    if (b + u >= n) break;
+#pragma unroll
+                    for (int j = 0; j < KM; ++j) p[j] = fma(t[u][j], xv[u], p[j]);
+                    if (fb[u] & kLast) {
+                        const T r = ws_reduce<T, KM>(p);
+                        if (lane < k) vec.yh[int64_t(ob[u]) * kx * vs + lane] = r;
+#pragma unroll
+                        for (int j = 0; j < KM; ++j) p[j] = T(0);
+                    }
+                }
+            }
+        }
+        c = __shfl_sync(0xffffffffu, next, 0);
+    }
+}
+
+}  // namespace h2s

@@ -300,3 +300,31 @@ def test_small_ranks_stream_dense_rows_apart(built, prec):
     gpu_matvec(op64, si.gaussian_vectors(len(pts64), 1, 42), prec)
     _, launches, _ = h2.h2_get_timing(op64.handle)
     assert launches[1] == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,order,leaf", [(2, 3, 128), (3, 3, 100)])
+def test_small_rank_warp_kernels_with_large_leaves(prec, dim, order, leaf):
+    """Ranks of at most 32 sweep the tree with one warp per node and stream the coupling rows
+    with one warp per chunk of rows at one vector; leaves of more than 64 points take their
+    rows beyond 64 in a second round. Each column against the oracle with alpha and beta, and
+    the 2-vector product (the staged kernels) against the oracle too."""
+    pts = si.uniform_cloud(9000 if dim == 2 else 6000, dim, 7 + dim)
+    ker = ("exp", 0.1 if dim == 2 else 0.2, 0, 0)
+    orc = oracle.OracleH2(pts, ker, leaf, order, 0.8)
+    op = h2.H2Operator(pts, ker, leaf, order, 0.8).upload(prec)
+    try:
+        assert op.info.rank == order ** dim and op.info.rank <= 32
+        X = si.gaussian_vectors(len(pts), 2, 21)
+        Y0 = si.gaussian_vectors(len(pts), 2, 22)
+        for v in range(2):
+            got = gpu_matvec(op, X[:, v:v + 1], prec, 0.75, -1.25, Y0[:, v:v + 1])
+            assert np.all(np.isfinite(got))
+            assert relerr(got, orc.matvec(X[:, v:v + 1], 0.75, -1.25, Y0[:, v:v + 1])) <= TOL[prec]
+        got = gpu_matvec(op, X[:, :1], prec, 2.0, 0.0)  # beta = 0: the NaN output is not read
+        assert np.all(np.isfinite(got)) and relerr(got, orc.matvec(X[:, :1], 2.0)) <= TOL[prec]
+        both = gpu_matvec(op, X, prec, 0.75, -1.25, Y0)
+        assert relerr(both, orc.matvec(X, 0.75, -1.25, Y0)) <= TOL[prec]
+        assert np.array_equal(gpu_matvec(op, X[:, :1], prec, 2.0, 0.0), got)  # deterministic
+    finally:
+        op.close()
