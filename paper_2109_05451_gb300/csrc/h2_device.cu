@@ -369,9 +369,12 @@ void launch_warp_sweep_km(bool up, const h2_op &op, const h2s::Op<T> &o, const h
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_down_warp<T, KM>, kWsThreads, 0);
         occ = std::max(1, std::min(a, b));
     }
-    const int top = up ? (edge ? hi : hi - 1) : hi;
-    if (top < lo) return;
-    const int64_t items = (int64_t(2) << top) - (int64_t(1) << lo);
+    // item levels lo .. last: the upsweep's last level is hi - 1 (with edge, hi = q >= 1, those
+    // items project their two leaves; a one-node tree has the leaf as its only item), the
+    // downsweep's hi
+    const int last = up ? (edge && hi == 0 ? 0 : hi - 1) : hi;
+    if (last < lo) return;
+    const int64_t items = (int64_t(2) << last) - (int64_t(1) << lo);
     const int64_t warps = (items + kWsChunk - 1) / kWsChunk;
     const int64_t ctas = std::min<int64_t>((warps + kWsWarps - 1) / kWsWarps, int64_t(dv.num_sms) * occ);
     const WarpSweep ws{w.tickets + ticket, w.tickets + 8, w.flags + (up ? 0 : op.nnodes + 1), lo, hi, edge};

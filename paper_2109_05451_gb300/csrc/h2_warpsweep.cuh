@@ -159,14 +159,45 @@ __device__ __forceinline__ void ws_load_row(const T *__restrict__ tile, int k, i
     }
 }
 
-// Upsweep: items bottom-up from level top = (edge ? hi : hi - 1) to level lo, item g of level
-// l being node 3 * 2^l + g - 2^(top+1).
+// Leaf projection xhat_t = U_t^T x_t (Sec. 3.1): lane i takes rows i, i + 32, ... of U_t
+// (column i of U_t^T, ld mp); returns entry o of xhat_t in lane o (o < KM, lane mod KM).
+template <typename T, int KM>
+__device__ __forceinline__ T ws_project_leaf(const Op<T> &op, const Vec<T> &vec, int64_t t)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = op.k, kx = op.kx, mp = op.mp;
+    const int R = op.leaf_lo[t + 1] - op.leaf_lo[t];
+    const T *__restrict__ x = vec.xt + t * mp * vec.vs;
+    const T *__restrict__ ut = op.Ut + t * kx * mp;
+    T p[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) p[j] = T(0);
+    for (int rb = 0; rb < mp; rb += 64) {  // two row blocks per round of loads
+        const int i0 = rb + lane, i1 = rb + 32 + lane;
+        const T x0 = i0 < R ? x[i0] : T(0), x1 = i1 < R ? x[i1] : T(0);
+        T u0[KM], u1[KM];
+#pragma unroll
+        for (int j = 0; j < KM; ++j) {
+            u0[j] = j < k && i0 < mp ? __ldg(ut + j * mp + i0) : T(0);
+            u1[j] = j < k && i1 < mp ? __ldg(ut + j * mp + i1) : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < KM; ++j) p[j] = fma(u1[j], x1, fma(u0[j], x0, p[j]));
+    }
+    return ws_reduce<T, KM>(p);
+}
+
+// Upsweep: items bottom-up from level top to level lo, item g of level l being node
+// 3 * 2^l + g - 2^(top+1). top = hi - 1; with edge (hi = q) the items of level q - 1 project
+// their two leaves first (their leaf vectors are written for the block stream but need no
+// flags). A tree of one node (q = 0) has the leaf as its only item.
 template <typename T, int KM>
 __global__ void __launch_bounds__(kWsThreads, 8) k_up_warp(Op<T> op, Vec<T> vec, WarpSweep ws)
 {
     const int lane = threadIdx.x & 31;
-    const int k = op.k, kx = op.kx, mp = op.mp, vs = vec.vs;
-    const int top = ws.edge ? ws.hi : ws.hi - 1;
+    const int k = op.k, kx = op.kx, vs = vec.vs;
+    const bool root_leaf = ws.edge && ws.hi == 0;
+    const int top = root_leaf ? 0 : ws.hi - 1;
     if (top < ws.lo) return;
     const int64_t span = int64_t(2) << top;  // 2^(top+1)
     const int64_t total = span - (int64_t(1) << ws.lo);
@@ -177,43 +208,36 @@ __global__ void __launch_bounds__(kWsThreads, 8) k_up_warp(Op<T> op, Vec<T> vec,
         for (int64_t g = g0; g < g1; ++g) {
             const int l = 63 - __clzll(static_cast<unsigned long long>(span - g - 1));
             const int64_t node = (int64_t(3) << l) + g - span;
-            T p[KM];
-            if (ws.edge && l == ws.hi) {
-                // leaf projection: lane i takes rows i, i + 32, ... of U_t (column i of U_t^T)
-                const int64_t t = node - op.first_leaf;
-                const int R = op.leaf_lo[t + 1] - op.leaf_lo[t];
-                const T *__restrict__ x = vec.xt + t * mp * vs;
-                const T *__restrict__ ut = op.Ut + t * kx * mp;
-#pragma unroll
-                for (int j = 0; j < KM; ++j) p[j] = T(0);
-                for (int rb = 0; rb < mp; rb += 64) {  // two row blocks per round of loads
-                    const int i0 = rb + lane, i1 = rb + 32 + lane;
-                    const T x0 = i0 < R ? x[i0] : T(0), x1 = i1 < R ? x[i1] : T(0);
-                    T u0[KM], u1[KM];
-#pragma unroll
-                    for (int j = 0; j < KM; ++j) {
-                        u0[j] = j < k && i0 < mp ? __ldg(ut + j * mp + i0) : T(0);
-                        u1[j] = j < k && i1 < mp ? __ldg(ut + j * mp + i1) : T(0);
-                    }
-#pragma unroll
-                    for (int j = 0; j < KM; ++j) p[j] = fma(u1[j], x1, fma(u0[j], x0, p[j]));
-                }
+            T r;
+            if (root_leaf) {
+                r = ws_project_leaf<T, KM>(op, vec, node - op.first_leaf);
             } else {
                 // transfers: xhat_p = sum over the two children of E_c^T xhat_c; lane j takes
-                // row j of each child's tile, loaded before the children are waited for
+                // row j of each child's tile and entry j of its vector
                 const int64_t c0 = 2 * node;
-                T e0[KM], e1[KM];
-                ws_load_row<T, KM>(op.E + c0 * k * kx, k, kx, e0);
-                ws_load_row<T, KM>(op.E + (c0 + 1) * k * kx, k, kx, e1);
-                const bool wait = l + 1 <= top;  // the children are items of this launch
-                if (wait && !ws_wait(ws.flag + c0, ws.abort, vec.err)) return;
-                if (wait && !ws_wait(ws.flag + c0 + 1, ws.abort, vec.err)) return;
-                const T x0 = lane < k ? __ldcg(vec.xh + c0 * kx * vs + lane) : T(0);
-                const T x1 = lane < k ? __ldcg(vec.xh + (c0 + 1) * kx * vs + lane) : T(0);
+                T e0[KM], e1[KM], x0, x1;
+                if (ws.edge && l == top) {
+                    x0 = ws_project_leaf<T, KM>(op, vec, c0 - op.first_leaf);
+                    if (lane < k) vec.xh[c0 * kx * vs + lane] = x0;
+                    x1 = ws_project_leaf<T, KM>(op, vec, c0 + 1 - op.first_leaf);
+                    if (lane < k) vec.xh[(c0 + 1) * kx * vs + lane] = x1;
+                    ws_load_row<T, KM>(op.E + c0 * k * kx, k, kx, e0);  // zero in lanes >= k
+                    ws_load_row<T, KM>(op.E + (c0 + 1) * k * kx, k, kx, e1);
+                } else {
+                    // the tiles are loaded before the children are waited for
+                    ws_load_row<T, KM>(op.E + c0 * k * kx, k, kx, e0);
+                    ws_load_row<T, KM>(op.E + (c0 + 1) * k * kx, k, kx, e1);
+                    const bool wait = l + 1 <= top;  // the children are items of this launch
+                    if (wait && !ws_wait(ws.flag + c0, ws.abort, vec.err)) return;
+                    if (wait && !ws_wait(ws.flag + c0 + 1, ws.abort, vec.err)) return;
+                    x0 = lane < k ? __ldcg(vec.xh + c0 * kx * vs + lane) : T(0);
+                    x1 = lane < k ? __ldcg(vec.xh + (c0 + 1) * kx * vs + lane) : T(0);
+                }
+                T p[KM];
 #pragma unroll
                 for (int j = 0; j < KM; ++j) p[j] = fma(e1[j], x1, e0[j] * x0);
+                r = ws_reduce<T, KM>(p);
             }
-            const T r = ws_reduce<T, KM>(p);
             if (lane < k) vec.xh[node * kx * vs + lane] = r;
             if (l > ws.lo) ws_publish(ws.flag + node);
         }
