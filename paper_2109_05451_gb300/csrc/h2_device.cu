@@ -359,7 +359,7 @@ void launch_mf(const h2_op &op, const h2s::Op<float> &o, const h2s::Vec<float> &
 
 template <typename T, int KM>
 void launch_warp_sweep_km(bool up, const h2_op &op, const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_device &dv,
-                          const Workspace &w, int lo, int hi, int edge, int ticket, cudaStream_t st)
+                          const Workspace &w, int lo, int hi, int ticket, cudaStream_t st)
 {
     using namespace h2s;
     static int occ = 0;  // resident CTAs per SM (per element type and partial width)
@@ -369,19 +369,41 @@ void launch_warp_sweep_km(bool up, const h2_op &op, const h2s::Op<T> &o, const h
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_down_warp<T, KM>, kWsThreads, 0);
         occ = std::max(1, std::min(a, b));
     }
-    // item levels lo .. last: the upsweep's last level is hi - 1 (with edge, hi = q >= 1, those
-    // items project their two leaves; a one-node tree has the leaf as its only item), the
-    // downsweep's hi
-    const int last = up ? (edge && hi == 0 ? 0 : hi - 1) : hi;
+    // item levels lo .. last: the upsweep's last level is hi - 1, the downsweep's hi
+    const int last = up ? hi - 1 : hi;
     if (last < lo) return;
     const int64_t items = (int64_t(2) << last) - (int64_t(1) << lo);
     const int64_t warps = (items + kWsChunk - 1) / kWsChunk;
     const int64_t ctas = std::min<int64_t>((warps + kWsWarps - 1) / kWsWarps, int64_t(dv.num_sms) * occ);
-    const WarpSweep ws{w.tickets + ticket, w.tickets + 8, w.flags + (up ? 0 : op.nnodes + 1), lo, hi, edge};
+    const WarpSweep ws{w.tickets + ticket, w.tickets + 8, w.flags + (up ? 0 : op.nnodes + 1), lo, hi};
     if (up)
         k_up_warp<T, KM><<<unsigned(ctas), kWsThreads, 0, st>>>(o, v, ws);
     else
         k_down_warp<T, KM><<<unsigned(ctas), kWsThreads, 0, st>>>(o, v, ws);
+}
+
+// Bottom subtrees of small ranks, one vector: one CTA per subtree of depth L rooted at level
+// Lr (k_up_cta / k_down_cta).
+template <typename T, int KM>
+void launch_cta_sweep_km(bool up, const h2s::Op<T> &o, const h2s::Vec<T> &v, int Lr, int L, cudaStream_t st)
+{
+    using namespace h2s;
+    const size_t smem = cta_smem_bytes<T, KM>(L);
+    const unsigned grid = unsigned(int64_t(1) << Lr);
+    if (up)
+        k_up_cta<T, KM><<<grid, kCtaThreads, smem, st>>>(o, v, Lr, L);
+    else
+        k_down_cta<T, KM><<<grid, kCtaThreads, smem, st>>>(o, v, Lr, L);
+}
+
+template <typename T>
+void launch_cta_sweep(bool up, const h2_op &op, const h2s::Op<T> &o, const h2s::Vec<T> &v, int Lr, int L,
+                      cudaStream_t st)
+{
+    if (op.k <= 16)
+        launch_cta_sweep_km<T, 16>(up, o, v, Lr, L, st);
+    else
+        launch_cta_sweep_km<T, 32>(up, o, v, Lr, L, st);
 }
 
 // Coupling rows of small ranks, one vector: one warp per chunk of rows (k_rows_warp) on the
@@ -389,7 +411,7 @@ void launch_warp_sweep_km(bool up, const h2_op &op, const h2s::Op<T> &o, const h
 template <typename T, int KM>
 void launch_rows_warp_km(const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_device &dv,
                          const h2s::StreamDesc *desc, const int64_t *chunks, int64_t nchunks, int ticket,
-                         cudaStream_t st)
+                         bool side, cudaStream_t st)
 {
     using namespace h2s;
     static int occ = 0;
@@ -397,35 +419,37 @@ void launch_rows_warp_km(const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_dev
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_warp<T, KM>, kWsThreads, 0);
         occ = std::max(1, occ);
     }
-    const int64_t ctas = std::min<int64_t>((nchunks + kWsWarps - 1) / kWsWarps, int64_t(dv.num_sms) * occ);
+    // a persistent launch that fills every register file would keep the side stream's
+    // kernels (the upper levels) from starting until it ends: `side` leaves them one slot
+    const int per_sm = side ? std::max(1, occ - 1) : occ;
+    const int64_t ctas = std::min<int64_t>((nchunks + kWsWarps - 1) / kWsWarps, int64_t(dv.num_sms) * per_sm);
     k_rows_warp<T, KM><<<unsigned(std::max<int64_t>(1, ctas)), kWsThreads, 0, st>>>(o, v, desc, chunks, nchunks,
                                                                                    ticket);
 }
 
 template <typename T>
 void launch_rows_warp(const h2_op &op, const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_device &dv,
-                      const h2s::StreamDesc *desc, const int64_t *chunks, int64_t nchunks, int ticket,
+                      const h2s::StreamDesc *desc, const int64_t *chunks, int64_t nchunks, int ticket, bool side,
                       cudaStream_t st)
 {
     if (op.k <= 16)
-        launch_rows_warp_km<T, 16>(o, v, dv, desc, chunks, nchunks, ticket, st);
+        launch_rows_warp_km<T, 16>(o, v, dv, desc, chunks, nchunks, ticket, side, st);
     else
-        launch_rows_warp_km<T, 32>(o, v, dv, desc, chunks, nchunks, ticket, st);
+        launch_rows_warp_km<T, 32>(o, v, dv, desc, chunks, nchunks, ticket, side, st);
 }
 
-// One launch of a warp-per-node sweep (ranks <= 32, one vector; h2_warpsweep.cuh): enough
-// warps for the launch's tickets, at most the CTAs resident on the device. Upsweep: levels
-// hi-1 .. lo from level hi (with edge, hi = q and the leaf projections); downsweep: levels
-// lo .. hi (with edge, hi = q and the leaf expansion and epilogue). `ticket` is the launch's
-// scheduling word.
+// One launch of a flag-ordered warp sweep of the upper levels (ranks <= 32, one vector;
+// h2_warpsweep.cuh): enough warps for the launch's tickets, at most the CTAs resident on the
+// device. Upsweep: levels hi-1 .. lo from level hi; downsweep: levels lo .. hi. `ticket` is
+// the launch's scheduling word.
 template <typename T>
 void launch_warp_sweep(bool up, const h2_op &op, const h2s::Op<T> &o, const h2s::Vec<T> &v, const h2_device &dv,
-                       const Workspace &w, int lo, int hi, int edge, int ticket, cudaStream_t st)
+                       const Workspace &w, int lo, int hi, int ticket, cudaStream_t st)
 {
     if (op.k <= 16)
-        launch_warp_sweep_km<T, 16>(up, op, o, v, dv, w, lo, hi, edge, ticket, st);
+        launch_warp_sweep_km<T, 16>(up, op, o, v, dv, w, lo, hi, ticket, st);
     else
-        launch_warp_sweep_km<T, 32>(up, op, o, v, dv, w, lo, hi, edge, ticket, st);
+        launch_warp_sweep_km<T, 32>(up, op, o, v, dv, w, lo, hi, ticket, st);
 }
 
 template <typename T, int NVMAX>
@@ -498,7 +522,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
         h2n::Range r("upsweep: leaf subtrees");
         k_gather<T><<<unsigned(std::min<int64_t>(op.nleaves(), 65535)), 128, 0, st>>>(o, v);
         if (wsw)
-            launch_warp_sweep<T>(true, op, o, v, dv, w, Lb, op.q, 1, 4, st);
+            launch_cta_sweep<T>(true, op, o, v, Lb, Lbot, st);
         else
             k_up_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
     }
@@ -516,7 +540,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
         h2n::Range r("upsweep: upper levels");
         eb = dv.begin(side);
         if (wsw) {
-            launch_warp_sweep<T>(true, op, o, v, dv, w, 0, Lb, 0, 5, side);
+            launch_warp_sweep<T>(true, op, o, v, dv, w, 0, Lb, 5, side);
             ++top_launches;
             return;
         }
@@ -542,7 +566,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     if (dv.n_chunks_bottom > 0) {
         h2n::Range r("tree multiply + dense: lower levels");
         if (wsw && dsplit && !mf) {  // the bottom list holds coupling rows only
-            launch_rows_warp<T>(op, o, v, dv, dv.desc_bottom, dv.chunks_bottom, dv.n_chunks_bottom, 0, st);
+            launch_rows_warp<T>(op, o, v, dv, dv.desc_bottom, dv.chunks_bottom, dv.n_chunks_bottom, 0, top, st);
         } else if constexpr (sizeof(T) == 4 && NVMAX <= kChunk) {
             if (mf) {
                 launch_mf<NVMAX>(op, o, v, dv.mfa, p_bot, sm_bot, grid_bot, dv.desc_bottom, dv.chunks_bottom,
@@ -571,14 +595,14 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
         h2n::Range r("tree multiply + downsweep: upper levels");
         if (dv.n_chunks_top > 0) {
             if (wsw)
-                launch_rows_warp<T>(op, o, v, dv, dv.desc_top, dv.chunks_top, dv.n_chunks_top, 1, sb);
+                launch_rows_warp<T>(op, o, v, dv, dv.desc_top, dv.chunks_top, dv.n_chunks_top, 1, false, sb);
             else
                 k_stream<T, NVMAX><<<dv.grid_top, kThreads, sm_top, sb>>>(o, v, p_top, dv.desc_top, dv.chunks_top,
                                                                           dv.n_chunks_top, 1);
             ++top_launches;
         }
         if (wsw) {
-            launch_warp_sweep<T>(false, op, o, v, dv, w, 0, Lb - 1, 0, 6, sb);
+            launch_warp_sweep<T>(false, op, o, v, dv, w, 0, Lb - 1, 6, sb);
             ++top_launches;
         } else {
             for (int lr = 0; lr <= Lb - 1;) {
@@ -599,7 +623,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     {
         h2n::Range r("downsweep: leaf subtrees");
         if (wsw)
-            launch_warp_sweep<T>(false, op, o, v, dv, w, Lb, op.q, 1, 7, st);
+            launch_cta_sweep<T>(false, op, o, v, Lb, Lbot, st);
         else
             k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
     }

@@ -1,33 +1,38 @@
 // h2_warpsweep.cuh -- sweeps and coupling rows of operators of small rank (k <= 32), one
-// vector: one warp per tree node or per chunk of block rows.
+// vector.
 //
 // With k <= 32 a node's coefficient vector fits one warp and a transfer or leaf-basis tile is
-// a few hundred bytes to a few KB. The staged sweeps of h2_stream.cuh (one tile per pipeline
-// stage, reductions across four consumer warps) are then bound by their per-tile latency, not
-// by HBM. Here each warp takes tree nodes from a ticket counter in dependency order and reads
-// its tiles straight from global memory:
+// a few hundred bytes to a few KB. The staged kernels of h2_stream.cuh (one tile per pipeline
+// stage, reductions across four consumer warps, one producer thread) are then bound by their
+// per-tile latency, not by HBM. The kernels here work at warp granularity and read their tiles
+// straight from global memory:
 //
-//   k_up_warp    xhat^q_t = U_t^T x_t at the leaves (Sec. 3.1), then
-//                xhat^{l-1}_p = sum_c E_c^T xhat^l_c (Alg 1), level by level upwards;
-//   k_down_warp  yhat^l_c = E_c yhat^{l-1}_p + yhat^l_c (the node's own coupling row), level
-//                by level downwards, and at the leaves y_t = U_t yhat^q_t + (A_de x)_t,
-//                Y[perm] = alpha y + beta Y (Sec. 3.3, Alg 6).
+//   k_up_cta     bottom subtrees, one CTA of eight warps each: leaf projections
+//                xhat^q_t = U_t^T x_t (Sec. 3.1), then xhat^{l-1}_p = sum_c E_c^T xhat^l_c
+//                (Alg 1) level by level, the vectors exchanged through shared memory;
+//   k_down_cta   bottom subtrees: yhat^l_c = E_c yhat^{l-1}_p + yhat^l_c (the node's own
+//                coupling row) level by level, then y_t = U_t yhat^q_t + (A_de x)_t and
+//                Y[perm] = alpha y + beta Y at the leaves (Sec. 3.3, Alg 6);
+//   k_up_warp,   the upper levels (few nodes per level), one warp per node, ordered by
+//   k_down_warp  flags in global memory;
+//   k_rows_warp  coupling rows (Sec. 3.2, Alg 4), one warp per chunk of rows.
 //
-// Every product of a node is formed the same way: each lane accumulates a partial vector of
-// KM (16 or 32 >= k) outputs from the tile entries it loaded (lane j takes row j of a
-// transfer tile, lane i row i of the leaf basis), and one reduce-scatter over the warp (31
-// shuffles) leaves output o in lane o. A node issues all its tile loads before it waits for
-// the nodes it reads, so one memory latency, not one per tile row, lies on each dependency.
-// Tiles are read in the layouts of h2_stream.cuh: U_t^T as [nu][i] (ld mp), E_c and E_c^T
-// as [j][o] (ld kx), where j is the input and o the output coefficient.
+// Every product of a node or block is formed the same way: each lane accumulates a partial
+// vector of KM (16 or 32 >= k) outputs from the tile entries it loaded (lane j takes row j of
+// a transfer or coupling tile, lane i row i of the leaf basis), and one reduce-scatter over
+// the warp (31 shuffles) leaves output o in lane o. A node issues its tile loads before it
+// waits for the nodes it reads, so one memory latency, not one per tile row, lies on each
+// dependency. Tiles are read in the layouts of h2_stream.cuh: U_t^T as [nu][i] (ld mp), E_c,
+// E_c^T and S_ts^T as [j][o] (ld kx), where j is the input and o the output coefficient.
 //
-// Ordering: a node's work item comes after the items of the nodes it reads (its children in
-// the upsweep, its parent in the downsweep), and a warp takes a ticket only while it runs, so
-// each wait is for a warp that is already running and that itself waits only on earlier
-// items; the waits end. Each one is still bounded (about a second): a wait that runs out
-// raises the launch's abort word and the operator's error flag, and every warp then returns.
-// A node publishes its vector by a release store of its flag after its lanes' stores and a
-// fence; a reader acquires the flag in every lane and reads the vector through L2.
+// Ordering of the flag-based sweeps: a node's work item comes after the items of the nodes it
+// reads (its children in the upsweep, its parent in the downsweep), and a warp takes a ticket
+// only while it runs, so each wait is for a warp that is already running and that itself
+// waits only on earlier items; the waits end. Each one is still bounded (about a second): a
+// wait that runs out raises the launch's abort word and the operator's error flag, and every
+// warp then returns. A node publishes its vector by a release store of its flag after its
+// lanes' stores and a fence; a reader acquires the flag in every lane and reads the vector
+// through L2.
 #pragma once
 
 #include <cstdint>
@@ -49,9 +54,8 @@ struct WarpSweep {
     int *ticket;  // this launch's work counter (zeroed by the gather)
     int *abort;   // raised by a wait that ran out (zeroed by the gather)
     int *flag;    // per heap node: set once the node's vector is final (zeroed by the gather)
-    int lo, hi;   // upsweep: levels hi-1 .. lo from the inputs of level hi (with edge, level hi
-                  // = q is computed too, from the leaf projections); downsweep: levels lo .. hi
-    int edge;     // upsweep: leaf projections; downsweep: leaf expansion and epilogue
+    int lo, hi;   // upsweep: levels hi-1 .. lo from the vectors of level hi; downsweep: levels
+                  // lo .. hi from the totals of level lo - 1
 };
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p)
@@ -187,17 +191,14 @@ __device__ __forceinline__ T ws_project_leaf(const Op<T> &op, const Vec<T> &vec,
     return ws_reduce<T, KM>(p);
 }
 
-// Upsweep: items bottom-up from level top to level lo, item g of level l being node
-// 3 * 2^l + g - 2^(top+1). top = hi - 1; with edge (hi = q) the items of level q - 1 project
-// their two leaves first (their leaf vectors are written for the block stream but need no
-// flags). A tree of one node (q = 0) has the leaf as its only item.
+// Upsweep of the levels hi - 1 .. lo from the vectors of level hi (computed by an earlier
+// launch): items bottom-up, item g of level l being node 3 * 2^l + g - 2^hi.
 template <typename T, int KM>
 __global__ void __launch_bounds__(kWsThreads, 8) k_up_warp(Op<T> op, Vec<T> vec, WarpSweep ws)
 {
     const int lane = threadIdx.x & 31;
     const int k = op.k, kx = op.kx, vs = vec.vs;
-    const bool root_leaf = ws.edge && ws.hi == 0;
-    const int top = root_leaf ? 0 : ws.hi - 1;
+    const int top = ws.hi - 1;
     if (top < ws.lo) return;
     const int64_t span = int64_t(2) << top;  // 2^(top+1)
     const int64_t total = span - (int64_t(1) << ws.lo);
@@ -208,48 +209,35 @@ __global__ void __launch_bounds__(kWsThreads, 8) k_up_warp(Op<T> op, Vec<T> vec,
         for (int64_t g = g0; g < g1; ++g) {
             const int l = 63 - __clzll(static_cast<unsigned long long>(span - g - 1));
             const int64_t node = (int64_t(3) << l) + g - span;
-            T r;
-            if (root_leaf) {
-                r = ws_project_leaf<T, KM>(op, vec, node - op.first_leaf);
-            } else {
-                // transfers: xhat_p = sum over the two children of E_c^T xhat_c; lane j takes
-                // row j of each child's tile and entry j of its vector
-                const int64_t c0 = 2 * node;
-                T e0[KM], e1[KM], x0, x1;
-                if (ws.edge && l == top) {
-                    x0 = ws_project_leaf<T, KM>(op, vec, c0 - op.first_leaf);
-                    if (lane < k) vec.xh[c0 * kx * vs + lane] = x0;
-                    x1 = ws_project_leaf<T, KM>(op, vec, c0 + 1 - op.first_leaf);
-                    if (lane < k) vec.xh[(c0 + 1) * kx * vs + lane] = x1;
-                    ws_load_row<T, KM>(op.E + c0 * k * kx, k, kx, e0);  // zero in lanes >= k
-                    ws_load_row<T, KM>(op.E + (c0 + 1) * k * kx, k, kx, e1);
-                } else {
-                    // the tiles are loaded before the children are waited for
-                    ws_load_row<T, KM>(op.E + c0 * k * kx, k, kx, e0);
-                    ws_load_row<T, KM>(op.E + (c0 + 1) * k * kx, k, kx, e1);
-                    const bool wait = l + 1 <= top;  // the children are items of this launch
-                    if (wait && !ws_wait(ws.flag + c0, ws.abort, vec.err)) return;
-                    if (wait && !ws_wait(ws.flag + c0 + 1, ws.abort, vec.err)) return;
-                    x0 = lane < k ? __ldcg(vec.xh + c0 * kx * vs + lane) : T(0);
-                    x1 = lane < k ? __ldcg(vec.xh + (c0 + 1) * kx * vs + lane) : T(0);
-                }
-                T p[KM];
+            // xhat_p = sum over the two children of E_c^T xhat_c; lane j takes row j of each
+            // child's tile (loaded before the children are waited for) and entry j of its vector
+            const int64_t c0 = 2 * node;
+            T e0[KM], e1[KM];
+            ws_load_row<T, KM>(op.E + c0 * k * kx, k, kx, e0);
+            ws_load_row<T, KM>(op.E + (c0 + 1) * k * kx, k, kx, e1);
+            const bool wait = l + 1 <= top;  // the children are items of this launch
+            if (wait && !ws_wait(ws.flag + c0, ws.abort, vec.err)) return;
+            if (wait && !ws_wait(ws.flag + c0 + 1, ws.abort, vec.err)) return;
+            const T x0 = lane < k ? __ldcg(vec.xh + c0 * kx * vs + lane) : T(0);
+            const T x1 = lane < k ? __ldcg(vec.xh + (c0 + 1) * kx * vs + lane) : T(0);
+            T p[KM];
 #pragma unroll
-                for (int j = 0; j < KM; ++j) p[j] = fma(e1[j], x1, e0[j] * x0);
-                r = ws_reduce<T, KM>(p);
-            }
+            for (int j = 0; j < KM; ++j) p[j] = fma(e1[j], x1, e0[j] * x0);
+            const T r = ws_reduce<T, KM>(p);
             if (lane < k) vec.xh[node * kx * vs + lane] = r;
             if (l > ws.lo) ws_publish(ws.flag + node);
         }
     }
 }
 
-// Downsweep: items top-down, item g being heap node 2^lo + g (level lo .. hi).
+// Downsweep of the levels lo .. hi (the totals of level lo - 1 from an earlier launch): items
+// top-down, item g being heap node 2^lo + g; every total is written to yhat for the next
+// launch or level.
 template <typename T, int KM>
 __global__ void __launch_bounds__(kWsThreads, 8) k_down_warp(Op<T> op, Vec<T> vec, WarpSweep ws)
 {
     const int lane = threadIdx.x & 31;
-    const int k = op.k, kx = op.kx, mp = op.mp, vs = vec.vs;
+    const int k = op.k, kx = op.kx, vs = vec.vs;
     if (ws.hi < ws.lo) return;
     const int64_t first = int64_t(1) << ws.lo;
     const int64_t total = (int64_t(2) << ws.hi) - first;
@@ -260,30 +248,10 @@ __global__ void __launch_bounds__(kWsThreads, 8) k_down_warp(Op<T> op, Vec<T> ve
         for (int64_t g = g0; g < g1; ++g) {
             const int64_t node = first + g;
             const int l = 63 - __clzll(static_cast<unsigned long long>(node));
-            const bool leaf = ws.edge && l == ws.hi;
             // everything that does not depend on the parent is loaded first
             const T own = lane < k ? vec.yh[node * kx * vs + lane] : T(0);  // the node's coupling row
             T e[KM];
             if (l >= 1) ws_load_row<T, KM>(op.Et + node * k * kx, k, kx, e);
-            int64_t t = 0;
-            int r0 = 0, R = 0;
-            T u0[KM], u1[KM], d0 = T(0), d1 = T(0);
-            int perm0 = 0, perm1 = 0;
-            if (leaf) {  // the leaf's basis rows, dense partial result and output rows
-                t = node - op.first_leaf;
-                r0 = op.leaf_lo[t];
-                R = op.leaf_lo[t + 1] - r0;
-                const T *__restrict__ ut = op.Ut + t * kx * mp;
-                const int i0 = lane, i1 = 32 + lane;
-#pragma unroll
-                for (int j = 0; j < KM; ++j) {
-                    u0[j] = j < k && i0 < mp ? __ldg(ut + j * mp + i0) : T(0);
-                    u1[j] = j < k && i1 < mp ? __ldg(ut + j * mp + i1) : T(0);
-                }
-                const T *__restrict__ yd = vec.yd + t * mp * vs;
-                if (i0 < R) d0 = yd[i0], perm0 = op.perm[r0 + i0];
-                if (i1 < R) d1 = yd[i1], perm1 = op.perm[r0 + i1];
-            }
             T acc = T(0);
             if (l >= 1) {
                 const int64_t p = node >> 1;
@@ -296,44 +264,174 @@ __global__ void __launch_bounds__(kWsThreads, 8) k_down_warp(Op<T> op, Vec<T> ve
                 acc = ws_reduce<T, KM>(q);
             }
             acc += own;
-            if (!leaf) {
-                if (lane < k) vec.yh[node * kx * vs + lane] = acc;
-                if (l < ws.hi) ws_publish(ws.flag + node);
-                continue;
-            }
-            // leaf: y_i = sum_nu U_t[i][nu] yhat_nu + (A_de x)_i for the rows i = lane, lane + 32,
-            // then the rows beyond 64 (leaves of up to 128 points) with loads of their own
-            T y0 = T(0), y1 = T(0);
+            if (lane < k) vec.yh[node * kx * vs + lane] = acc;
+            if (l < ws.hi) ws_publish(ws.flag + node);
+        }
+    }
+}
+
+// ---- bottom subtrees: one CTA of eight warps per subtree, vectors in shared memory
+
+constexpr int kCtaWarps = 8;
+constexpr int kCtaThreads = 32 * kCtaWarps;
+
+// Shared memory of a subtree CTA: one KM-entry slot per node of a subtree of depth L (local
+// heap order: slot 1 is the root, slots 2^L .. 2^(L+1)-1 the leaves).
+template <typename T, int KM>
+__host__ __device__ constexpr size_t cta_smem_bytes(int L)
+{
+    return (size_t(2) << L) * KM * sizeof(T);
+}
+
+// Upsweep of the subtree st rooted at level Lr with depth L = q - Lr (Sec. 3.1, Alg 1): the
+// warps project the 2^L leaves, then compute the levels q - 1 .. Lr one barrier apart, every
+// warp taking the nodes w, w + 8, ... of a level; each vector is written to xhat (for the block
+// streams and the upper levels) and to the CTA's slot of the node. A warp loads the transfer
+// rows of its next node before it waits at the barrier.
+template <typename T, int KM>
+__global__ void __launch_bounds__(kCtaThreads, 2) k_up_cta(Op<T> op, Vec<T> vec, int Lr, int L)
+{
+    extern __shared__ __align__(16) unsigned char ws_smem[];
+    T *sx = reinterpret_cast<T *>(ws_smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = op.k, kx = op.kx, vs = vec.vs;
+    const int64_t st = blockIdx.x;
+    const int nleaf = 1 << L;
+    for (int j = warp; j < nleaf; j += kCtaWarps) {
+        const int64_t t = st * nleaf + j;
+        const T r = ws_project_leaf<T, KM>(op, vec, t);
+        if (lane < k) {
+            vec.xh[(op.first_leaf + t) * kx * vs + lane] = r;
+            sx[(nleaf + j) * KM + lane] = r;
+        }
+    }
+    T e0[KM], e1[KM];
+    auto load_rows = [&](int rel, int i) {  // transfer rows of the children of local node (rel, i)
+        const int64_t c0 = 2 * ((int64_t(1) << (Lr + rel)) + st * (int64_t(1) << rel) + i);
+        ws_load_row<T, KM>(op.E + c0 * k * kx, k, kx, e0);
+        ws_load_row<T, KM>(op.E + (c0 + 1) * k * kx, k, kx, e1);
+    };
+    if (L >= 1 && warp < (1 << (L - 1))) load_rows(L - 1, warp);
+    __syncthreads();
+    for (int rel = L - 1; rel >= 0; --rel) {
+        const int cnt = 1 << rel;
+        for (int i = warp; i < cnt; i += kCtaWarps) {
+            if (i != warp) load_rows(rel, i);  // nodes beyond the first of this warp
+            const int slot = cnt + i;
+            const T x0 = lane < k ? sx[(2 * slot) * KM + lane] : T(0);
+            const T x1 = lane < k ? sx[(2 * slot + 1) * KM + lane] : T(0);
+            T p[KM];
 #pragma unroll
-            for (int j = 0; j < KM; ++j) {
-                const T a = __shfl_sync(0xffffffffu, acc, j);
-                y0 = fma(u0[j], a, y0);
-                y1 = fma(u1[j], a, y1);
+            for (int j = 0; j < KM; ++j) p[j] = fma(e1[j], x1, e0[j] * x0);
+            const T r = ws_reduce<T, KM>(p);
+            if (lane < k) {
+                vec.xh[((int64_t(1) << (Lr + rel)) + st * cnt + i) * kx * vs + lane] = r;
+                sx[slot * KM + lane] = r;
             }
-            if (lane < R) {
-                const T v = y0 + d0;
-                T *dst = vec.Y + perm0;
+        }
+        if (rel >= 1 && warp < (cnt >> 1)) load_rows(rel - 1, warp);
+        __syncthreads();
+    }
+}
+
+// Downsweep of the subtree st rooted at level Lr with depth L = q - Lr (Sec. 3.3, Alg 6): the
+// root's total yhat_r = E_r yhat_parent + own_r (the parent's total from an earlier launch;
+// none at the tree root), then the levels below one barrier apart (totals in the CTA's slots
+// only), and at the leaves the expansion and epilogue. A warp loads its next node's transfer
+// rows, coupling row and, for a leaf, basis rows, dense result and output rows before it
+// waits at the barrier.
+template <typename T, int KM>
+__global__ void __launch_bounds__(kCtaThreads, 2) k_down_cta(Op<T> op, Vec<T> vec, int Lr, int L)
+{
+    extern __shared__ __align__(16) unsigned char ws_smem[];
+    T *sy = reinterpret_cast<T *>(ws_smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = op.k, kx = op.kx, mp = op.mp, vs = vec.vs;
+    const int64_t st = blockIdx.x;
+    T e[KM], own = T(0);
+    auto node_of = [&](int rel, int i) { return (int64_t(1) << (Lr + rel)) + st * (int64_t(1) << rel) + i; };
+    auto load_node = [&](int rel, int i) {
+        const int64_t node = node_of(rel, i);
+        own = lane < k ? vec.yh[node * kx * vs + lane] : T(0);
+        if (Lr + rel >= 1) ws_load_row<T, KM>(op.Et + node * k * kx, k, kx, e);
+    };
+    // the parent's vector (lane j: entry j): the CTA's slot, or for the root the total of an
+    // earlier launch
+    auto parent_of = [&](int rel, int i) -> T {
+        if (rel >= 1) return lane < k ? sy[((1 << (rel - 1)) + (i >> 1)) * KM + lane] : T(0);
+        if (Lr == 0) return T(0);
+        return lane < k ? __ldcg(vec.yh + (node_of(0, 0) >> 1) * kx * vs + lane) : T(0);
+    };
+    auto total_of = [&](int rel, int i) -> T {
+        T acc = T(0);
+        if (Lr + rel >= 1) {
+            const T yp = parent_of(rel, i);
+            T q[KM];
+#pragma unroll
+            for (int j = 0; j < KM; ++j) q[j] = e[j] * yp;
+            acc = ws_reduce<T, KM>(q);
+        }
+        return acc + own;
+    };
+    // internal levels Lr .. q - 1
+    if (L >= 1 && warp == 0) load_node(0, 0);
+    for (int rel = 0; rel < L; ++rel) {
+        const int cnt = 1 << rel;
+        for (int i = warp; i < cnt; i += kCtaWarps) {
+            if (i != warp) load_node(rel, i);
+            const T acc = total_of(rel, i);
+            if (lane < k) sy[(cnt + i) * KM + lane] = acc;
+        }
+        if (rel + 1 < L && warp < 2 * cnt) load_node(rel + 1, warp);
+        __syncthreads();
+    }
+    // leaves: y_i = sum_nu U_t[i][nu] yhat_nu + (A_de x)_i, Y[perm] = alpha y + beta Y
+    const int nleaf = 1 << L;
+    for (int j = warp; j < nleaf; j += kCtaWarps) {
+        const int64_t t = st * nleaf + j;
+        load_node(L, j);
+        const int r0 = op.leaf_lo[t], R = op.leaf_lo[t + 1] - r0;
+        const T *__restrict__ ut = op.Ut + t * kx * mp;
+        const T *__restrict__ yd = vec.yd + t * mp * vs;
+        const int i0 = lane, i1 = 32 + lane;
+        T u0[KM], u1[KM], d0 = T(0), d1 = T(0);
+        int perm0 = 0, perm1 = 0;
+#pragma unroll
+        for (int jj = 0; jj < KM; ++jj) {
+            u0[jj] = jj < k && i0 < mp ? __ldg(ut + jj * mp + i0) : T(0);
+            u1[jj] = jj < k && i1 < mp ? __ldg(ut + jj * mp + i1) : T(0);
+        }
+        if (i0 < R) d0 = yd[i0], perm0 = op.perm[r0 + i0];
+        if (i1 < R) d1 = yd[i1], perm1 = op.perm[r0 + i1];
+        const T acc = total_of(L, j);
+        T y0 = T(0), y1 = T(0);
+#pragma unroll
+        for (int jj = 0; jj < KM; ++jj) {
+            const T a = __shfl_sync(0xffffffffu, acc, jj);
+            y0 = fma(u0[jj], a, y0);
+            y1 = fma(u1[jj], a, y1);
+        }
+        if (i0 < R) {
+            const T v = y0 + d0;
+            T *dst = vec.Y + perm0;
+            *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
+        }
+        if (i1 < R) {
+            const T v = y1 + d1;
+            T *dst = vec.Y + perm1;
+            *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
+        }
+        for (int ib = 64; ib < R; ib += 32) {  // rows beyond 64, uniform over the warp
+            const int i = ib + lane;
+            T y = T(0);
+            for (int jj = 0; jj < k; ++jj) {
+                const T a = __shfl_sync(0xffffffffu, acc, jj);
+                if (i < mp) y = fma(__ldg(ut + jj * mp + i), a, y);
+            }
+            if (i < R) {
+                const T v = y + yd[i];
+                T *dst = vec.Y + op.perm[r0 + i];
                 *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
-            }
-            if (32 + lane < R) {
-                const T v = y1 + d1;
-                T *dst = vec.Y + perm1;
-                *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
-            }
-            const T *__restrict__ ut = op.Ut + t * kx * mp;
-            const T *__restrict__ yd = vec.yd + t * mp * vs;
-            for (int ib = 64; ib < R; ib += 32) {  // uniform over the warp
-                const int i = ib + lane;
-                T y = T(0);
-                for (int j = 0; j < k; ++j) {
-                    const T a = __shfl_sync(0xffffffffu, acc, j);
-                    if (i < mp) y = fma(__ldg(ut + j * mp + i), a, y);
-                }
-                if (i < R) {
-                    const T v = y + yd[i];
-                    T *dst = vec.Y + op.perm[r0 + i];
-                    *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
-                }
             }
         }
     }
