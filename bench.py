@@ -293,7 +293,7 @@ def cpu_baseline(steps: int = 0, all_cores: bool = True):
 
 
 def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with_fp64=True,
-              ffma_peak=FFMA_PEAK_TFLOPS, dfma_peak=None):
+              ffma_peak=FFMA_PEAK_TFLOPS, dfma_peak=None, alu_kind="measured (h2_measure_peak, {} FMA chains)"):
     """The multi-vector workload: N = 2^21 uniform random points in [0,1]^3, exp(-r/0.2),
     leaf 64, 4 x 4 x 4 Chebyshev grid (rank 64), eta 0.7, 32 vectors, in split-BF16 on the
     tensor cores, in FP32 on the tensor cores (3xTF32; the default for FP32 passes of more
@@ -366,14 +366,14 @@ def multi_rhs(h2, torch, steps, warmup, peak_hbm, peak_kind, n_points=None, with
             # 16 flop per byte at 32 vectors: the FP32 stream is bound by the CUDA-core FMA rate
             roof = {"kernel": "k_stream (FP32, register-blocked wide accumulator)", "bound": "alu",
                     "achieved": blk_tflops, "peak": ffma_peak, "unit": "TFLOP/s",
-                    "frac": blk_tflops / ffma_peak, "peak_kind": "measured (h2_measure_peak, FP32 FMA chains)",
+                    "frac": blk_tflops / ffma_peak, "peak_kind": alu_kind.format("FP32"),
                     "hbm_GB/s": blk_gbs}
         if prec == "fp64":
             # 8 flop per FP64 byte at 32 vectors: bound by the FP64 FMA rate
             roof = {"kernel": "k_stream (FP64, register-blocked wide accumulator)", "bound": "alu",
                     "achieved": blk_tflops, "peak": dfma_peak, "unit": "TFLOP/s",
                     "frac": blk_tflops / dfma_peak if dfma_peak else None,
-                    "peak_kind": "measured (h2_measure_peak, FP64 FMA chains)"}
+                    "peak_kind": alu_kind.format("FP64")}
             gbs = 8 * (mat_entries + vec_elems) / (ms_step * 1e-3) / 1e9
         out[prec] = {"ms_per_step": ms_step, "ms_median": float(np.median(ms)), "GB/s": gbs,
                      "gflops": flops / (ms_step * 1e-3) / 1e9, "frac_of_hbm": gbs / peak_hbm,
@@ -1014,7 +1014,7 @@ def main():
         try:
             mr_steps = args.multi_rhs_steps if args.multi_rhs_steps > 0 else max(5, args.steps // 20)
             line["multi_rhs"] = multi_rhs(h2, torch, mr_steps, 3, peak_hbm, peak_kind, args.cloud_n,
-                                          not args.no_multi_rhs_fp64, ffma_peak, dfma_peak)
+                                          not args.no_multi_rhs_fp64, ffma_peak, dfma_peak, rate_kind)
         except Exception as exc:  # reported, never silently dropped
             line["multi_rhs"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batch:
@@ -1027,7 +1027,7 @@ def main():
     if not args.no_compress:
         try:
             line["compress"] = compress_benchmark(h2, torch, args.compress_steps, tuple(args.compress_sets.split(",")),
-                                                  args.compress_grid, dfma_peak)
+                                                  args.compress_grid, None if args.no_peaks else dfma_peak)
             if rank == 0 and world == 1 and not args.no_cpu_baseline:
                 line["compress"]["cpu_baseline"] = compress_oracle_sample(h2, torch)
         except Exception as exc:  # reported, never silently dropped
