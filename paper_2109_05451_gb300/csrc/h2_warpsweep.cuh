@@ -138,17 +138,16 @@ __device__ __forceinline__ T ws_reduce(T (&p)[KM])
     return p[0];
 }
 
-// Row j = lane of a transfer tile ([j][o], ld kx): r[o] for o < KM, zero beyond kx and for
-// lanes j >= k. 16-byte loads (kx is a multiple of 4, tile rows start on 16 bytes).
+// Row j of a tile ([j][o], ld kx): r[o] for o < KM, zero beyond kx and when not active.
+// 16-byte loads (kx is a multiple of 4, tile rows start on 16 bytes).
 template <typename T, int KM>
-__device__ __forceinline__ void ws_load_row(const T *__restrict__ tile, int k, int kx, T (&r)[KM])
+__device__ __forceinline__ void ws_load_row_at(const T *__restrict__ tile, int j, bool active, int kx, T (&r)[KM])
 {
-    const int lane = threadIdx.x & 31;
     constexpr int V = 16 / sizeof(T);  // elements per 16-byte load
-    const T *__restrict__ row = tile + int64_t(lane) * kx;
+    const T *__restrict__ row = tile + int64_t(j) * kx;
 #pragma unroll
     for (int q = 0; q < KM / V; ++q) {
-        if (lane < k && q * V < kx) {
+        if (active && q * V < kx) {
             if constexpr (V == 4) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(row) + q);
                 r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
@@ -161,6 +160,14 @@ __device__ __forceinline__ void ws_load_row(const T *__restrict__ tile, int k, i
             for (int e = 0; e < V; ++e) r[V * q + e] = T(0);
         }
     }
+}
+
+// Row j = lane of a transfer tile (zero for lanes j >= k).
+template <typename T, int KM>
+__device__ __forceinline__ void ws_load_row(const T *__restrict__ tile, int k, int kx, T (&r)[KM])
+{
+    const int lane = threadIdx.x & 31;
+    ws_load_row_at<T, KM>(tile, lane, lane < k, kx, r);
 }
 
 // Leaf projection xhat_t = U_t^T x_t (Sec. 3.1): lane i takes rows i, i + 32, ... of U_t
@@ -439,24 +446,29 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_down_cta(Op<T> op, Vec<T> ve
 
 // Block rows of small coupling blocks (k <= 32), one vector (Sec. 3.2, Alg 4): one warp per
 // scheduling chunk of whole rows (chunks[c] = (first descriptor << 16) | count), taken from
-// the ticket vec.tickets[ticket_index]; lane j takes row j of each block's tile S_ts^T ([j][o],
-// ld kx) and entry j of xhat_s, so a row's partial vectors need one reduce-scatter at its end.
-// The tiles of NB blocks are loaded at once (NB x KM values per lane), and the next chunk's
-// ticket is drawn while the current one is processed. An empty row (kZero) is stored as zeros.
-// Rows are independent: no warp waits for another.
+// the ticket vec.tickets[ticket_index]. With KM = 16 each half-warp takes its own block (H = 2
+// blocks per load slot), with KM = 32 the whole warp one; lane j of a group takes row j of the
+// block's tile S_ts^T ([j][o], ld kx) and entry j of xhat_s, so a row's partial vectors need
+// one reduce-scatter at its end. The blocks are added in order (the groups of a slot one
+// after the other), so a row that ends inside a slot is reduced before the next row's block
+// is added. The tiles of NB slots are loaded at once (NB x KM values per lane), and the next
+// chunk's ticket is drawn while the current one is processed. An empty row (kZero) is stored
+// as zeros. Rows are independent: no warp waits for another.
 template <typename T, int KM>
 __global__ void __launch_bounds__(kWsThreads, 8)
     k_rows_warp(Op<T> op, Vec<T> vec, const StreamDesc *__restrict__ desc, const int64_t *__restrict__ chunks,
                 int64_t nchunks, int ticket_index)
 {
-    constexpr int NB = (64 * 4 / int(sizeof(T))) / KM;  // blocks in flight: 64 registers of tiles
+    constexpr int NB = (64 * 4 / int(sizeof(T))) / KM;  // load slots: 64 registers of tiles
+    constexpr int H = 32 / KM;                          // blocks per slot, one per lane group
     const int lane = threadIdx.x & 31;
+    const int grp = lane / KM, j = lane % KM;
     const int k = op.k, kx = op.kx, vs = vec.vs;
     int *ticket = vec.tickets + ticket_index;
     int64_t c = ws_ticket(ticket);
     T p[KM];
 #pragma unroll
-    for (int j = 0; j < KM; ++j) p[j] = T(0);
+    for (int q = 0; q < KM; ++q) p[q] = T(0);
     while (c < nchunks) {
         int next = 0;
         if (lane == 0) next = atomicAdd(ticket, 1);  // used after this chunk
@@ -475,30 +487,41 @@ __global__ void __launch_bounds__(kWsThreads, 8)
                 on = d.out_node;
                 fl = d.flags;
             }
-            for (int b = 0; b < n; b += NB) {
+            for (int b = 0; b < n; b += NB * H) {
                 T t[NB][KM], xv[NB];
-                int fb[NB], ob[NB];
+                int fb[NB][H], ob[NB][H];
 #pragma unroll
                 for (int u = 0; u < NB; ++u) {
-                    const int bi = b + u < n ? b + u : n - 1;
+#pragma unroll
+                    for (int e = 0; e < H; ++e) {
+                        const int be = b + H * u + e < n ? b + H * u + e : n - 1;
+                        fb[u][e] = __shfl_sync(0xffffffffu, fl, be);
+                        ob[u][e] = __shfl_sync(0xffffffffu, on, be);
+                    }
+                    const int mine = b + H * u + grp;  // this lane group's block
+                    const int bi = mine < n ? mine : n - 1;
                     const uint64_t sb = __shfl_sync(0xffffffffu, src, bi);
                     const int xb = __shfl_sync(0xffffffffu, xn, bi);
-                    fb[u] = __shfl_sync(0xffffffffu, fl, bi);
-                    ob[u] = __shfl_sync(0xffffffffu, on, bi);
-                    const bool live = b + u < n && !(fb[u] & kZero);
-                    ws_load_row<T, KM>(reinterpret_cast<const T *>(op.vals + sb), live ? k : 0, kx, t[u]);
-                    xv[u] = live && lane < k ? vec.xh[int64_t(xb) * kx * vs + lane] : T(0);
+                    const int fm = __shfl_sync(0xffffffffu, fl, bi);
+                    const bool live = mine < n && !(fm & kZero) && j < k;
+                    ws_load_row_at<T, KM>(reinterpret_cast<const T *>(op.vals + sb), j, live, kx, t[u]);
+                    xv[u] = live ? vec.xh[int64_t(xb) * kx * vs + j] : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < NB; ++u) {
-                    if (b + u >= n) break;
 #pragma unroll
-                    for (int j = 0; j < KM; ++j) p[j] = fma(t[u][j], xv[u], p[j]);
-                    if (fb[u] & kLast) {
-                        const T r = ws_reduce<T, KM>(p);
-                        if (lane < k) vec.yh[int64_t(ob[u]) * kx * vs + lane] = r;
+                    for (int e = 0; e < H; ++e) {
+                        if (b + H * u + e >= n) break;
+                        if (grp == e) {
 #pragma unroll
-                        for (int j = 0; j < KM; ++j) p[j] = T(0);
+                            for (int q = 0; q < KM; ++q) p[q] = fma(t[u][q], xv[u], p[q]);
+                        }
+                        if (fb[u][e] & kLast) {
+                            const T r = ws_reduce<T, KM>(p);
+                            if (lane < k) vec.yh[int64_t(ob[u][e]) * kx * vs + lane] = r;
+#pragma unroll
+                            for (int q = 0; q < KM; ++q) p[q] = T(0);
+                        }
                     }
                 }
             }
