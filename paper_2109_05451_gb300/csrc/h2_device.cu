@@ -71,8 +71,9 @@ struct h2_device {
     // FP32 operators with ranks and leaves of at most 64: passes of more than 8 vectors run on
     // the tensor cores (3xTF32, k_stream_tf32) unless switched off by h2_set_fp32_tensor
     bool tf32_ok = false, tf32_on = true;
-    // ranks of at most 32: single-vector products sweep the tree with one warp per node
-    // (h2_warpsweep.cuh) instead of the staged subtree kernels
+    // ranks of at most 32: single-vector products run the warp-granular kernels of
+    // h2_warpsweep.cuh (bottom subtrees one CTA each, upper levels one warp per node,
+    // coupling rows one warp per chunk) instead of the staged subtree kernels and streams
     bool warp_sweeps = false;
     // views into the arena
     int32_t *perm = nullptr, *leaf_lo = nullptr;
@@ -466,7 +467,8 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
              static_cast<T *>(w.yh), w.tickets, dv.err};
     const int Lbot = dv.L, Lb = dv.Lb;
     const int64_t nsub = int64_t(1) << Lb;
-    // ranks of at most 32, one vector: warp-per-node sweeps, one launch per part of the tree
+    // ranks of at most 32, one vector: the warp-granular kernels, one launch per part of the
+    // tree (bottom subtrees, upper levels) and per row list
     const bool wsw = NVMAX == 1 && dv.warp_sweeps && w.flags;
     if (wsw) {
         v.flags = w.flags;
