@@ -393,9 +393,13 @@ int h2_server_destroy(h2_server_t s);
 
 /* Self-test of the bounded device waits (no paper counterpart): launches one thread that
  * waits on a shared-memory barrier nothing arrives on, with a budget of budget_cycles clock
- * cycles; the wait gives up, records the failure in a device flag and returns, so the call
- * returns H2_ETIMEOUT and the CUDA context stays usable. The kernels' own waits use the same
- * mechanism with a budget of about one second. */
+ * cycles, and two warps that wait on node flags in global memory nothing sets (the waits of
+ * the small-rank warp sweeps), the first with budget_cycles, the second with fifty times that.
+ * The barrier wait and the first flag wait give up and record the failure in device flags;
+ * the first also raises the launch's abort word, on which the second must leave. The call
+ * returns H2_ETIMEOUT when all of this happened (H2_OK otherwise), and the CUDA context stays
+ * usable. H2_EINVAL unless 1 <= budget_cycles <= 8e7. The kernels' own waits use the same
+ * mechanisms with a budget of about one second. */
 int h2_selftest_wait_timeout(int64_t budget_cycles);
 
 /* Measured arithmetic peak of the current device (no paper counterpart; it supplies the

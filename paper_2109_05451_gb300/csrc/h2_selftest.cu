@@ -4,7 +4,10 @@
 //    clock cycles without progress the waiting thread records the failure in a device flag and
 //    returns, so a stalled pipeline ends its kernel instead of hanging the GPU. The self-test
 //    exercises that path on purpose and harmlessly: one thread waits on a shared-memory barrier
-//    nothing arrives on, with a short budget, and the host reads the flag.
+//    nothing arrives on, with a short budget, and the host reads the flag. The warp sweeps'
+//    waits on node flags in global memory are exercised the same way: two warps wait on flags
+//    nothing sets; the first gives up after the budget and raises the launch's abort word, and
+//    the second, whose own budget is fifty times longer, must leave on that abort word.
 // 2. Arithmetic peaks. The FP64 product is bound by the FP64 fused multiply-add rate, the FP32
 //    multi-vector product on the CUDA cores by the FP32 one, and the matrix-free product by the
 //    special-function unit; their rooflines need those rates as this device delivers them, not
@@ -18,6 +21,7 @@
 
 #include "../../include/h2.h"
 #include "h2_pipe.cuh"
+#include "h2_warpsweep.cuh"
 
 namespace {
 
@@ -32,6 +36,16 @@ __global__ void k_wait_timeout(long long budget, int *err)
     }
     __syncthreads();
     if (threadIdx.x == 0) h2p::mbar_wait_for(&bar, 0, &abort_flag, err, budget);  // no arrival ever comes
+}
+
+// words[0], words[1]: the two warps' node flags (never set); words[2]: the abort word.
+// waited[0]: clock cycles the second warp waited.
+__global__ void k_flag_wait_timeout(long long budget, int *words, int *err, long long *waited)
+{
+    const int warp = threadIdx.x / 32;
+    const long long t0 = clock64();
+    (void)h2s::ws_wait_for(words + warp, words + 2, err, warp == 0 ? budget : 50 * budget);
+    if (warp == 1 && (threadIdx.x & 31) == 0) waited[0] = clock64() - t0;
 }
 
 constexpr int kChains = 8;  // ex2 chains per thread
@@ -133,23 +147,32 @@ cudaError_t launch_chains(int unit, int form, int grid, int iters, const void *i
 
 extern "C" int h2_selftest_wait_timeout(int64_t budget_cycles)
 {
-    if (budget_cycles < 1 || budget_cycles > 4000000000LL) return H2_EINVAL;
-    int *err = nullptr;
-    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    if (budget_cycles < 1 || budget_cycles > 4000000000LL / 50) return H2_EINVAL;
+    // [0] error flag of the barrier wait, [1] error flag of the flag waits, [2 .. 4] flags and
+    // abort word, then the second warp's wait in cycles (8-byte aligned)
+    int *buf = nullptr;
+    if (cudaMalloc(&buf, 8 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return H2_ENOMEM;
     }
-    int flag = 0;
-    cudaError_t e = cudaMemset(err, 0, sizeof(int));
+    int host[8] = {};
+    long long waited = 0;
+    long long *dwaited = reinterpret_cast<long long *>(buf + 6);
+    cudaError_t e = cudaMemset(buf, 0, 8 * sizeof(int));
     if (e == cudaSuccess) {
-        k_wait_timeout<<<1, 32>>>(budget_cycles, err);
+        k_wait_timeout<<<1, 32>>>(budget_cycles, buf);
+        k_flag_wait_timeout<<<1, 64>>>(budget_cycles, buf + 2, buf + 1, dwaited);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaFree(err);
+    if (e == cudaSuccess) e = cudaMemcpy(host, buf, 6 * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&waited, dwaited, sizeof(waited), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
     if (e != cudaSuccess) return H2_ECUDA;
-    return flag ? H2_ETIMEOUT : H2_OK;
+    // both kinds of wait gave up and said so, and the second flag waiter left on the abort
+    // word rather than on its own (fifty times longer) budget
+    const bool flag_waits = host[1] && host[4] && waited < 10 * budget_cycles;
+    return host[0] && flag_waits ? H2_ETIMEOUT : H2_OK;
 }
 
 extern "C" int h2_measure_peak(int unit, double target_ms, double *rate, double *ms)

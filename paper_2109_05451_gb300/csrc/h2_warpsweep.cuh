@@ -70,9 +70,10 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v)
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Waits (lane 0, bounded) until *flag is set, then acquires it in every lane. False, in every
-// lane, once this launch aborted.
-__device__ __forceinline__ bool ws_wait(const int *flag, int *abort, int *err)
+// Waits (lane 0) until *flag is set, then acquires it in every lane. False, in every lane,
+// once this launch aborted: another wait raised the abort word, or this one saw no flag for
+// `budget` clock cycles and raised it (and the error flag) itself.
+__device__ __forceinline__ bool ws_wait_for(const int *flag, int *abort, int *err, long long budget)
 {
     const int lane = threadIdx.x & 31;
     int ok = 1;
@@ -84,7 +85,7 @@ __device__ __forceinline__ bool ws_wait(const int *flag, int *abort, int *err)
                 ok = 0;
                 break;
             }
-            if (clock64() - t0 > h2p::kWaitCycles) {
+            if (clock64() - t0 > budget) {
                 atomicExch(abort, 1);
                 if (err) atomicExch(err, 1);
                 ok = 0;
@@ -95,6 +96,11 @@ __device__ __forceinline__ bool ws_wait(const int *flag, int *abort, int *err)
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (ok) (void)ld_acquire_gpu(flag);
     return ok != 0;
+}
+
+__device__ __forceinline__ bool ws_wait(const int *flag, int *abort, int *err)
+{
+    return ws_wait_for(flag, abort, err, h2p::kWaitCycles);
 }
 
 // After the lanes' stores of a node's vector: every lane fences, then lane 0 sets the flag.

@@ -2,7 +2,10 @@
 
 * Device side: every wait of the pipelined kernels gives up after a cycle budget, records the
   failure in a device flag and returns. A self-test waits on a barrier nothing arrives on with
-  a short budget: the call reports H2_ETIMEOUT and the context keeps working.
+  a short budget, and two warps wait on node flags nothing sets (the small-rank warp sweeps'
+  waits): the first gives up and raises the abort word, on which the second, with a fifty
+  times longer budget, leaves. The call reports H2_ETIMEOUT and the context keeps working (a
+  small-rank product, which runs those warp sweeps, still matches the oracle).
 * Host side (the serving loop): a cancelled queued request, a cancelled running request, a
   right-hand side with a NaN, an argument error and a request too large for the slot memory;
   the loop survives all of them and still serves an ordinary request with the same result it
@@ -26,6 +29,8 @@ SIGMA2 = 0.1
 
 def test_bounded_wait_gives_up_and_the_context_stays_usable():
     assert h2.load().h2_selftest_wait_timeout(2_000_000) == h2.H2_ETIMEOUT
+    assert h2.load().h2_selftest_wait_timeout(0) == h2.H2_EINVAL
+    assert h2.load().h2_selftest_wait_timeout(10 ** 9) == h2.H2_EINVAL
     pts = si.grid_2d(40)
     ker = ("exp", 0.1, 0, 0)
     orc = oracle.OracleH2(pts, ker, 32, 4, 0.9)
