@@ -967,8 +967,10 @@ def main():
         except Exception as exc:  # the baseline is context; its failure must not hide the GPU line
             cpu = {"value": None, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
 
+    # the metric names the default 2^20-point grid; another --grid names its own size
+    metric = METRIC if args.grid == 1024 else METRIC.replace("N=2^20", f"N={n}")
     line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": n, "nv": 1, "rank": info.rank, "leaf": info.leaf_size, "eta": w.eta,
