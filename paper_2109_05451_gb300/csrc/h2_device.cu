@@ -75,6 +75,9 @@ struct h2_device {
     // h2_warpsweep.cuh (bottom subtrees one CTA each, upper levels one warp per node,
     // coupling rows one warp per chunk) instead of the staged subtree kernels and streams
     bool warp_sweeps = false;
+    // FP32 ranks 33 .. 64: single-vector products run the bottom subtrees' downsweep with one
+    // CTA each, two warps per node (k_down_cta2)
+    bool cta64 = false;
     // views into the arena
     int32_t *perm = nullptr, *leaf_lo = nullptr;
     int64_t *cpl_rowptr = nullptr;
@@ -407,6 +410,17 @@ void launch_cta_sweep(bool up, const h2_op &op, const h2s::Op<T> &o, const h2s::
         launch_cta_sweep_km<T, 32>(up, o, v, Lr, L, st);
 }
 
+// Bottom downsweep of ranks 33 .. 64, FP32, one vector: one CTA per subtree, two warps per
+// node (k_down_cta2).
+template <typename T>
+void launch_cta2_down(const h2s::Op<T> &o, const h2s::Vec<T> &v, int Lr, int L, cudaStream_t st)
+{
+    if constexpr (sizeof(T) == 4) {
+        using namespace h2s;
+        k_down_cta2<T><<<unsigned(int64_t(1) << Lr), kCtaThreads, cta_smem_bytes<float, 64>(L), st>>>(o, v, Lr, L);
+    }
+}
+
 // Coupling rows of small ranks, one vector: one warp per chunk of rows (k_rows_warp) on the
 // scheduling word `ticket`, at most the CTAs resident on the device.
 template <typename T, int KM>
@@ -470,6 +484,7 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
     // ranks of at most 32, one vector: the warp-granular kernels, one launch per part of the
     // tree (bottom subtrees, upper levels) and per row list
     const bool wsw = NVMAX == 1 && dv.warp_sweeps && w.flags;
+    const bool c64 = NVMAX == 1 && sizeof(T) == 4 && dv.cta64;  // ranks 33 .. 64, FP32
     if (wsw) {
         v.flags = w.flags;
         v.nflags = 2 * (op.nnodes + 1);
@@ -626,6 +641,8 @@ int launch_chunk(const h2_op &op, h2_device &dv, const T *X, T *Y, int nv, doubl
         h2n::Range r("downsweep: leaf subtrees");
         if (wsw)
             launch_cta_sweep<T>(false, op, o, v, Lb, Lbot, st);
+        else if (c64)
+            launch_cta2_down<T>(o, v, Lb, Lbot, st);
         else
             k_down_sub<T, NVMAX><<<grid_bsub, kThreads, sm_bsub, st>>>(o, v, p_bsub, Lb, Lbot, nsub, 1);
     }
@@ -1930,6 +1947,7 @@ int h2_upload(h2_handle h, h2_prec prec, void *cuda_stream)
     dv->kkp = int64_t(k) * round4(k);  // entries per stored coupling tile (ld kx)
     dv->tf32_ok = prec == H2_FP32 && k <= 64 && dv->max_leaf_rows <= 64;
     dv->warp_sweeps = !dv->tc && k <= h2s::kWsMaxRank && dv->mp <= 128;
+    dv->cta64 = !dv->tc && es == 4 && k > h2s::kWsMaxRank && k <= 64 && dv->mp <= 128;
     dv->L = std::min(op.q, 4);
     dv->Lb = op.q - dv->L;
     dv->root_row = op.cpl_rowptr[2] > op.cpl_rowptr[1];

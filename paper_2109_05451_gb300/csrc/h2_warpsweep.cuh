@@ -13,6 +13,7 @@
 //   k_down_cta   bottom subtrees: yhat^l_c = E_c yhat^{l-1}_p + yhat^l_c (the node's own
 //                coupling row) level by level, then y_t = U_t yhat^q_t + (A_de x)_t and
 //                Y[perm] = alpha y + beta Y at the leaves (Sec. 3.3, Alg 6);
+//   k_down_cta2  the same downsweep for FP32 ranks 33 .. 64, two warps per node;
 //   k_up_warp,   the upper levels (few nodes per level), one warp per node, ordered by
 //   k_down_warp  flags in global memory;
 //   k_rows_warp  coupling rows (Sec. 3.2, Alg 4), one warp per chunk of rows.
@@ -445,6 +446,121 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_down_cta(Op<T> op, Vec<T> ve
                 const T v = y + yd[i];
                 T *dst = vec.Y + op.perm[r0 + i];
                 *dst = (vec.beta == T(0)) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
+            }
+        }
+    }
+}
+
+// ---- bottom downsweep of ranks 33 .. 64 (FP32): two warps per node
+//
+// A 64-output product does not fit one warp's registers, so each node is taken by a pair of
+// warps: warp h of the pair forms the outputs 32h .. 32h + 31, lane j accumulating rows j and
+// j + 32 of the tile, and one reduce-scatter leaves output 32h + o in lane o. The CTA's four
+// pairs take the nodes of a level in turn, one barrier apart, as in k_down_cta; the
+// shared-memory slots hold 64 entries per node (cta_smem_bytes<float, 64>). (The same scheme
+// for the upsweep measured slower than the staged k_up_sub at these ranks: its leaf
+// projections read 16 KB tiles per warp pair without the bulk-copy pipeline's depth.)
+
+constexpr int kCtaPairs = kCtaWarps / 2;
+
+// Barrier of the 64 threads of warp pair `pair` (named barrier 1 + pair; barrier 0 is
+// __syncthreads).
+__device__ __forceinline__ void ws_pair_sync(int pair)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+}
+
+// Rows j = lane and j + 32 of a tile ([j][o], ld kx), columns 32h .. 32h + 31: zero for rows
+// >= k and columns >= kx. 16-byte loads (kx is a multiple of 4, tile rows start on 16 bytes).
+__device__ __forceinline__ void wp_load_rows(const float *__restrict__ tile, int k, int kx, int h, float (&a)[32],
+                                             float (&b)[32])
+{
+    const int lane = threadIdx.x & 31;
+    const float4 *ra = reinterpret_cast<const float4 *>(tile + int64_t(lane) * kx + 32 * h);
+    const float4 *rb = reinterpret_cast<const float4 *>(tile + int64_t(lane + 32) * kx + 32 * h);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const bool col = 32 * h + 4 * q < kx;
+        const float4 va = col && lane < k ? __ldg(ra + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 vb = col && lane + 32 < k ? __ldg(rb + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[4 * q] = va.x, a[4 * q + 1] = va.y, a[4 * q + 2] = va.z, a[4 * q + 3] = va.w;
+        b[4 * q] = vb.x, b[4 * q + 1] = vb.y, b[4 * q + 2] = vb.z, b[4 * q + 3] = vb.w;
+    }
+}
+
+// p[o] += a[o] x_j + b[o] x_{j+32} with the inputs of a node in slot `slot` (lane j: j, j + 32)
+__device__ __forceinline__ void wp_accumulate(const float *__restrict__ s, int slot, int k, const float (&a)[32],
+                                              const float (&b)[32], float (&p)[32])
+{
+    const int lane = threadIdx.x & 31;
+    const float xa = lane < k ? s[slot * 64 + lane] : 0.f;
+    const float xb = lane + 32 < k ? s[slot * 64 + lane + 32] : 0.f;
+#pragma unroll
+    for (int o = 0; o < 32; ++o) p[o] = fmaf(b[o], xb, fmaf(a[o], xa, p[o]));
+}
+
+// Downsweep of the subtree st rooted at level Lr with depth L = q - Lr (Sec. 3.3, Alg 6), ranks
+// 33 .. 64: the totals level by level in the CTA's slots (the root's parent total from an
+// earlier launch), then per leaf its total, the expansion (warp h of the pair takes the rows
+// 32h + lane, 32h + lane + 64, ...) and the epilogue.
+template <typename T>
+__global__ void __launch_bounds__(kCtaThreads, 2) k_down_cta2(Op<T> op, Vec<T> vec, int Lr, int L)
+{
+    static_assert(sizeof(T) == 4, "FP32 only: 64 FP64 outputs per warp pair would not fit the registers");
+    extern __shared__ __align__(16) unsigned char ws_smem[];
+    float *sy = reinterpret_cast<float *>(ws_smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pair = warp >> 1, h = warp & 1, o = 32 * h + lane;
+    const int k = op.k, kx = op.kx, mp = op.mp, vs = vec.vs;
+    const int64_t st = blockIdx.x;
+    // the total of node (rel, i) into its slot: E_node yhat_parent + own
+    auto total = [&](int rel, int i) {
+        const int64_t node = (int64_t(1) << (Lr + rel)) + st * (int64_t(1) << rel) + i;
+        const float own = o < k ? vec.yh[node * kx * vs + o] : 0.f;
+        float p[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) p[q] = 0.f;
+        float r = 0.f;
+        if (Lr + rel >= 1) {
+            float a[32], b[32];
+            wp_load_rows(op.Et + node * k * kx, k, kx, h, a, b);
+            if (rel >= 1) {
+                wp_accumulate(sy, (1 << (rel - 1)) + (i >> 1), k, a, b, p);
+            } else {  // the subtree root: its parent's total from an earlier launch
+                const float *yp = vec.yh + (node >> 1) * kx * vs;
+                const float xa = lane < k ? __ldcg(yp + lane) : 0.f;
+                const float xb = lane + 32 < k ? __ldcg(yp + lane + 32) : 0.f;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) p[q] = fmaf(b[q], xb, fmaf(a[q], xa, p[q]));
+            }
+            r = ws_reduce<float, 32>(p);
+        }
+        if (o < k) sy[((1 << rel) + i) * 64 + o] = r + own;
+    };
+    for (int rel = 0; rel < L; ++rel) {
+        for (int i = pair; i < (1 << rel); i += kCtaPairs) total(rel, i);
+        __syncthreads();
+    }
+    const int nleaf = 1 << L;
+    for (int j = pair; j < nleaf; j += kCtaPairs) {
+        total(L, j);
+        ws_pair_sync(pair);  // both halves of the leaf's total are in its slot
+        const int64_t t = st * nleaf + j;
+        const int r0 = op.leaf_lo[t], R = op.leaf_lo[t + 1] - r0;
+        const float *__restrict__ ut = op.Ut + t * kx * mp;
+        const float *__restrict__ yd = vec.yd + t * mp * vs;
+        const float *__restrict__ yl = sy + (nleaf + j) * 64;
+        for (int ib = 32 * h; ib < R; ib += 64) {  // uniform over the warp
+            const int i = ib + lane;
+            float y = 0.f;
+            if (i < mp) {
+#pragma unroll 16
+                for (int nu = 0; nu < k; ++nu) y = fmaf(__ldg(ut + nu * mp + i), yl[nu], y);
+            }
+            if (i < R) {
+                const float v = y + yd[i];
+                float *dst = vec.Y + op.perm[r0 + i];
+                *dst = (vec.beta == 0.f) ? vec.alpha * v : vec.alpha * v + vec.beta * *dst;
             }
         }
     }
