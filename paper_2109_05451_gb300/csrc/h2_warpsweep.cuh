@@ -1,5 +1,5 @@
-// h2_warpsweep.cuh -- sweeps and coupling rows of operators of small rank (k <= 32), one
-// vector.
+// h2_warpsweep.cuh -- sweeps and coupling rows of operators of small rank (k <= 32), and the
+// bottom downsweep of FP32 ranks 33 .. 64, one vector.
 //
 // With k <= 32 a node's coefficient vector fits one warp and a transfer or leaf-basis tile is
 // a few hundred bytes to a few KB. The staged kernels of h2_stream.cuh (one tile per pipeline
